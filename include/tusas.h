@@ -1,0 +1,162 @@
+/*
+ * tusas-b300: C-ABI of the B300 (sm_103a) hot path of the fully implicit
+ * phase-field method of Ghosh, Newman and Francois, "Tusas: a fully implicit
+ * parallel approach for coupled phase-field equations" (arXiv 2006.16764).
+ *
+ * The library evaluates, on one GPU, the discrete residual F(U) of the coupled
+ * phase-field / solute (or dimensionless temperature) system on a structured
+ * box of Q1 quadrilaterals or hexahedra (Sec. 2.1.1, Eqs. pf2, conc2, gs, jat,
+ * with the theta-method of Eqs. dpf / theta at theta = 1), its Jacobian action
+ * (finite difference, Eq. JFmatvec, or an exact tangent), the transposed
+ * action, the block-diagonal preconditioner of Eq. (pre) and a Newton-Krylov
+ * time step (Sec. 2.2, 2.3).
+ *
+ * Conventions for every entry point:
+ *   - vectors are FP64 arrays of length 2*N_nodes, field-major
+ *     [phi(0..N_nodes-1) ; u(0..N_nodes-1)], node index i + (nx+1)(j + (ny+1)k);
+ *   - vector pointers are caller-owned DEVICE memory of the handle's device
+ *     unless an entry point says otherwise; the library never frees them;
+ *   - work is enqueued on the handle's stream (tusas_set_stream) and is
+ *     asynchronous unless the entry point says that it synchronises;
+ *   - every call returns TUSAS_OK (0) or a negative code and never aborts the
+ *     process; tusas_last_error() gives a one-line description.
+ */
+#ifndef TUSAS_H
+#define TUSAS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TUSAS_OK = 0,
+  TUSAS_EINVAL = -1,     /* bad mesh, parameters, pointer or size            */
+  TUSAS_ECUDA = -2,      /* a CUDA runtime call failed                        */
+  TUSAS_ENOMEM = -3,     /* device allocation failed or exceeded the cap      */
+  TUSAS_ENOCONV = -4,    /* Newton / GMRES / line search did not converge     */
+  TUSAS_ENONFINITE = -5  /* a NaN or Inf appeared in a residual norm          */
+};
+
+/* Structured box of Q1 elements; dim 2 (nz = 0) or 3. Node (i,j,k) sits at
+ * (x0 + i h, y0 + j h, z0 + k h). */
+typedef struct tusas_mesh {
+  int dim;
+  int nx, ny, nz;
+  double h;
+  double x0, y0, z0;
+} tusas_mesh;
+
+/* Model and solver parameters, nondimensional (Sec. 4.2: W0 = tau0 = 1).
+ * model 0: pure metal (Karma-Rappel phi + temperature u, k must be 1);
+ * model 1: dilute binary alloy (Sec. 4.2, Eqs. pf2..jat). */
+typedef struct tusas_params {
+  int model;
+  double W0, tau0, eps4, lam, D, k;
+  double lT, Vp, zT;     /* frozen gradient G4 = (x_last - zT - Vp t)/lT, model 1, lT != 0 */
+  double theta;          /* must be 1 (backward Euler) */
+  int jat_normalised;    /* 1: antitrapping along grad(phi)/|grad(phi)|, 0: along grad(phi) */
+  int time_form;         /* 0: tau0 B a^2 (phi - phi^n)/dt; 1: tau0 ([B a^2 phi]^{n+1} - [..]^n)/dt */
+  int jvp_mode;          /* Newton-Krylov Jacobian action: 0 finite difference, 1 exact tangent */
+  int precond;           /* 0 none, 1 point Jacobi, 2 block Jacobi with geometric multigrid */
+  int smoother_fp32;     /* multigrid operators, smoother and coarse levels in FP32 (1) or FP64 (0) */
+  int gmres_restart, gmres_maxit, newton_maxit;
+  double newton_rtol, newton_atol;
+  double eta0, eta_min, eta_max, gamma, omega;   /* forcing terms, Eqs. force1..forcing */
+  int mg_levels, cheb_degree, coarse_degree, linesearch_max;
+} tusas_params;
+
+/* Statistics of one tusas_step. */
+typedef struct tusas_stats {
+  int converged;
+  int newton_its;
+  int gmres_its;
+  int linesearch_halvings;
+  int residual_evals;      /* evaluations of F over the whole mesh          */
+  int jv_evals;            /* Jacobian actions over the whole mesh          */
+  double fnorm0, fnorm;    /* ||F|| at the first and last Newton iterate     */
+  int gmres_per_newton[32];
+} tusas_stats;
+
+typedef struct tusas_handle tusas_handle;
+
+/* Create a handle on the current CUDA device: validates mesh and parameters
+ * and allocates the handle's workspaces (state, Krylov basis, linearisation
+ * store, multigrid hierarchy). Returns TUSAS_EINVAL, TUSAS_ENOMEM or
+ * TUSAS_ECUDA on failure with *out = NULL. */
+int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handle** out);
+
+/* Free every workspace of the handle (synchronises its stream). NULL is a no-op. */
+void tusas_destroy(tusas_handle* h);
+
+/* Stream for all later work (a cudaStream_t; NULL = legacy default stream). */
+int tusas_set_stream(tusas_handle* h, void* cuda_stream);
+
+/* Replace the parameters (same rules as tusas_create; the mesh is fixed). */
+int tusas_set_params(tusas_handle* h, const tusas_params* params);
+
+/* Number of unknowns 2*(nx+1)(ny+1)(nz+1) of the handle's mesh. */
+long long tusas_ndofs(const tusas_handle* h);
+
+/* Set the state U^n (copied; host or device pointer, any memory the CUDA
+ * runtime can address), its time t^n and the step dt used by later calls.
+ * Synchronises. */
+int tusas_set_state(tusas_handle* h, const double* U, double t, double dt);
+
+/* Copy the current state into U (host or device pointer). Synchronises. */
+int tusas_get_state(tusas_handle* h, double* U);
+
+/* Current time t^n of the state. */
+double tusas_time(const tusas_handle* h);
+
+/* F(U) of Eqs. (pf2)/(conc2) at theta = 1 with the stored U^n, t^n, dt:
+ * Galerkin residual on the Q1 mesh with the 2^dim-point Gauss rule. U and F
+ * are device vectors (may not alias). Deterministic: bitwise identical on
+ * repeated calls. */
+int tusas_residual(tusas_handle* h, const double* U, double* F);
+
+/* Exact Jacobian action Jv = F'(U) v (Sec. 2.2, the operator that Eq.
+ * JFmatvec approximates). Builds the pointwise linearisation at U, then
+ * applies it. U, v, Jv device vectors (Jv may not alias U or v). */
+int tusas_jvp(tusas_handle* h, const double* U, const double* v, double* Jv);
+
+/* Finite-difference action (F(U + eps v) - F(U))/eps of Eq. (JFmatvec) with
+ * eps = sqrt((1 + ||U||) 2^-52)/||v||. Device vectors; Jv = 0 when v = 0. */
+int tusas_jvp_fd(tusas_handle* h, const double* U, const double* v, double* Jv);
+
+/* Transposed action JTw = F'(U)^T w (the adjoint of tusas_jvp). */
+int tusas_jtvp(tusas_handle* h, const double* U, const double* w, double* JTw);
+
+/* (dF/dU^n)^T w at U, with the stored U^n: the coupling of consecutive time
+ * steps in a discrete adjoint. */
+int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* out);
+
+/* dF/dp at U for parameter `which` (0 = eps4, the anisotropy of Eq. gs). */
+int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF);
+
+/* Build the preconditioner of Eq. (pre) (blocks of Eqs. pref2 / preconc2)
+ * at the iterate U with the stored U^n and dt. */
+int tusas_precond_setup(tusas_handle* h, const double* U);
+
+/* z = M^-1 r with the preconditioner of the last tusas_precond_setup:
+ * identity, point Jacobi, or one multigrid V-cycle per diagonal block.
+ * r and z are FP64 device vectors and may not alias. */
+int tusas_precond_apply(tusas_handle* h, const double* r, double* z);
+
+/* One backward-Euler step of size dt: solve F(U; U^n) = 0 by Newton-Krylov
+ * (Sec. 2.2/2.3: right-preconditioned restarted GMRES, forcing terms,
+ * backtracking line search) from U = U^n, then U^n <- U, t^n <- t^n + dt.
+ * Synchronises; fills *stats if non-NULL. On TUSAS_ENOCONV the state is
+ * left unchanged. */
+int tusas_step(tusas_handle* h, tusas_stats* stats);
+
+/* Deterministic FP64 dot product x . y of n doubles (device vectors); the
+ * result is written to *result (host pointer). Synchronises. */
+int tusas_dot(tusas_handle* h, const double* x, const double* y, long long n, double* result);
+
+/* Description of the last error on this handle (never NULL). */
+const char* tusas_last_error(const tusas_handle* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TUSAS_H */

@@ -1,0 +1,590 @@
+// C-ABI entry points (include/tusas.h): handle, state, operator calls and the
+// Newton-Krylov time step of Sec. 2.2 / 2.3. The host loop only sees scalars
+// (norms, the Hessenberg column); every vector operation runs in the
+// library's kernels on the handle's stream.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "../../include/tusas.h"
+#include "ops.h"
+#include "precond.h"
+
+using tusas::i64;
+
+struct tusas_handle {
+  tusas_mesh mesh;
+  tusas_params prm;
+  tusas::DevMesh dm;
+  tusas::ElemCtx ec;
+  cudaStream_t st = nullptr;
+  int device = 0;
+  i64 nn = 0, N = 0;
+  double t = 0.0, dt = 0.0;
+  bool have_state = false;
+  double *Un = nullptr, *U = nullptr, *F = nullptr, *Ft = nullptr, *dU = nullptr, *Ut = nullptr, *tmp = nullptr,
+         *tmp2 = nullptr;
+  double *lin = nullptr, *lin_t = nullptr;
+  size_t lin_n = 0;
+  double *V = nullptr, *Z = nullptr;
+  int m = 0;  // restart length the basis was allocated for
+  double* partials = nullptr;
+  double* sc = nullptr;  // device scalars: [0..63] h1, [64..127] h2, [128..191] y, [192..] misc
+  tusas::Precond pc;
+  bool pc_ready = false;
+  std::string err;
+};
+
+namespace {
+
+
+int fail(tusas_handle* h, int code, const std::string& msg) {
+  if (h) h->err = msg;
+  return code;
+}
+
+#define TCK(call)                                                                                  \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(h, TUSAS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
+  if (!m || !p) {
+    why = "null mesh or params";
+    return TUSAS_EINVAL;
+  }
+  if (m->dim != 2 && m->dim != 3) {
+    why = "dim must be 2 or 3";
+    return TUSAS_EINVAL;
+  }
+  if (m->nx < 1 || m->ny < 1 || (m->dim == 3 && m->nz < 1) || (m->dim == 2 && m->nz != 0)) {
+    why = "element counts must be >= 1 (nz = 0 in 2D)";
+    return TUSAS_EINVAL;
+  }
+  if (!(m->h > 0.0) || !isfinite(m->h)) {
+    why = "h must be positive and finite";
+    return TUSAS_EINVAL;
+  }
+  const double nodes = (double)(m->nx + 1) * (m->ny + 1) * (m->dim == 3 ? m->nz + 1 : 1);
+  if (nodes > 2.0e9) {
+    why = "mesh too large (more than 2e9 nodes)";
+    return TUSAS_EINVAL;
+  }
+  if (p->model != 0 && p->model != 1) {
+    why = "model must be 0 (pure metal) or 1 (alloy)";
+    return TUSAS_EINVAL;
+  }
+  if (p->model == 0 && p->k != 1.0) {
+    why = "the pure-metal model needs k = 1";
+    return TUSAS_EINVAL;
+  }
+  if (p->theta != 1.0) {
+    why = "only theta = 1 (backward Euler) is implemented";
+    return TUSAS_EINVAL;
+  }
+  if (!(p->W0 > 0) || !(p->tau0 > 0) || !(p->D >= 0) || !(p->eps4 >= 0 && p->eps4 < 0.25)) {
+    why = "W0, tau0 must be > 0, D >= 0, 0 <= eps4 < 1/4";
+    return TUSAS_EINVAL;
+  }
+  if (p->model == 1 && p->lT != 0.0 && !isfinite(p->lT)) {
+    why = "lT must be finite";
+    return TUSAS_EINVAL;
+  }
+  if (p->precond < 0 || p->precond > 2 || p->jvp_mode < 0 || p->jvp_mode > 1 || p->time_form < 0 ||
+      p->time_form > 1) {
+    why = "precond in 0..2, jvp_mode in 0..1, time_form in 0..1";
+    return TUSAS_EINVAL;
+  }
+  if (p->gmres_restart < 1 || p->gmres_restart > 30 || p->gmres_maxit < 1 || p->newton_maxit < 0 ||
+      p->newton_maxit > 30 || p->linesearch_max < 0) {
+    why = "gmres_restart in 1..30, gmres_maxit >= 1, newton_maxit in 0..30, linesearch_max >= 0";
+    return TUSAS_EINVAL;
+  }
+  if (p->precond == 2 && (p->mg_levels < 1 || p->cheb_degree < 1 || p->coarse_degree < 1)) {
+    why = "mg_levels, cheb_degree, coarse_degree must be >= 1";
+    return TUSAS_EINVAL;
+  }
+  return TUSAS_OK;
+}
+
+void fill_phys(tusas_handle* h) {
+  tusas::DevPhys P;
+  const tusas_params& p = h->prm;
+  P.model = p.model;
+  P.time_form = p.time_form;
+  P.jat_norm = p.jat_normalised;
+  P.W0 = p.W0;
+  P.tau0 = p.tau0;
+  P.eps4 = p.eps4;
+  P.lam = p.lam;
+  P.D = p.D;
+  P.k = p.k;
+  P.lT = p.lT;
+  P.Vp = p.Vp;
+  P.zT = p.zT;
+  P.dt = h->dt;
+  P.idt = h->dt > 0 ? 1.0 / h->dt : 0.0;
+  P.t_new = h->t + h->dt;
+  P.has_g4 = p.model == 1 && p.lT != 0.0;
+  tusas::elem_ctx_init(h->ec, h->dm, P);
+}
+
+int ensure_lin(tusas_handle* h, bool trial) {
+  if (!h->lin) {
+    h->lin_n = tusas::elem_lin_doubles(h->ec);
+    TCK(cudaMalloc(&h->lin, sizeof(double) * h->lin_n));
+  }
+  if (trial && !h->lin_t) TCK(cudaMalloc(&h->lin_t, sizeof(double) * h->lin_n));
+  return TUSAS_OK;
+}
+
+int ready(tusas_handle* h) {
+  if (!h) return TUSAS_EINVAL;
+  if (!h->have_state || !(h->dt > 0)) return fail(h, TUSAS_EINVAL, "call tusas_set_state with dt > 0 first");
+  return TUSAS_OK;
+}
+
+// ||x||^2 into device scalar slot `slot` (no synchronisation)
+cudaError_t norm2_dev(tusas_handle* h, const double* x, int slot) {
+  return tusas::multidot(h->N, 1, x, 0, x, h->partials, h->sc + slot, h->st);
+}
+
+int host_norm(tusas_handle* h, const double* x, double* out) {
+  TCK(norm2_dev(h, x, 200));
+  double v;
+  TCK(cudaMemcpyAsync(&v, h->sc + 200, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  *out = sqrt(v);
+  return TUSAS_OK;
+}
+
+__global__ void k_fd_eps(const double* unorm2, const double* vnorm2, double* eps_out) {
+  const double un = sqrt(*unorm2), vn = sqrt(*vnorm2);
+  if (vn == 0.0) {
+    eps_out[0] = 0.0;
+    eps_out[1] = 0.0;
+  } else {
+    const double e = sqrt((1.0 + un) * 2.220446049250313e-16) / vn;
+    eps_out[0] = e;
+    eps_out[1] = 1.0 / e;
+  }
+}
+
+// Jv = (F(U + eps v) - F0)/eps with ||U||^2 already in sc[210]
+int fd_jv(tusas_handle* h, const double* U, const double* F0, const double* v, double* Jv) {
+  TCK(norm2_dev(h, v, 211));
+  k_fd_eps<<<1, 1, 0, h->st>>>(h->sc + 210, h->sc + 211, h->sc + 212);
+  TCK(tusas::vxpay(h->N, U, 0.0, h->sc + 212, v, h->tmp2, h->st));
+  TCK(tusas::elem_run(tusas::M_RES, h->ec, h->tmp2, h->Un, nullptr, Jv, nullptr, h->st));
+  TCK(tusas::vfdq(h->N, F0, Jv, h->sc + 213, h->st));
+  return TUSAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handle** out) {
+  if (!out) return TUSAS_EINVAL;
+  *out = nullptr;
+  std::string why;
+  int rc = validate(mesh, params, why);
+  if (rc) return rc;
+  tusas_handle* h = new tusas_handle();
+  h->mesh = *mesh;
+  h->prm = *params;
+  TCK(cudaGetDevice(&h->device));
+  tusas::DevMesh& d = h->dm;
+  d.dim = mesh->dim;
+  d.nx = mesh->nx;
+  d.ny = mesh->ny;
+  d.nz = mesh->dim == 3 ? mesh->nz : 0;
+  d.nnx = mesh->nx + 1;
+  d.nny = mesh->ny + 1;
+  d.nnz = mesh->dim == 3 ? mesh->nz + 1 : 1;
+  d.nn = (i64)d.nnx * d.nny * d.nnz;
+  d.ne = (i64)d.nx * d.ny * (mesh->dim == 3 ? d.nz : 1);
+  d.h = mesh->h;
+  d.x0 = mesh->x0;
+  d.y0 = mesh->y0;
+  d.z0 = mesh->z0;
+  h->nn = d.nn;
+  h->N = 2 * d.nn;
+  fill_phys(h);
+  double** vecs[] = {&h->Un, &h->U, &h->F, &h->Ft, &h->dU, &h->Ut, &h->tmp, &h->tmp2};
+  for (double** v : vecs) {
+    cudaError_t e = cudaMalloc(v, sizeof(double) * h->N);
+    if (e != cudaSuccess) {
+      tusas_destroy(h);
+      return TUSAS_ENOMEM;
+    }
+  }
+  h->m = params->gmres_restart;
+  if (cudaMalloc(&h->V, sizeof(double) * h->N * (h->m + 1)) != cudaSuccess ||
+      cudaMalloc(&h->Z, sizeof(double) * h->N * h->m) != cudaSuccess ||
+      cudaMalloc(&h->partials, sizeof(double) * tusas::reduce_blocks() * 32) != cudaSuccess ||
+      cudaMalloc(&h->sc, sizeof(double) * 256) != cudaSuccess) {
+    tusas_destroy(h);
+    return TUSAS_ENOMEM;
+  }
+  if (params->precond > 0) {
+    cudaError_t e = h->pc.create(h->dm, params->precond, params->smoother_fp32, params->mg_levels,
+                                 params->cheb_degree, params->coarse_degree);
+    if (e != cudaSuccess) {
+      tusas_destroy(h);
+      return e == cudaErrorMemoryAllocation ? TUSAS_ENOMEM : TUSAS_ECUDA;
+    }
+  }
+  *out = h;
+  return TUSAS_OK;
+}
+
+void tusas_destroy(tusas_handle* h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  cudaDeviceSynchronize();
+  double* vecs[] = {h->Un, h->U, h->F, h->Ft, h->dU, h->Ut, h->tmp, h->tmp2, h->lin, h->lin_t, h->V, h->Z,
+                    h->partials, h->sc};
+  for (double* v : vecs)
+    if (v) cudaFree(v);
+  h->pc.destroy();
+  delete h;
+}
+
+int tusas_set_stream(tusas_handle* h, void* s) {
+  if (!h) return TUSAS_EINVAL;
+  h->st = (cudaStream_t)s;
+  return TUSAS_OK;
+}
+
+int tusas_set_params(tusas_handle* h, const tusas_params* p) {
+  if (!h) return TUSAS_EINVAL;
+  std::string why;
+  int rc = validate(&h->mesh, p, why);
+  if (rc) return fail(h, rc, why);
+  if (p->gmres_restart > h->m || p->precond != h->prm.precond || p->smoother_fp32 != h->prm.smoother_fp32 ||
+      p->mg_levels != h->prm.mg_levels || p->model != h->prm.model)
+    return fail(h, TUSAS_EINVAL, "restart length, preconditioner kind/precision/levels and model are fixed at create");
+  h->prm = *p;
+  h->pc.cheb_degree = p->cheb_degree;
+  h->pc.coarse_degree = p->coarse_degree;
+  fill_phys(h);
+  h->pc_ready = false;
+  return TUSAS_OK;
+}
+
+long long tusas_ndofs(const tusas_handle* h) { return h ? (long long)h->N : -1; }
+
+double tusas_time(const tusas_handle* h) { return h ? h->t : 0.0; }
+
+int tusas_set_state(tusas_handle* h, const double* U, double t, double dt) {
+  if (!h || !U) return TUSAS_EINVAL;
+  if (!(dt > 0) || !isfinite(dt) || !isfinite(t)) return fail(h, TUSAS_EINVAL, "dt must be positive, t finite");
+  TCK(cudaMemcpyAsync(h->Un, U, sizeof(double) * h->N, cudaMemcpyDefault, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  h->t = t;
+  h->dt = dt;
+  h->have_state = true;
+  h->pc_ready = false;
+  fill_phys(h);
+  return TUSAS_OK;
+}
+
+int tusas_get_state(tusas_handle* h, double* U) {
+  if (!h || !U) return TUSAS_EINVAL;
+  if (!h->have_state) return fail(h, TUSAS_EINVAL, "no state set");
+  TCK(cudaMemcpyAsync(U, h->Un, sizeof(double) * h->N, cudaMemcpyDefault, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  return TUSAS_OK;
+}
+
+int tusas_residual(tusas_handle* h, const double* U, double* F) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U || !F || U == F) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, F, nullptr, h->st));
+  return TUSAS_OK;
+}
+
+int tusas_jvp(tusas_handle* h, const double* U, const double* v, double* Jv) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U || !v || !Jv || Jv == U || Jv == v) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  rc = ensure_lin(h, false);
+  if (rc) return rc;
+  TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st));
+  TCK(tusas::elem_run(tusas::M_JV, h->ec, nullptr, nullptr, v, Jv, h->lin, h->st));
+  return TUSAS_OK;
+}
+
+int tusas_jvp_fd(tusas_handle* h, const double* U, const double* v, double* Jv) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U || !v || !Jv || Jv == U || Jv == v) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, h->tmp, nullptr, h->st));
+  TCK(norm2_dev(h, U, 210));
+  return fd_jv(h, U, h->tmp, v, Jv);
+}
+
+int tusas_jtvp(tusas_handle* h, const double* U, const double* w, double* JTw) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U || !w || !JTw || JTw == U || JTw == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  rc = ensure_lin(h, false);
+  if (rc) return rc;
+  TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st));
+  TCK(tusas::elem_run(tusas::M_JTV, h->ec, nullptr, nullptr, w, JTw, h->lin, h->st));
+  return TUSAS_OK;
+}
+
+int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* out) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U || !w || !out || out == U || out == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  TCK(tusas::elem_run(tusas::M_PREV_T, h->ec, U, h->Un, w, out, nullptr, h->st));
+  return TUSAS_OK;
+}
+
+int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U || !dF || U == dF) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  if (which != 0) return fail(h, TUSAS_EINVAL, "only which = 0 (eps4) is available");
+  TCK(tusas::elem_run(tusas::M_DEPS, h->ec, U, h->Un, nullptr, dF, nullptr, h->st));
+  return TUSAS_OK;
+}
+
+int tusas_precond_setup(tusas_handle* h, const double* U) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!U) return fail(h, TUSAS_EINVAL, "null vector");
+  TCK(h->pc.setup(h->ec, h->prm.theta, U, h->Un, h->st));
+  h->pc_ready = true;
+  return TUSAS_OK;
+}
+
+int tusas_precond_apply(tusas_handle* h, const double* r, double* z) {
+  if (!h || !r || !z || r == z) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  if (h->prm.precond == 0) {
+    TCK(tusas::vcopy(h->N, r, z, h->st));
+    return TUSAS_OK;
+  }
+  if (!h->pc_ready) return fail(h, TUSAS_EINVAL, "call tusas_precond_setup first");
+  TCK(h->pc.apply(r, z, h->st));
+  return TUSAS_OK;
+}
+
+int tusas_dot(tusas_handle* h, const double* x, const double* y, long long n, double* result) {
+  if (!h || !x || !y || !result || n < 0) return TUSAS_EINVAL;
+  if (n == 0) {
+    *result = 0.0;
+    return TUSAS_OK;
+  }
+  TCK(tusas::multidot(n, 1, x, 0, y, h->partials, h->sc + 200, h->st));
+  TCK(cudaMemcpyAsync(result, h->sc + 200, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  return TUSAS_OK;
+}
+
+const char* tusas_last_error(const tusas_handle* h) {
+  if (!h) return "null handle";
+  return h->err.empty() ? "no error" : h->err.c_str();
+}
+
+// ---------------------------------------------------------------------------
+// Newton-Krylov step
+// ---------------------------------------------------------------------------
+
+static int jv_apply(tusas_handle* h, bool exact, const double* z, double* out) {
+  if (exact) {
+    TCK(tusas::elem_run(tusas::M_JV, h->ec, nullptr, nullptr, z, out, h->lin, h->st));
+    return TUSAS_OK;
+  }
+  return fd_jv(h, h->U, h->F, z, out);
+}
+
+static int prec_apply(tusas_handle* h, const double* r, double* z) {
+  if (h->prm.precond == 0) {
+    TCK(tusas::vcopy(h->N, r, z, h->st));
+    return TUSAS_OK;
+  }
+  TCK(h->pc.apply(r, z, h->st));
+  return TUSAS_OK;
+}
+
+// Flexible right-preconditioned restarted GMRES with classical Gram-Schmidt
+// applied twice, x0 = 0; solves J x = b (b = -F) to ||b - J x|| <= tol_abs.
+static int gmres(tusas_handle* h, bool exact, const double* b, double* x, double tol_abs, int* its_out,
+                 tusas_stats* stats) {
+  const int m = h->prm.gmres_restart;
+  const i64 N = h->N;
+  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), col(64);
+  TCK(cudaMemsetAsync(x, 0, sizeof(double) * N, h->st));
+  int its = 0;
+  // r = b
+  double* r = h->V;  // V_0 doubles as the residual buffer
+  TCK(tusas::vcopy(N, b, r, h->st));
+  double beta;
+  int rc = host_norm(h, r, &beta);
+  if (rc) return rc;
+  double resid = beta;
+  while (beta > tol_abs && its < h->prm.gmres_maxit) {
+    if (!isfinite(beta)) return fail(h, TUSAS_ENONFINITE, "non-finite GMRES residual");
+    TCK(tusas::vscal(N, 1.0 / beta, r, h->st));  // V_0 = r / beta
+    std::fill(g.begin(), g.end(), 0.0);
+    std::fill(H.begin(), H.end(), 0.0);
+    g[0] = beta;
+    int mu = 0;
+    for (int j = 0; j < m; ++j) {
+      double* Vj = h->V + (i64)j * N;
+      double* Zj = h->Z + (i64)j * N;
+      double* w = h->V + (i64)(j + 1) * N;
+      rc = prec_apply(h, Vj, Zj);
+      if (rc) return rc;
+      rc = jv_apply(h, exact, Zj, w);
+      if (rc) return rc;
+      if (stats) stats->jv_evals++;
+      ++its;
+      // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
+      TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc, h->st));
+      TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc, w, nullptr, h->st));
+      TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc + 64, h->st));
+      TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc + 64, w, h->sc, h->st));
+      TCK(norm2_dev(h, w, 63));
+      TCK(cudaMemcpyAsync(col.data(), h->sc, sizeof(double) * 64, cudaMemcpyDeviceToHost, h->st));
+      TCK(cudaStreamSynchronize(h->st));
+      const double hn = sqrt(col[63]);
+      if (!isfinite(hn)) return fail(h, TUSAS_ENONFINITE, "non-finite Krylov vector");
+      for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
+      H[(j + 1) * m + j] = hn;
+      if (hn > 0.0) TCK(tusas::vscal(N, 1.0 / hn, w, h->st));
+      for (int i = 0; i < j; ++i) {
+        const double a = H[i * m + j], bb = H[(i + 1) * m + j];
+        H[i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+      cs[j] = H[j * m + j] / den;
+      sn[j] = H[(j + 1) * m + j] / den;
+      H[j * m + j] = den;
+      H[(j + 1) * m + j] = 0.0;
+      g[j + 1] = -sn[j] * g[j];
+      g[j] = cs[j] * g[j];
+      resid = fabs(g[j + 1]);
+      mu = j + 1;
+      if (resid <= tol_abs || its >= h->prm.gmres_maxit || den == 0.0) break;
+    }
+    for (int i = mu - 1; i >= 0; --i) {
+      double s = g[i];
+      for (int k = i + 1; k < mu; ++k) s -= H[i * m + k] * y[k];
+      y[i] = s / H[i * m + i];
+    }
+    TCK(cudaMemcpyAsync(h->sc + 128, y.data(), sizeof(double) * mu, cudaMemcpyHostToDevice, h->st));
+    TCK(tusas::multi_comb(N, mu, h->Z, N, h->sc + 128, x, h->st));
+    if (resid <= tol_abs || its >= h->prm.gmres_maxit) break;
+    // restart: r = b - J x
+    rc = jv_apply(h, exact, x, h->tmp);
+    if (rc) return rc;
+    if (stats) stats->jv_evals++;
+    TCK(tusas::vcopy(N, b, r, h->st));
+    TCK(tusas::vaxpy(N, -1.0, h->tmp, r, h->st));
+    rc = host_norm(h, r, &beta);
+    if (rc) return rc;
+    resid = beta;
+  }
+  *its_out = its;
+  return TUSAS_OK;
+}
+
+static double forcing(const tusas_params& p, int l, double fn, double fprev, double eta_prev) {
+  if (l == 0) return p.eta0;
+  double eta = p.gamma * pow(fn / fprev, p.omega);
+  eta = std::max(eta, std::max(p.gamma * pow(eta_prev, p.omega), p.eta_min));
+  return std::min(p.eta_max, eta);
+}
+
+int tusas_step(tusas_handle* h, tusas_stats* stats) {
+  int rc = ready(h);
+  if (rc) return rc;
+  tusas_stats S = {};
+  const tusas_params& p = h->prm;
+  const bool exact = p.jvp_mode == 1;
+  const i64 N = h->N;
+  if (exact) {
+    rc = ensure_lin(h, true);
+    if (rc) return rc;
+  }
+  TCK(tusas::vcopy(N, h->Un, h->U, h->st));
+  TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->U, h->Un, nullptr, h->F, h->lin, h->st));
+  S.residual_evals = 1;
+  double fn;
+  rc = host_norm(h, h->F, &fn);
+  if (rc) return rc;
+  if (!isfinite(fn)) return fail(h, TUSAS_ENONFINITE, "non-finite initial residual norm");
+  S.fnorm0 = S.fnorm = fn;
+  const double tol = p.newton_rtol * fn + p.newton_atol;
+  double eta_prev = p.eta0, fprev = 0.0;
+  bool converged = false;
+  for (int l = 0; l <= p.newton_maxit; ++l) {
+    if (S.fnorm < tol || S.fnorm == 0.0) {
+      converged = true;
+      break;
+    }
+    if (l == p.newton_maxit) break;
+    const double eta = forcing(p, l, S.fnorm, fprev, eta_prev);
+    if (p.precond > 0) {
+      TCK(h->pc.setup(h->ec, p.theta, h->U, h->Un, h->st));
+      h->pc_ready = true;
+    }
+    if (!exact) TCK(norm2_dev(h, h->U, 210));
+    // b = -F (in Ft), solve J dU = b
+    TCK(tusas::vfill(N, 0.0, h->Ft, h->st));
+    TCK(tusas::vaxpy(N, -1.0, h->F, h->Ft, h->st));
+    int its = 0;
+    rc = gmres(h, exact, h->Ft, h->dU, eta * S.fnorm, &its, &S);
+    if (rc) return rc;
+    S.gmres_its += its;
+    if (S.newton_its < 32) S.gmres_per_newton[S.newton_its] = its;
+    double lam = 1.0, ftn = 0.0;
+    bool accepted = false;
+    for (int ls = 0; ls <= p.linesearch_max; ++ls) {
+      TCK(tusas::vxpay(N, h->U, lam, nullptr, h->dU, h->Ut, h->st));
+      TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t,
+                          h->st));
+      S.residual_evals++;
+      rc = host_norm(h, h->Ft, &ftn);
+      if (rc) return rc;
+      if (!isfinite(ftn)) return fail(h, TUSAS_ENONFINITE, "non-finite residual norm in the line search");
+      if (ftn <= S.fnorm) {
+        accepted = true;
+        break;
+      }
+      lam *= 0.5;
+      S.linesearch_halvings++;
+    }
+    if (!accepted) break;
+    std::swap(h->U, h->Ut);
+    std::swap(h->F, h->Ft);
+    if (exact) std::swap(h->lin, h->lin_t);
+    fprev = S.fnorm;
+    eta_prev = eta;
+    S.fnorm = ftn;
+    S.newton_its++;
+  }
+  S.converged = converged ? 1 : 0;
+  if (stats) *stats = S;
+  if (!converged) return fail(h, TUSAS_ENOCONV, "Newton did not converge");
+  TCK(tusas::vcopy(N, h->U, h->Un, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  h->t += h->dt;
+  fill_phys(h);
+  h->pc_ready = false;
+  return TUSAS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,39 @@
+// Shared device-side definitions of the tusas-b300 library (sm_103a).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tusas {
+
+typedef long long i64;
+
+// Structured box of Q1 elements (node (i,j,k) at x0 + i h, index i + nnx (j + nny k)).
+struct DevMesh {
+  int dim;
+  int nx, ny, nz;        // elements per axis (nz = 0 in 2D)
+  int nnx, nny, nnz;     // nodes per axis (nnz = 1 in 2D)
+  i64 nn;                // number of nodes
+  i64 ne;                // number of elements
+  double h, x0, y0, z0;
+};
+
+// Pointwise physics constants (Sec. 4.2 model in Karma-Rappel units).
+struct DevPhys {
+  int model;             // 0 pure metal, 1 dilute alloy
+  int time_form;         // 0 c^{n+1}(phi - phi^n)/dt, 1 difference of products
+  int jat_norm;          // antitrapping direction: 1 unit normal, 0 grad(phi)
+  double W0, tau0, eps4, lam, D, k;
+  double lT, Vp, zT;
+  double dt, idt;        // time step and its reciprocal
+  double t_new;          // t^{n+1}, used by the frozen gradient
+  int has_g4;            // model 1 and lT != 0
+};
+
+// Tile shape of the element kernels: one thread per element.
+template <int DIM> struct Tile;
+template <> struct Tile<2> { static const int X = 16, Y = 8, Z = 1; };
+template <> struct Tile<3> { static const int X = 8, Y = 4, Z = 4; };
+
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+
+}  // namespace tusas

@@ -1,0 +1,350 @@
+// Per-element Q1 arithmetic on structured boxes: sum-factorised interpolation
+// to the 2^dim Gauss points, the pointwise integrands of the phase-field /
+// solute system, their linearisation, and the transposed (test-function)
+// accumulation back to the element nodes.
+//
+// Sum factorisation. With eta = 2 xi - 1 per axis, the Q1 interpolant of the
+// element's nodal values v_a (a = ax + 2 ay + 4 az) is
+//     v(eta) = 2^-dim sum_b C_b prod_{d in b} eta_d,
+// C = H v the Walsh-Hadamard transform (butterfly (x, y) -> (x + y, y - x) on
+// every axis). The 2-point Gauss points sit at eta_d = +-1/sqrt(3), so values
+// at all Gauss points are H^T applied to C_b s^|b| 2^-dim (s = 1/sqrt 3), and
+// the derivative along axis d is the (dim-1)-dimensional H^T of the
+// coefficients with bit d set, scaled by 2/(h 2^dim) s^(|b|-1). The test-
+// function accumulation is the exact transpose. In 3D this costs 92 FP64
+// operations for the values and gradient of one field at all 8 Gauss points
+// (256 for the direct basis sums), which matters because the kernels are
+// bound by the FP64 pipe, not by memory.
+#pragma once
+#include "common.cuh"
+
+namespace tusas {
+
+__host__ __device__ constexpr int insert_bit(int j, int d, int bit) {
+  return ((j >> d) << (d + 1)) | (bit << d) | (j & ((1 << d) - 1));
+}
+__host__ __device__ constexpr int remove_bit(int g, int d) {
+  return ((g >> (d + 1)) << d) | (g & ((1 << d) - 1));
+}
+__host__ __device__ constexpr int popc(int x) { return x == 0 ? 0 : (x & 1) + popc(x >> 1); }
+
+// forward transform H (nodes or Gauss points -> Walsh coefficients)
+template <int DIM, typename T = double>
+__device__ __forceinline__ void walsh_fwd(T* v) {
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int a = 0; a < (1 << DIM); ++a) {
+      if (!(a & (1 << d))) {
+        const T x = v[a], y = v[a | (1 << d)];
+        v[a] = x + y;
+        v[a | (1 << d)] = y - x;
+      }
+    }
+  }
+}
+
+// evaluation transform H^T (Walsh coefficients -> values at sign points)
+template <int DIM, typename T = double>
+__device__ __forceinline__ void walsh_eval(T* v) {
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int a = 0; a < (1 << DIM); ++a) {
+      if (!(a & (1 << d))) {
+        const T c0 = v[a], c1 = v[a | (1 << d)];
+        v[a] = c0 - c1;
+        v[a | (1 << d)] = c0 + c1;
+      }
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void walsh_eval<0, double>(double*) {}
+template <>
+__device__ __forceinline__ void walsh_fwd<0, double>(double*) {}
+template <>
+__device__ __forceinline__ void walsh_eval<0, float>(float*) {}
+template <>
+__device__ __forceinline__ void walsh_fwd<0, float>(float*) {}
+
+// Scale factors, computed on the host: value scale vs[k] = s^k 2^-dim,
+// gradient scale gs[k] = s^k 2/(h 2^dim); the "w" variants include the Gauss
+// weight (h/2)^dim for the accumulation.
+template <typename T>
+struct ScalesT {
+  T vs[4], gs[3], vsw[4], gsw[3];
+};
+typedef ScalesT<double> Scales;
+
+// Values (and, if GRAD, gradients) of one field at all Gauss points.
+// grad[d][j]: derivative along d at the Gauss points whose other-axis bits are j.
+template <int DIM, bool GRAD, typename T = double>
+__device__ __forceinline__ void interp(const T* nodal, T* val, T (*grad)[1 << (DIM - 1)], const ScalesT<T>& S) {
+  constexpr int NN = 1 << DIM;
+  T c[NN];
+#pragma unroll
+  for (int a = 0; a < NN; ++a) c[a] = nodal[a];
+  walsh_fwd<DIM, T>(c);
+  if (GRAD) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+      for (int j = 0; j < NN / 2; ++j) grad[d][j] = c[insert_bit(j, d, 1)] * S.gs[popc(j)];
+      walsh_eval<DIM - 1, T>(grad[d]);
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NN; ++b) val[b] = c[b] * S.vs[popc(b)];
+  walsh_eval<DIM, T>(val);
+}
+
+// Transposed accumulation: out_a = w sum_g ( s_g N_a(g) + sum_d f_dg dN_a/dx_d(g) ).
+template <int DIM>
+__device__ __forceinline__ void accumulate(const double* s, double (*f)[1 << DIM], double* out, const Scales& S) {
+  constexpr int NN = 1 << DIM;
+  double acc[NN];
+#pragma unroll
+  for (int g = 0; g < NN; ++g) acc[g] = s[g];
+  walsh_fwd<DIM>(acc);
+#pragma unroll
+  for (int b = 0; b < NN; ++b) acc[b] *= S.vsw[popc(b)];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    double t[NN / 2];
+#pragma unroll
+    for (int j = 0; j < NN / 2; ++j) t[j] = f[d][insert_bit(j, d, 0)] + f[d][insert_bit(j, d, 1)];
+    walsh_fwd<DIM - 1>(t);
+#pragma unroll
+    for (int j = 0; j < NN / 2; ++j) acc[insert_bit(j, d, 1)] += t[j] * S.gsw[popc(j)];
+  }
+  walsh_eval<DIM>(acc);
+#pragma unroll
+  for (int a = 0; a < NN; ++a) out[a] = acc[a];
+}
+
+// ---------------------------------------------------------------------------
+// Pointwise physics (Sec. 4.2, Eqs. pf2, lambda, directional, conc2, jat, gs)
+// ---------------------------------------------------------------------------
+
+#define TUSAS_GUARD_Q 1e-20
+#define TUSAS_INV_2SQRT2 0.35355339059327373
+
+// Anisotropy a(p) = 1 - 3 eps + 4 eps sum n_i^4 (Eq. gs) from p = grad phi.
+// On return n[] is the unit normal, n2[] its squares, sn = sum n_i^4, r = 1/|p|
+// (all zero and a = 1 where |p|^2 < 1e-20).
+template <int DIM>
+struct Aniso {
+  double a, sn, r;
+  double n[DIM], n2[DIM];
+  __device__ __forceinline__ void eval(const double* p, double eps) {
+    double q = p[0] * p[0];
+#pragma unroll
+    for (int d = 1; d < DIM; ++d) q = fma(p[d], p[d], q);
+    if (q < TUSAS_GUARD_Q) {
+      a = 1.0;
+      sn = 0.0;
+      r = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) n[d] = n2[d] = 0.0;
+    } else {
+      r = rsqrt(q);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        n[d] = p[d] * r;
+        n2[d] = n[d] * n[d];
+      }
+      sn = n2[0] * n2[0];
+#pragma unroll
+      for (int d = 1; d < DIM; ++d) sn = fma(n2[d], n2[d], sn);
+      a = fma(4.0 * eps, sn, 1.0 - 3.0 * eps);
+    }
+  }
+};
+
+// Integrands at one Gauss point.
+template <int DIM>
+struct GPOut {
+  double sphi, fphi[DIM], su, fu[DIM];
+};
+
+// Number of stored linearisation coefficients per Gauss point.
+template <int DIM, int MODEL>
+struct NLin {
+  static const int SYM = DIM * (DIM + 1) / 2;
+  static const int PHI = 2 + DIM + SYM;              // alpha_phi, alpha_u, alpha_p, H
+  static const int VALUE = MODEL == 0 ? PHI : PHI + 2 + DIM + 4 + DIM;
+};
+
+// symmetric index (i <= j) -> 0..SYM-1: diagonal first, then (0,1),(0,2),(1,2)
+template <int DIM>
+__host__ __device__ constexpr int sym_index(int i, int j) {
+  return i == j ? i : (DIM == 2 ? 2 : (i + j == 1 ? 3 : (i + j == 2 ? 4 : 5)));
+}
+
+// Residual integrands and, if LIN, the pointwise Jacobian written to L[c]
+// (c-th coefficient of this Gauss point; stride given by the caller's writer).
+template <int DIM, int MODEL, bool LIN>
+__device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u, double dphi, double du,
+                                          const double* p, const double* g, const double* pn, double G4,
+                                          GPOut<DIM>& o, double* L) {
+  Aniso<DIM> A;
+  A.eval(p, P.eps4);
+  const double eps = P.eps4;
+  const double W2 = P.W0 * P.W0;
+  const double c16 = 16.0 * eps;
+  // anisotropic flux f = W0^2 a p_i (a + 16 eps (n_i^2 - sn))
+  const double W2a = W2 * A.a;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, A.n2[d] - A.sn, A.a);
+  const double phihat = dphi * P.idt;
+  const double omk = 1.0 - P.k;
+  const double B = fma(omk, u, 1.0);
+  const double a2 = A.a * A.a;
+  const double phi2 = phi * phi;
+  const double om = 1.0 - phi2;
+  const double ug = u + G4;
+  double time;
+  double an2 = 0.0, Bn = 0.0, phin = phi - dphi;
+  if (P.time_form == 0) {
+    time = P.tau0 * B * a2 * phihat;
+  } else {
+    Aniso<DIM> An;
+    An.eval(pn, eps);
+    an2 = An.a * An.a;
+    Bn = fma(omk, u - du, 1.0);
+    time = P.tau0 * (B * a2 * phi - Bn * an2 * phin) * P.idt;
+  }
+  o.sphi = time - (phi * om - P.lam * om * om * ug);
+  const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - omk * phin);
+  o.su = Acoef * du * P.idt - 0.5 * phihat * B;
+  double Dq = P.D, jn = 0.0;
+  if (MODEL == 0) {
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o.fu[d] = P.D * g[d];
+  } else {
+    Dq = 0.5 * P.D * (1.0 - phi);
+    const double cj = TUSAS_INV_2SQRT2 * P.W0 * B * phihat;
+    jn = P.jat_norm ? cj * A.r : cj;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o.fu[d] = fma(Dq, g[d], jn * p[d]);
+  }
+  if (!LIN) return;
+  // ---- pointwise Jacobian -------------------------------------------------
+  double ap[DIM];  // da/dp_i = 16 eps n_i (n_i^2 - sn) / |p|
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) ap[d] = c16 * A.n[d] * (A.n2[d] - A.sn) * A.r;
+  const double dbulk = (1.0 - 3.0 * phi2) + 4.0 * P.lam * phi * om * ug;
+  const double tfac = P.time_form == 0 ? phihat : phi * P.idt;  // multiplies d(B a^2)
+  L[0] = P.tau0 * B * a2 * P.idt - dbulk;                       // alpha_phi
+  L[1] = P.tau0 * omk * a2 * tfac + P.lam * om * om;            // alpha_u
+  const double c2a = 2.0 * P.tau0 * B * tfac * A.a;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * ap[d];         // alpha_p
+  // H = W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn))
+  //            + n_i n_j (32 eps a (sn - n_i^2 - n_j^2) + 256 eps^2 (n_i^2 - sn)(n_j^2 - sn)) ]
+  const double e32a = 32.0 * eps * A.a, e256 = 256.0 * eps * eps, e16a = 16.0 * eps * A.a;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+#pragma unroll
+    for (int j = i; j < DIM; ++j) {
+      const double mi = A.n2[i] - A.sn, mj = A.n2[j] - A.sn;
+      double v = A.n[i] * A.n[j] * (e32a * (A.sn - A.n2[i] - A.n2[j]) + e256 * mi * mj);
+      if (i == j) v += a2 + e16a * (3.0 * A.n2[i] - A.sn);
+      L[2 + DIM + sym_index<DIM>(i, j)] = W2 * v;
+    }
+  }
+  if (MODEL == 1) {
+    constexpr int o0 = NLin<DIM, 1>::PHI;
+    L[o0 + 0] = -0.5 * B * P.idt;                    // beta_phi
+    L[o0 + 1] = Acoef * P.idt - 0.5 * phihat * omk;  // beta_u
+    // direction of the antitrapping current and its derivative factors
+    const double cw = TUSAS_INV_2SQRT2 * P.W0;
+    double nv[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) nv[d] = P.jat_norm ? A.n[d] : p[d];
+    const double kap = P.jat_norm ? cw * B * phihat * A.r : cw * B * phihat;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(-0.5 * P.D, g[d], cw * B * P.idt * nv[d]);  // gamma_phi
+    L[o0 + 2 + DIM] = cw * omk * phihat;                                                             // c_u
+    L[o0 + 3 + DIM] = Dq;                                                                            // gamma_g
+    L[o0 + 4 + DIM] = kap;                                                                           // kappa1
+    L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                                        // kappa2
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];                                      // nvec
+  }
+}
+
+// Apply the stored pointwise Jacobian (TRANS = false) or its transpose.
+// Inputs (x0, x1, xp, xg): forward = (dphi, du, dp, dg);
+// transpose = (s_phi, s_u, f_phi, f_u) test-side quantities.
+template <int DIM, int MODEL, bool TRANS>
+__device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, double x0, double x1, const double* xp,
+                                          const double* xg, GPOut<DIM>& o) {
+  constexpr int S0 = 2 + DIM;
+  double Hx[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    double v = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) v = fma(L[S0 + sym_index<DIM>(i < j ? i : j, i < j ? j : i)], xp[j], v);
+    Hx[i] = v;
+  }
+  if (!TRANS) {
+    double sp = fma(L[0], x0, L[1] * x1);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) sp = fma(L[2 + d], xp[d], sp);
+    o.sphi = sp;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o.fphi[d] = Hx[d];
+    if (MODEL == 0) {
+      o.su = (x1 - 0.5 * x0) * P.idt;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) o.fu[d] = P.D * xg[d];
+    } else {
+      constexpr int o0 = NLin<DIM, 1>::PHI;
+      o.su = fma(L[o0], x0, L[o0 + 1] * x1);
+      const double* nv = L + o0 + 6 + DIM;
+      double ndp = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) ndp = fma(nv[d], xp[d], ndp);
+      const double cu = L[o0 + 2 + DIM] * x1 - L[o0 + 5 + DIM] * ndp;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d)
+        o.fu[d] = fma(L[o0 + 2 + d], x0, fma(L[o0 + 3 + DIM], xg[d], fma(L[o0 + 4 + DIM], xp[d], cu * nv[d])));
+    }
+  } else {
+    // x0 = s_phi-hat, x1 = s_u-hat, xp = f_phi-hat, xg = f_u-hat
+    double s0 = L[0] * x0, s1 = L[1] * x0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) o.fphi[d] = fma(L[2 + d], x0, Hx[d]);
+    if (MODEL == 0) {
+      s0 = fma(-0.5 * P.idt, x1, s0);
+      s1 = fma(P.idt, x1, s1);
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) o.fu[d] = P.D * xg[d];
+    } else {
+      constexpr int o0 = NLin<DIM, 1>::PHI;
+      const double* nv = L + o0 + 6 + DIM;
+      s0 = fma(L[o0], x1, s0);
+      s1 = fma(L[o0 + 1], x1, s1);
+      double nfu = 0.0;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        s0 = fma(L[o0 + 2 + d], xg[d], s0);
+        nfu = fma(nv[d], xg[d], nfu);
+      }
+      s1 = fma(L[o0 + 2 + DIM] * nfu, 1.0, s1);
+      const double k2 = L[o0 + 5 + DIM] * nfu;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        o.fphi[d] = fma(L[o0 + 4 + DIM], xg[d], fma(-k2, nv[d], o.fphi[d]));
+        o.fu[d] = L[o0 + 3 + DIM] * xg[d];
+      }
+    }
+    o.sphi = s0;
+    o.su = s1;
+  }
+}
+
+}  // namespace tusas

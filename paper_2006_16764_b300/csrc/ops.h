@@ -1,0 +1,54 @@
+// Host-side launch interface of the tusas-b300 kernels (internal to the library).
+#pragma once
+#include <cuda_runtime.h>
+
+#include "common.cuh"
+#include "element.cuh"
+
+namespace tusas {
+
+enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5 };
+
+struct ElemCtx {
+  DevMesh m;
+  DevPhys P;
+  Scales S;
+  int ntx, nty, ntz;  // tiles per axis
+  int nlin;           // linearisation coefficients per Gauss point
+};
+
+void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P);
+// Doubles of the linearisation store for this mesh / model.
+size_t elem_lin_doubles(const ElemCtx& c);
+// Element-tile pass: out = (mode-dependent) assembled vector; out is zeroed
+// first, then the 2^dim tile colours accumulate in a fixed order.
+cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
+                     double* lin, cudaStream_t st);
+
+// ---- FP64 vector kernels (deterministic) ----------------------------------
+// y = a*x + y
+cudaError_t vaxpy(i64 n, double a, const double* x, double* y, cudaStream_t st);
+// z = x + a*y   (a read from device memory when ad != nullptr: z = x + (*ad)*y)
+cudaError_t vxpay(i64 n, const double* x, double a, const double* ad, const double* y, double* z, cudaStream_t st);
+// y = (y - x) * (*ainv)   (finite-difference quotient, ainv on device)
+cudaError_t vfdq(i64 n, const double* x, double* y, const double* ainv, cudaStream_t st);
+// y = x * (*s) (s on device, optionally inverted)
+cudaError_t vscale_dev(i64 n, const double* x, double* y, const double* s, int invert, cudaStream_t st);
+cudaError_t vcopy(i64 n, const double* x, double* y, cudaStream_t st);
+// y *= a
+cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st);
+cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st);
+
+// out[j] = sum_i X_j[i] * y[i] for j < k, X_j = X + j*ld; partials has
+// k * reduce_blocks() doubles. Deterministic (fixed partition and order).
+int reduce_blocks();
+cudaError_t multidot(i64 n, int k, const double* X, i64 ld, const double* y, double* partials, double* out,
+                     cudaStream_t st);
+// y -= sum_j c[j] X_j (c on device, k entries), optionally scaled: if accum_c
+// != nullptr, accum_c[j] += c[j] as well.
+cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* accum_c,
+                       cudaStream_t st);
+// x = sum_j c[j] X_j + x (c on host memory passed by value through a device array)
+cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st);
+
+}  // namespace tusas

@@ -1,0 +1,55 @@
+// Block-diagonal physics-based preconditioner (internal interface).
+#pragma once
+#include <vector>
+
+#include "ops.h"
+
+namespace tusas {
+
+struct PrecondLevel {
+  DevMesh m;
+  i64 nn;
+  void* st;    // stencils [2 blocks][3^dim offsets][nn], FP32 or FP64
+  void* dinv;  // [2][nn]
+  void* b;     // right-hand side [2][nn]
+  void* x;     // iterate
+  void* r;     // Jacobi-scaled Chebyshev residual
+  void* d;     // Chebyshev direction (double buffered with d2)
+  void* d2;
+  void* res;   // unscaled residual for the restriction
+  double lmax[2];
+};
+
+class Precond {
+ public:
+  int kind = 0;          // 0 identity, 1 point Jacobi, 2 block Jacobi + GMG
+  int fp32 = 1;          // operator / smoother precision
+  int cheb_degree = 2, coarse_degree = 10;
+  std::vector<PrecondLevel> lv;
+  double* gersh_partials = nullptr;  // [blocks][2]
+  double* lmax_dev = nullptr;        // [levels][2]
+  size_t bytes = 0;
+
+  // Allocate the hierarchy for the mesh (levels: coarsen by 2 while every
+  // element count is even and >= 2, at most `levels`).
+  cudaError_t create(const DevMesh& m, int kind, int fp32, int levels, int cheb_degree, int coarse_degree);
+  void destroy();
+  // Fill the fine stencils of M11 / M22 at the iterate U (Gauss-point
+  // coefficients of Eqs. pref2 / preconc2), the Galerkin coarse stencils,
+  // D^-1 and the Gershgorin bounds. Synchronises the stream once.
+  cudaError_t setup(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st);
+  // z = M^-1 r (FP64 in and out).
+  cudaError_t apply(const double* r, double* z, cudaStream_t st);
+
+ private:
+  template <typename T>
+  cudaError_t setup_t(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st);
+  template <typename T>
+  cudaError_t apply_t(const double* r, double* z, cudaStream_t st);
+  template <typename T>
+  cudaError_t vcycle(int l, cudaStream_t st);
+  template <typename T>
+  cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st);
+};
+
+}  // namespace tusas

@@ -1,0 +1,193 @@
+// FP64 vector kernels of the Krylov / Newton path (GMRES inner products run on
+// the GPU, Sec. 4.3). Reductions are deterministic: a fixed partition of the
+// index range into reduce_blocks() chunks, a fixed in-block tree, and a
+// second pass that sums the per-block partials in index order.
+#include "ops.h"
+
+namespace tusas {
+
+static const int VT = 256;  // threads per block of the vector kernels
+
+static int grid_for(i64 n) {
+  i64 g = (n + VT - 1) / VT;
+  const i64 cap = 148 * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return (int)g;
+}
+
+__global__ void k_axpy(i64 n, double a, const double* __restrict__ x, double* __restrict__ y) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    y[i] = fma(a, x[i], y[i]);
+}
+__global__ void k_xpay(i64 n, const double* __restrict__ x, double a, const double* __restrict__ ad,
+                       const double* __restrict__ y, double* __restrict__ z) {
+  const double s = ad ? *ad : a;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    z[i] = fma(s, y[i], x[i]);
+}
+__global__ void k_fdq(i64 n, const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ ainv) {
+  const double s = *ainv;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    y[i] = (y[i] - x[i]) * s;
+}
+__global__ void k_scale_dev(i64 n, const double* __restrict__ x, double* __restrict__ y, const double* __restrict__ s,
+                            int invert) {
+  const double f = invert ? 1.0 / *s : *s;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    y[i] = x[i] * f;
+}
+__global__ void k_scal(i64 n, double a, double* __restrict__ y) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) y[i] *= a;
+}
+__global__ void k_fill(i64 n, double v, double* __restrict__ y) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) y[i] = v;
+}
+
+cudaError_t vaxpy(i64 n, double a, const double* x, double* y, cudaStream_t st) {
+  k_axpy<<<grid_for(n), VT, 0, st>>>(n, a, x, y);
+  return cudaGetLastError();
+}
+cudaError_t vxpay(i64 n, const double* x, double a, const double* ad, const double* y, double* z, cudaStream_t st) {
+  k_xpay<<<grid_for(n), VT, 0, st>>>(n, x, a, ad, y, z);
+  return cudaGetLastError();
+}
+cudaError_t vfdq(i64 n, const double* x, double* y, const double* ainv, cudaStream_t st) {
+  k_fdq<<<grid_for(n), VT, 0, st>>>(n, x, y, ainv);
+  return cudaGetLastError();
+}
+cudaError_t vscale_dev(i64 n, const double* x, double* y, const double* s, int invert, cudaStream_t st) {
+  k_scale_dev<<<grid_for(n), VT, 0, st>>>(n, x, y, s, invert);
+  return cudaGetLastError();
+}
+cudaError_t vcopy(i64 n, const double* x, double* y, cudaStream_t st) {
+  return cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
+}
+cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st) {
+  k_scal<<<grid_for(n), VT, 0, st>>>(n, a, y);
+  return cudaGetLastError();
+}
+cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st) {
+  k_fill<<<grid_for(n), VT, 0, st>>>(n, v, y);
+  return cudaGetLastError();
+}
+
+// ---- deterministic multi-dot ------------------------------------------------
+static const int RB = 296;  // reduction blocks: 2 per SM
+int reduce_blocks() { return RB; }
+
+template <int KM>
+__global__ void __launch_bounds__(VT) k_multidot(i64 n, int k, const double* __restrict__ X, i64 ld,
+                                                 const double* __restrict__ y, double* __restrict__ partials) {
+  __shared__ double red[VT / 32][KM];
+  double acc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+  const i64 chunk = (n + gridDim.x - 1) / gridDim.x;
+  const i64 lo = blockIdx.x * chunk;
+  const i64 hi = lo + chunk < n ? lo + chunk : n;
+  for (i64 i = lo + threadIdx.x; i < hi; i += VT) {
+    const double yi = y[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) acc[j] = fma(X[j * ld + i], yi, acc[j]);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    if (j < k) {
+      double v = acc[j];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][j] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < VT / 32; ++w) s += red[w][threadIdx.x];
+    partials[blockIdx.x * (i64)KM + threadIdx.x] = s;
+  }
+}
+
+__global__ void k_reduce_partials(int nb, int k, int km, const double* __restrict__ partials, double* __restrict__ out) {
+  const int j = threadIdx.x;
+  if (j >= k) return;
+  double s = 0.0;
+  for (int b = 0; b < nb; ++b) s += partials[b * (i64)km + j];
+  out[j] = s;
+}
+
+cudaError_t multidot(i64 n, int k, const double* X, i64 ld, const double* y, double* partials, double* out,
+                     cudaStream_t st) {
+  if (k <= 0 || k > 32) return cudaErrorInvalidValue;
+  int km;
+  if (k == 1) {
+    km = 1;
+    k_multidot<1><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+  } else if (k <= 4) {
+    km = 4;
+    k_multidot<4><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+  } else if (k <= 8) {
+    km = 8;
+    k_multidot<8><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+  } else if (k <= 16) {
+    km = 16;
+    k_multidot<16><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+  } else {
+    km = 32;
+    k_multidot<32><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+  }
+  k_reduce_partials<<<1, 32, 0, st>>>(RB, k, km, partials, out);
+  return cudaGetLastError();
+}
+
+template <int KM>
+__global__ void __launch_bounds__(VT) k_multi_axpy(i64 n, int k, const double* __restrict__ X, i64 ld,
+                                                   const double* __restrict__ c, double sign, double* __restrict__ y) {
+  double cc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) cc[j] = j < k ? sign * c[j] : 0.0;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    double v = y[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) v = fma(cc[j], X[j * ld + i], v);
+    y[i] = v;
+  }
+}
+
+__global__ void k_add_small(int k, const double* __restrict__ c, double* __restrict__ acc) {
+  if (threadIdx.x < k) acc[threadIdx.x] += c[threadIdx.x];
+}
+
+static cudaError_t multi_axpy_sign(i64 n, int k, const double* X, i64 ld, const double* c, double sign, double* y,
+                                   cudaStream_t st) {
+  if (k <= 0) return cudaSuccess;
+  if (k > 32) return cudaErrorInvalidValue;
+  const int g = grid_for(n);
+  if (k <= 4)
+    k_multi_axpy<4><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+  else if (k <= 8)
+    k_multi_axpy<8><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+  else if (k <= 16)
+    k_multi_axpy<16><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+  else
+    k_multi_axpy<32><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+  return cudaGetLastError();
+}
+
+cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* accum_c,
+                       cudaStream_t st) {
+  cudaError_t e = multi_axpy_sign(n, k, X, ld, c, -1.0, y, st);
+  if (e != cudaSuccess || accum_c == nullptr) return e;
+  k_add_small<<<1, 32, 0, st>>>(k, c, accum_c);
+  return cudaGetLastError();
+}
+
+cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st) {
+  return multi_axpy_sign(n, k, X, ld, c, 1.0, x, st);
+}
+
+}  // namespace tusas

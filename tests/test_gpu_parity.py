@@ -1,0 +1,202 @@
+"""GPU kernels (through the C-ABI) against the CPU oracle on the same seeded inputs.
+
+Tolerances: residual, tangent, adjoint and dF/d eps4 normwise 1e-12 relative
+(FP64 kernels with a different summation order than the oracle); converged
+time steps 1e-8 relative to the solution (Newton tolerance 1e-10 relative on
+||F||, oracle solved to 1e-13 with a direct solver).
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import synth
+from synth import Mesh, Params
+from oracle import jacobian as OJ
+from oracle import precond as OP
+from oracle import residual as OR
+from oracle import solver as OS
+from tests.gpu_util import dev, handle, host, rel
+
+pytestmark = pytest.mark.gpu
+
+PURE = Params(model=0, eps4=0.05, lam=3.19, D=2.0, precond=1)
+ALLOY = Params(model=1, k=0.15, eps4=0.02, lam=3.1913, D=2.0, lT=60.0, Vp=0.12, zT=-5.0, precond=1)
+
+CASES = [
+    ("2d-pure-ragged", Mesh(2, 37, 19, 0, 0.9, -3.0, 1.0), PURE),
+    ("2d-alloy-ragged", Mesh(2, 35, 17, 0, 0.8), ALLOY),
+    ("2d-alloy-jat0", Mesh(2, 33, 9, 0, 0.8), dataclasses.replace(ALLOY, jat_normalised=0)),
+    ("2d-pure-literal-time", Mesh(2, 18, 18, 0, 1.1), dataclasses.replace(PURE, time_form=1)),
+    ("3d-pure-ragged", Mesh(3, 19, 9, 6, 0.8, -1.0, 2.0, 0.5), PURE),
+    ("3d-alloy-ragged", Mesh(3, 17, 10, 9, 0.8), ALLOY),
+    ("3d-alloy-literal-jat0", Mesh(3, 9, 5, 5, 0.7), dataclasses.replace(ALLOY, time_form=1, jat_normalised=0)),
+    ("2d-1x1", Mesh(2, 1, 1, 0, 0.5), ALLOY),
+    ("2d-2x3", Mesh(2, 2, 3, 0, 0.5), PURE),
+    ("3d-1x1x1", Mesh(3, 1, 1, 1, 0.5), ALLOY),
+    ("3d-3x2x5", Mesh(3, 3, 2, 5, 0.6), PURE),
+]
+IDS = [c[0] for c in CASES]
+
+
+def _inputs(mesh, seed=42):
+    U, Un = synth.random_fields(mesh, seed)
+    return U, Un
+
+
+@pytest.mark.parametrize("name,mesh,prm", CASES, ids=IDS)
+def test_residual_matches_oracle(name, mesh, prm):
+    U, Un = _inputs(mesh)
+    dt, tn = 0.37, 1.25
+    h = handle(mesh, prm)
+    h.set_state(dev(Un), tn, dt)
+    tU = dev(U)
+    F = dev(np.zeros_like(U))
+    h.residual(tU, F)
+    want = OR.residual(mesh, prm, U, Un, tn, dt)
+    assert rel(host(F), want) <= 1e-12
+
+
+@pytest.mark.parametrize("name,mesh,prm", CASES, ids=IDS)
+def test_tangent_adjoint_and_parameter_derivative(name, mesh, prm):
+    U, Un = _inputs(mesh, 7)
+    v = synth.random_vector(mesh, 8)
+    w = synth.random_vector(mesh, 9)
+    dt, tn = 0.41, 0.5
+    h = handle(mesh, prm)
+    h.set_state(dev(Un), tn, dt)
+    tU, tv, tw = dev(U), dev(v), dev(w)
+    out = dev(np.zeros_like(U))
+    h.jvp(tU, tv, out)
+    assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v)) <= 1e-12
+    h.jtvp(tU, tw, out)
+    assert rel(host(out), OJ.jtvp(mesh, prm, U, Un, tn, dt, w)) <= 1e-12
+    h.jtvp_prev(tU, tw, out)
+    assert rel(host(out), OJ.dF_dUn_T(mesh, prm, U, Un, tn, dt, w)) <= 1e-12
+    h.dFdp(tU, out, 0)
+    want = OJ.dF_deps4(mesh, prm, U, Un, tn, dt)
+    assert rel(host(out), want) <= 1e-12
+    # finite-difference action (Eq. JFmatvec) approximates the exact one
+    h.jvp_fd(tU, tv, out)
+    assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v)) <= 1e-5
+
+
+def test_residual_is_bitwise_deterministic():
+    mesh = Mesh(3, 21, 13, 9, 0.8)
+    U, Un = _inputs(mesh, 3)
+    h = handle(mesh, ALLOY)
+    h.set_state(dev(Un), 0.0, 0.2)
+    tU = dev(U)
+    ref = host(h.residual(tU, dev(np.zeros_like(U)))).copy()
+    F = dev(np.zeros_like(U))
+    for _ in range(10):
+        h.residual(tU, F)
+        assert np.array_equal(host(F), ref)
+    assert h.dot(tU, tU) == h.dot(tU, tU)
+    assert abs(h.dot(tU, tU) - float(U @ U)) <= 1e-12 * float(U @ U)
+
+
+def _precond_case(dim, fp32, kind=2):
+    if dim == 2:
+        w = synth.scaled(synth.workload("dendrite2d_1024"), 32, 32)
+    else:
+        w = synth.scaled(synth.workload("alloy3d_256x256x128"), 16, 16, 32)
+    prm = dataclasses.replace(w.params, precond=kind, smoother_fp32=fp32)
+    U0 = synth.initial_state(w)
+    U = U0 + 0.01 * synth.random_vector(w.mesh, 3)
+    return w, prm, U, U0
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("kind,fp32,tol", [(1, 0, 1e-13), (2, 0, 1e-10), (2, 1, 2e-4)])
+def test_preconditioner_matches_oracle(dim, kind, fp32, tol):
+    """Jacobi and the GMG V-cycle per block: FP64 operators to roundoff, FP32 to a few
+    single-precision ulps amplified by the V-cycle (bound 2e-4 normwise)."""
+    w, prm, U, U0 = _precond_case(dim, fp32, kind)
+    h = handle(w.mesh, prm)
+    h.set_state(dev(U0), 0.0, w.dt)
+    h.precond_setup(dev(U))
+    r = synth.random_vector(w.mesh, 11)
+    z = dev(np.zeros_like(r))
+    h.precond_apply(dev(r), z)
+    want = OP.Preconditioner(w.mesh, prm, U, U0, w.dt).apply(r)
+    assert rel(host(z), want) <= tol
+
+
+STEP_CASES = [
+    ("dendrite2d_128", (32, 32), dict(precond=1, jvp_mode=0, smoother_fp32=0), 2),
+    ("dendrite2d_1024", (32, 32), dict(precond=2, jvp_mode=1, smoother_fp32=1), 2),
+    ("dendrite3d_192", (12, 12, 12), dict(precond=2, jvp_mode=0, smoother_fp32=0), 1),
+    ("alloy3d_256x256x128", (8, 8, 24), dict(precond=2, jvp_mode=1, smoother_fp32=1), 2),
+    ("alloy3d_256x256x128", (8, 8, 24), dict(precond=2, jvp_mode=0, smoother_fp32=0), 1),
+]
+
+
+@pytest.mark.parametrize("name,dims,opts,nsteps", STEP_CASES,
+                         ids=[f"{c[0]}-{'x'.join(map(str, c[1]))}-pc{c[2]['precond']}-jv{c[2]['jvp_mode']}-fp32{c[2]['smoother_fp32']}" for c in STEP_CASES])
+def test_converged_steps_match_oracle(name, dims, opts, nsteps):
+    w = synth.scaled(synth.workload(name), *dims)
+    prm = dataclasses.replace(w.params, **opts)
+    U0 = synth.initial_state(w)
+    h = handle(w.mesh, prm)
+    h.set_state(dev(U0), 0.0, w.dt)
+    Uo = U0.copy()
+    t = 0.0
+    out = dev(np.zeros_like(U0))
+    for _ in range(nsteps):
+        st = h.step()
+        assert st["converged"] and st["fnorm"] < prm.newton_rtol * st["fnorm0"], st
+        Uo, ratio = OS.newton_direct(w.mesh, prm, Uo, t, w.dt)
+        assert ratio < 1e-12
+        t += w.dt
+        assert rel(host(h.get_state(out)), Uo) <= 1e-8
+    assert abs(h.time - t) < 1e-12
+
+
+@pytest.mark.parametrize("name", ["alloy3d_256x256x128", "dendrite3d_192", "dendrite2d_1024"])
+def test_full_size_residual_on_sampled_nodes(name):
+    """At the full workload size the oracle evaluates sampled nodes one by one (Sec. 4.3 sizes)."""
+    w = synth.workload(name)
+    U0 = synth.initial_state(w)
+    pert = 0.05 * synth.uniform_pm1(77, w.mesh.n_dofs)
+    U = U0 + pert
+    h = handle(w.mesh, dataclasses.replace(w.params, precond=0))
+    h.set_state(dev(U0), 1.0, w.dt)
+    F = host(h.residual(dev(U), dev(np.zeros_like(U))))
+    n = w.mesh.n_nodes
+    rng_nodes = (synth.splitmix64(5, 48) % np.uint64(n)).astype(np.int64)
+    nodes = np.unique(np.concatenate([rng_nodes, [0, n - 1, w.mesh.nx, n // 2]]))
+    rp, ru = OR.residual_at_nodes(w.mesh, w.params, U, U0, 1.0, w.dt, nodes)
+    scale = max(np.abs(rp).max(), np.abs(ru).max())
+    assert np.abs(F[nodes] - rp).max() <= 1e-12 * scale
+    assert np.abs(F[n + nodes] - ru).max() <= 1e-12 * scale
+
+
+def test_error_codes():
+    import paper_2006_16764_b300 as pkg
+
+    mesh = Mesh(2, 8, 8, 0, 1.0)
+    h = handle(mesh, PURE)
+    U = dev(np.zeros(mesh.n_dofs))
+    with pytest.raises(pkg.TusasError) as e:
+        h.residual(U, dev(np.zeros(mesh.n_dofs)))
+    assert e.value.code == pkg.EINVAL
+    with pytest.raises(pkg.TusasError) as e:
+        h.set_state(U, 0.0, -1.0)
+    assert e.value.code == pkg.EINVAL
+    with pytest.raises(pkg.TusasError) as e:
+        pkg.Tusas(mesh, dataclasses.replace(PURE, k=0.5))
+    assert e.value.code == pkg.EINVAL
+    bad = synth.seed_state(mesh, PURE, 3.0)
+    bad[5] = np.nan
+    h.set_state(dev(bad), 0.0, 0.5)
+    with pytest.raises(pkg.TusasError) as e:
+        h.step()
+    assert e.value.code == pkg.ENONFINITE
+    h2 = handle(mesh, dataclasses.replace(PURE, newton_maxit=1))
+    h2.set_state(dev(synth.seed_state(mesh, PURE, 3.0)), 0.0, 0.5)
+    st = h2.step(allow_noconv=True)
+    assert not st["converged"]
+    with pytest.raises(pkg.TusasError) as e:
+        h2.step()
+    assert e.value.code == pkg.ENOCONV
