@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Benchmark of the B300 hot path: backward-Euler Newton-Krylov steps of the
+3D dilute-alloy phase-field problem (256x256x128 Q1 hexes, 17,040,642 dofs).
+
+One bench step = one implicit time step through the whole hot path: residual
+F(U), pointwise linearisation, exact tangent J v, FP32 block-Jacobi / GMG
+preconditioner fill and apply, FGMRES(30) with CGS2, Newton update and line
+search. The metric counts residual-type operator evaluations (F and J v, each
+over all 17.04M dofs) per second of whole-job device time; the same line
+reports the FD-J v + FP64-preconditioner path for comparison (s/step), the
+isolated kernel roofline, the end-to-end number through the C-ABI with host
+buffers, and the CPU oracle on a bounded sample.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+METRIC = "3D residual Mdof-evals/s (%HBM roofline); JFNK s/step exact-JVP+FP32 vs FD-FP64"
+UNIT = "Mdof-evals/s"
+WORKLOAD = "alloy3d_256x256x128"
+# Oracle sample for the CPU baseline: the same physics, spacing, time step and
+# initial front on a 48x48x32 sub-box (about 150k dofs per evaluation).
+CPU_SAMPLE = (48, 48, 32)
+
+# FP64 floating-point operations per element of one element-tile pass, counted
+# from the compiled kernels (DADD + DMUL + 2 DFMA per element, ncu
+# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum / elements of
+# the 3D alloy kernels). Algorithmic bytes per element: nodal reads/writes
+# (8 B per field value, one node per element) plus the stored linearisation
+# (23 coefficients x 8 Gauss points x 8 B).
+FP64_FLOPS_PER_ELEM = {"residual": 1272.0, "residual_lin": 1770.0, "jv": 1024.0}
+BYTES_PER_ELEM = {"residual": 48.0, "residual_lin": 48.0 + 1472.0, "jv": 32.0 + 1472.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--fd-steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--kernels", action="store_true",
+                    help="profiling case: a few residual / linearisation / tangent passes on a 256x192x64 "
+                         "sub-box of the alloy workload (inputs > L2, about 5 GB on the device)")
+    return ap.parse_args()
+
+
+def run_kernels():
+    """Small case for detailed counters: 2 residuals, 2 linearisations, 2 tangent actions."""
+    import dataclasses
+
+    import torch
+
+    import paper_2006_16764_b300 as pkg
+
+    w = synth.scaled(synth.workload(WORKLOAD), 256, 192, 64)
+    prm = dataclasses.replace(w.params, gmres_restart=2, precond=0)
+    dev = torch.device("cuda", 0)
+    U0 = torch.tensor(synth.initial_state(w), device=dev)
+    U = U0 + 0.01 * torch.tensor(synth.uniform_pm1(3, w.mesh.n_dofs), device=dev)
+    v = torch.tensor(synth.uniform_pm1(4, w.mesh.n_dofs), device=dev)
+    h = pkg.Tusas(w.mesh, prm)
+    h.set_state(U0, 0.0, w.dt)
+    F = torch.empty_like(U)
+    for _ in range(2):
+        h.residual(U, F)
+    for _ in range(2):
+        h.jvp(U, v, F)
+    torch.cuda.synchronize()
+    print(json.dumps({"kernels": "ok", "dofs": w.mesh.n_dofs, "elems": w.mesh.n_elems}))
+    h.close()
+
+
+# ----------------------------------------------------------------------------
+def cpu_oracle_rate(seconds, warm=0):
+    """Oracle residual evaluations on the bounded sample; Mdof-evals/s on 1 host core."""
+    from oracle import residual as OR
+
+    w = synth.scaled(synth.workload(WORKLOAD), *CPU_SAMPLE)
+    U0 = synth.initial_state(w)
+    U = U0 + 0.01 * synth.uniform_pm1(5, w.mesh.n_dofs)
+    for _ in range(warm):
+        OR.residual(w.mesh, w.params, U, U0, 0.0, w.dt)
+    n = 0
+    t0 = time.perf_counter()
+    while True:
+        OR.residual(w.mesh, w.params, U, U0, 0.0, w.dt)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return w.mesh.n_dofs * n / el / 1e6, n, el, w
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows if len(r) >= 9 for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        import torch
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def allreduce_max(ws, x, dev):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(ws, x, dev):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+def run_reference(args, ws, rank):
+    """The CPU oracle as it stands, on rank 0 only: residual evaluations on the bounded sample."""
+    if rank != 0:
+        return
+    per = []
+    w = None
+    for i in range(args.warmup + args.steps):
+        rate, n, el, w = cpu_oracle_rate(0.0)
+        if i >= args.warmup:
+            per.append((n, el))
+    units = sum(n for n, _ in per) * w.mesh.n_dofs
+    secs = sum(el for _, el in per)
+    value = units / secs / 1e6
+    sample = f"oracle residual on {CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-box of {WORKLOAD} ({w.mesh.n_dofs} dofs), one evaluation per step"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample": list(CPU_SAMPLE)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import torch
+
+    import paper_2006_16764_b300 as pkg
+
+    assert torch.cuda.is_available(), "bench needs a CUDA device"
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    w = synth.workload(args.workload)
+    prm = w.params
+    mesh = w.mesh
+    N = mesh.n_dofs
+    U0 = torch.tensor(synth.initial_state(w), device=dev)
+    stream = torch.cuda.current_stream(dev)
+    fp64_peak, fp32_peak = pkg.fma_peak()
+    h = pkg.Tusas(mesh, prm, stream=stream)
+    h.set_state(U0, 0.0, w.dt)
+    for _ in range(args.warmup):
+        h.step()
+    Ustart = torch.empty_like(U0)
+    h.get_state(Ustart)
+    t_start = h.time
+    h.timers(True)
+    l0 = pkg.kernel_launches()
+    clocks = ClockSampler(local)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.append(h.step())
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clk = clocks.stop()
+    launches = pkg.kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    ms_max = allreduce_max(ws, ms, dev)
+    timers = h.get_timers()
+    evals = sum(s["residual_evals"] + s["jv_evals"] for s in stats)
+    units = allreduce_sum(ws, float(evals) * N, dev)
+    value = units / (ms_max * 1e-3) / 1e6
+
+    # dominant kernel class and its roofline (per operator application = one launch set)
+    dom = max(("residual", "residual_lin", "jv"), key=lambda k: timers[k][0])
+    d_ms, d_cnt = timers[dom]
+    per_launch = d_ms / max(d_cnt, 1)
+    ne = mesh.n_elems
+    flops = FP64_FLOPS_PER_ELEM[dom] * ne
+    achieved = flops / (per_launch * 1e-3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved * 1e12 / fp64_peak, "traffic": None, "kernel": f"elem_kernel {dom} (3D alloy)",
+            "launch_ms": per_launch, "launches": d_cnt,
+            "peak_kind": "fp64 FMA-chain throughput measured in this run (tusas_fma_peak)",
+            "hbm": {"achieved_gbs": BYTES_PER_ELEM[dom] * ne / (per_launch * 1e-3) / 1e9,
+                    "peak_gbs": 6489.6, "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
+    roof["hbm"]["frac"] = roof["hbm"]["achieved_gbs"] / roof["hbm"]["peak_gbs"]
+
+    # isolated residual kernel (CUDA events on the same stream)
+    F = torch.empty_like(U0)
+    Ut = torch.empty_like(U0)
+    h.get_state(Ut)
+    for _ in range(2):
+        h.residual(Ut, F)
+    r0 = torch.cuda.Event(enable_timing=True)
+    r1 = torch.cuda.Event(enable_timing=True)
+    r0.record(stream)
+    nres = 5
+    for _ in range(nres):
+        h.residual(Ut, F)
+    r1.record(stream)
+    torch.cuda.synchronize(dev)
+    res_ms = r0.elapsed_time(r1) / nres
+    residual_kernel = {"ms": res_ms, "Mdof_evals_per_s": N / (res_ms * 1e-3) / 1e6,
+                       "fp64_tflops": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_ms * 1e-3) / 1e12,
+                       "hbm_gbs": BYTES_PER_ELEM["residual"] * ne / (res_ms * 1e-3) / 1e9}
+    del F
+
+    # FD-FP64 comparison path from the same starting state
+    jfnk = {"exact_fp32": {"s_per_step": ms / args.steps / 1e3,
+                           "newton_its": [s["newton_its"] for s in stats],
+                           "gmres_its": [s["gmres_its"] for s in stats],
+                           "kappa": 2 * w.dt * (prm.D / (1 + prm.k)) / mesh.h ** 2}}
+    if args.fd_steps > 0:
+        import dataclasses
+
+        pfd = dataclasses.replace(prm, jvp_mode=0, smoother_fp32=0)
+        hf = pkg.Tusas(mesh, pfd, stream=stream)
+        hf.set_state(Ustart, t_start, w.dt)
+        hf.timers(True)
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize(dev)
+        f0.record(stream)
+        fst = [hf.step() for _ in range(args.fd_steps)]
+        f1.record(stream)
+        torch.cuda.synchronize(dev)
+        fms = f0.elapsed_time(f1)
+        jfnk["fd_fp64"] = {"s_per_step": fms / args.fd_steps / 1e3,
+                           "newton_its": [s["newton_its"] for s in fst],
+                           "gmres_its": [s["gmres_its"] for s in fst],
+                           "timers_ms": {k: round(v[0], 3) for k, v in hf.get_timers().items()}}
+        # the exact path over the same first fd_steps steps
+        ex = stats[: args.fd_steps]
+        jfnk["speedup_exact_fp32_over_fd_fp64"] = jfnk["fd_fp64"]["s_per_step"] / jfnk["exact_fp32"]["s_per_step"]
+        hf.close()
+
+    # end to end through the C-ABI with pinned host buffers (H2D state in, D2H state out per step)
+    e2e = None
+    if args.e2e_steps > 0:
+        Uh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        Uh.copy_(Ustart.cpu())
+        torch.cuda.synchronize(dev)
+        tt = t_start
+        ev = 0
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            h.set_state(Uh, tt, w.dt)
+            s = h.step()
+            h.get_state(Uh)
+            tt += w.dt
+            ev += s["residual_evals"] + s["jv_evals"]
+        el = time.perf_counter() - t0
+        e2e = {"value": ev * N / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
+               "steps": args.e2e_steps}
+
+    line = None
+    if rank == 0:
+        cpu_rate, n, el, wsub = cpu_oracle_rate(args.cpu_seconds, warm=1)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "mesh": f"{mesh.nx}x{mesh.ny}x{mesh.nz} Q1 hex, h={mesh.h}",
+                       "dofs": N, "dt": w.dt, "jvp": "exact (stored pointwise linearisation)",
+                       "precond": "block Jacobi, GMG V-cycle, Chebyshev(2), FP32",
+                       "newton_rtol": prm.newton_rtol, "gmres_restart": prm.gmres_restart,
+                       "l2": "inputs larger than L2 (state 136 MB per vector, linearisation 12.3 GB)",
+                       "parallelism": f"{ws} independent replica(s)"},
+            "roofline": roof,
+            "cpu_baseline": {"value": cpu_rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"numpy oracle residual, {n} evaluations in {el:.1f} s on the "
+                                       f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-box ({wsub.mesh.n_dofs} dofs)"},
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk,
+            "jfnk": jfnk,
+            "residual_kernel": residual_kernel,
+            "timers_ms": {k: [round(v[0], 3), v[1]] for k, v in timers.items()},
+            "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12,
+        }
+        print(json.dumps(line), flush=True)
+    h.close()
+
+
+def main():
+    args = parse()
+    if args.kernels:
+        run_kernels()
+        return
+    ws, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -153,6 +153,31 @@ int tusas_step(tusas_handle* h, tusas_stats* stats);
  * result is written to *result (host pointer). Synchronises. */
 int tusas_dot(tusas_handle* h, const double* x, const double* y, long long n, double* result);
 
+/* ---- Instrumentation (no counterpart in the paper) ------------------------
+ * Device time per kernel class, measured with CUDA events recorded on the
+ * handle's stream around each operator application inside the library. */
+enum {
+  TUSAS_T_RESIDUAL = 0,      /* F(U) element-tile pass                         */
+  TUSAS_T_RESIDUAL_LIN = 1,  /* F(U) + pointwise linearisation store           */
+  TUSAS_T_JV = 2,            /* Jacobian action (stored tangent or FD sequence)*/
+  TUSAS_T_ADJOINT = 3,       /* J^T w, (dF/dU^n)^T w, dF/d eps4                */
+  TUSAS_T_PC_APPLY = 4,      /* preconditioner application                     */
+  TUSAS_T_PC_SETUP = 5,      /* stencil fill, Galerkin coarsening, bounds      */
+  TUSAS_T_ORTHO = 6,         /* GMRES classical Gram-Schmidt (twice) + norm    */
+  TUSAS_NTIMERS = 7
+};
+/* Enable (1) or disable (0) the timers; either resets them. */
+int tusas_timers(tusas_handle* h, int enable);
+/* Accumulated milliseconds and counts per class (host arrays of
+ * TUSAS_NTIMERS entries). Synchronises the stream. */
+int tusas_get_timers(tusas_handle* h, double* ms, long long* counts);
+/* Number of CUDA kernels this library has launched in this process. */
+long long tusas_kernel_launches(void);
+/* Throughput of dependent FMA chains on the current device (all SMs, 8
+ * independent chains per thread): FP64 and FP32 FLOP/s (an FMA counts 2).
+ * Allocates and frees a small device buffer. Synchronises the device. */
+int tusas_fma_peak(double* fp64_flops, double* fp32_flops);
+
 /* Description of the last error on this handle (never NULL). */
 const char* tusas_last_error(const tusas_handle* h);
 

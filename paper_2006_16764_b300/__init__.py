@@ -21,7 +21,10 @@ ERROR_NAMES = {EINVAL: "TUSAS_EINVAL", ECUDA: "TUSAS_ECUDA", ENOMEM: "TUSAS_ENOM
 EXPORTS = ["tusas_create", "tusas_destroy", "tusas_set_stream", "tusas_set_params", "tusas_ndofs",
            "tusas_set_state", "tusas_get_state", "tusas_time", "tusas_residual", "tusas_jvp",
            "tusas_jvp_fd", "tusas_jtvp", "tusas_jtvp_prev", "tusas_dFdp", "tusas_precond_setup",
-           "tusas_precond_apply", "tusas_step", "tusas_dot", "tusas_last_error"]
+           "tusas_precond_apply", "tusas_step", "tusas_dot", "tusas_last_error", "tusas_timers",
+           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak"]
+
+TIMER_NAMES = ["residual", "residual_lin", "jv", "adjoint", "pc_apply", "pc_setup", "ortho"]
 
 
 class CMesh(ctypes.Structure):
@@ -87,6 +90,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tusas_step": ([vp, ctypes.POINTER(CStats)], ctypes.c_int),
         "tusas_dot": ([vp, dp, dp, i64, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
         "tusas_last_error": ([vp], ctypes.c_char_p),
+        "tusas_timers": ([vp, ctypes.c_int], ctypes.c_int),
+        "tusas_get_timers": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
+        "tusas_kernel_launches": ([], i64),
+        "tusas_fma_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -103,6 +110,20 @@ def lib() -> ctypes.CDLL:
     if _LIB is None:
         _LIB = load_library()
     return _LIB
+
+
+def kernel_launches() -> int:
+    """Kernels launched by the library in this process."""
+    return int(lib().tusas_kernel_launches())
+
+
+def fma_peak():
+    """(FP64, FP32) FLOP/s of dependent FMA chains on the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    rc = lib().tusas_fma_peak(ctypes.byref(a), ctypes.byref(b))
+    if rc != OK:
+        raise TusasError(rc, "tusas_fma_peak failed")
+    return a.value, b.value
 
 
 class TusasError(RuntimeError):
@@ -229,6 +250,16 @@ class Tusas:
             return st.as_dict()
         self._check(rc)
         return st.as_dict()
+
+    def timers(self, enable=True):
+        self._check(self._lib.tusas_timers(self._h, int(enable)))
+
+    def get_timers(self):
+        """{class: (milliseconds, count)} of the enabled timers."""
+        ms = (ctypes.c_double * len(TIMER_NAMES))()
+        cnt = (ctypes.c_longlong * len(TIMER_NAMES))()
+        self._check(self._lib.tusas_get_timers(self._h, ms, cnt))
+        return {n: (ms[i], int(cnt[i])) for i, n in enumerate(TIMER_NAMES)}
 
     def dot(self, x, y, n=None):
         r = ctypes.c_double()

@@ -36,6 +36,13 @@ struct tusas_handle {
   tusas::Precond pc;
   bool pc_ready = false;
   std::string err;
+  // instrumentation: CUDA-event pairs per kernel class
+  bool timers_on = false;
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> marks;
+  double t_ms[TUSAS_NTIMERS] = {};
+  long long t_cnt[TUSAS_NTIMERS] = {};
 };
 
 namespace {
@@ -52,6 +59,37 @@ int fail(tusas_handle* h, int code, const std::string& msg) {
     if (e_ != cudaSuccess)                                                                         \
       return fail(h, TUSAS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));             \
   } while (0)
+
+// Start / stop a timed region of class `cls` on the handle's stream.
+size_t tbeg(tusas_handle* h) {
+  if (!h->timers_on) return (size_t)-1;
+  while (h->ev.size() < h->ev_used + 2) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+    h->ev.push_back(e);
+  }
+  const size_t i = h->ev_used;
+  h->ev_used += 2;
+  cudaEventRecord(h->ev[i], h->st);
+  return i;
+}
+void tend(tusas_handle* h, int cls, size_t i) {
+  if (i == (size_t)-1) return;
+  cudaEventRecord(h->ev[i + 1], h->st);
+  h->marks.push_back(std::make_pair(cls, i));
+}
+// Fold recorded event pairs into the per-class sums (stream must be idle).
+void tcollect(tusas_handle* h) {
+  for (auto& mk : h->marks) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[mk.second], h->ev[mk.second + 1]) == cudaSuccess) {
+      h->t_ms[mk.first] += ms;
+      h->t_cnt[mk.first] += 1;
+    }
+  }
+  h->marks.clear();
+  h->ev_used = 0;
+}
 
 int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
   if (!m || !p) {
@@ -179,6 +217,7 @@ __global__ void k_fd_eps(const double* unorm2, const double* vnorm2, double* eps
 int fd_jv(tusas_handle* h, const double* U, const double* F0, const double* v, double* Jv) {
   TCK(norm2_dev(h, v, 211));
   k_fd_eps<<<1, 1, 0, h->st>>>(h->sc + 210, h->sc + 211, h->sc + 212);
+  tusas::count_launches(1);
   TCK(tusas::vxpay(h->N, U, 0.0, h->sc + 212, v, h->tmp2, h->st));
   TCK(tusas::elem_run(tusas::M_RES, h->ec, h->tmp2, h->Un, nullptr, Jv, nullptr, h->st));
   TCK(tusas::vfdq(h->N, F0, Jv, h->sc + 213, h->st));
@@ -252,6 +291,7 @@ void tusas_destroy(tusas_handle* h) {
                     h->partials, h->sc};
   for (double* v : vecs)
     if (v) cudaFree(v);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   h->pc.destroy();
   delete h;
 }
@@ -307,7 +347,9 @@ int tusas_residual(tusas_handle* h, const double* U, double* F) {
   int rc = ready(h);
   if (rc) return rc;
   if (!U || !F || U == F) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, F, nullptr, h->st));
+  tend(h, TUSAS_T_RESIDUAL, t0);
   return TUSAS_OK;
 }
 
@@ -317,8 +359,12 @@ int tusas_jvp(tusas_handle* h, const double* U, const double* v, double* Jv) {
   if (!U || !v || !Jv || Jv == U || Jv == v) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   rc = ensure_lin(h, false);
   if (rc) return rc;
+  size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st));
+  tend(h, TUSAS_T_RESIDUAL_LIN, t0);
+  t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_JV, h->ec, nullptr, nullptr, v, Jv, h->lin, h->st));
+  tend(h, TUSAS_T_JV, t0);
   return TUSAS_OK;
 }
 
@@ -337,8 +383,12 @@ int tusas_jtvp(tusas_handle* h, const double* U, const double* w, double* JTw) {
   if (!U || !w || !JTw || JTw == U || JTw == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   rc = ensure_lin(h, false);
   if (rc) return rc;
+  size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st));
+  tend(h, TUSAS_T_RESIDUAL_LIN, t0);
+  t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_JTV, h->ec, nullptr, nullptr, w, JTw, h->lin, h->st));
+  tend(h, TUSAS_T_ADJOINT, t0);
   return TUSAS_OK;
 }
 
@@ -346,7 +396,9 @@ int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* o
   int rc = ready(h);
   if (rc) return rc;
   if (!U || !w || !out || out == U || out == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_PREV_T, h->ec, U, h->Un, w, out, nullptr, h->st));
+  tend(h, TUSAS_T_ADJOINT, t0);
   return TUSAS_OK;
 }
 
@@ -355,7 +407,9 @@ int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF) {
   if (rc) return rc;
   if (!U || !dF || U == dF) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   if (which != 0) return fail(h, TUSAS_EINVAL, "only which = 0 (eps4) is available");
+  const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_DEPS, h->ec, U, h->Un, nullptr, dF, nullptr, h->st));
+  tend(h, TUSAS_T_ADJOINT, t0);
   return TUSAS_OK;
 }
 
@@ -363,7 +417,9 @@ int tusas_precond_setup(tusas_handle* h, const double* U) {
   int rc = ready(h);
   if (rc) return rc;
   if (!U) return fail(h, TUSAS_EINVAL, "null vector");
+  const size_t t0 = tbeg(h);
   TCK(h->pc.setup(h->ec, h->prm.theta, U, h->Un, h->st));
+  tend(h, TUSAS_T_PC_SETUP, t0);
   h->pc_ready = true;
   return TUSAS_OK;
 }
@@ -375,7 +431,9 @@ int tusas_precond_apply(tusas_handle* h, const double* r, double* z) {
     return TUSAS_OK;
   }
   if (!h->pc_ready) return fail(h, TUSAS_EINVAL, "call tusas_precond_setup first");
+  const size_t t0 = tbeg(h);
   TCK(h->pc.apply(r, z, h->st));
+  tend(h, TUSAS_T_PC_APPLY, t0);
   return TUSAS_OK;
 }
 
@@ -391,6 +449,30 @@ int tusas_dot(tusas_handle* h, const double* x, const double* y, long long n, do
   return TUSAS_OK;
 }
 
+int tusas_timers(tusas_handle* h, int enable) {
+  if (!h) return TUSAS_EINVAL;
+  TCK(cudaStreamSynchronize(h->st));
+  h->marks.clear();
+  h->ev_used = 0;
+  for (int i = 0; i < TUSAS_NTIMERS; ++i) {
+    h->t_ms[i] = 0.0;
+    h->t_cnt[i] = 0;
+  }
+  h->timers_on = enable != 0;
+  return TUSAS_OK;
+}
+
+int tusas_get_timers(tusas_handle* h, double* ms, long long* counts) {
+  if (!h || !ms || !counts) return TUSAS_EINVAL;
+  TCK(cudaStreamSynchronize(h->st));
+  tcollect(h);
+  for (int i = 0; i < TUSAS_NTIMERS; ++i) {
+    ms[i] = h->t_ms[i];
+    counts[i] = h->t_cnt[i];
+  }
+  return TUSAS_OK;
+}
+
 const char* tusas_last_error(const tusas_handle* h) {
   if (!h) return "null handle";
   return h->err.empty() ? "no error" : h->err.c_str();
@@ -401,11 +483,15 @@ const char* tusas_last_error(const tusas_handle* h) {
 // ---------------------------------------------------------------------------
 
 static int jv_apply(tusas_handle* h, bool exact, const double* z, double* out) {
+  const size_t t0 = tbeg(h);
   if (exact) {
     TCK(tusas::elem_run(tusas::M_JV, h->ec, nullptr, nullptr, z, out, h->lin, h->st));
-    return TUSAS_OK;
+  } else {
+    int rc = fd_jv(h, h->U, h->F, z, out);
+    if (rc) return rc;
   }
-  return fd_jv(h, h->U, h->F, z, out);
+  tend(h, TUSAS_T_JV, t0);
+  return TUSAS_OK;
 }
 
 static int prec_apply(tusas_handle* h, const double* r, double* z) {
@@ -413,7 +499,9 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
     TCK(tusas::vcopy(h->N, r, z, h->st));
     return TUSAS_OK;
   }
+  const size_t t0 = tbeg(h);
   TCK(h->pc.apply(r, z, h->st));
+  tend(h, TUSAS_T_PC_APPLY, t0);
   return TUSAS_OK;
 }
 
@@ -451,11 +539,13 @@ static int gmres(tusas_handle* h, bool exact, const double* b, double* x, double
       if (stats) stats->jv_evals++;
       ++its;
       // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
+      const size_t to = tbeg(h);
       TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc, h->st));
       TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc, w, nullptr, h->st));
       TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc + 64, h->st));
       TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc + 64, w, h->sc, h->st));
       TCK(norm2_dev(h, w, 63));
+      tend(h, TUSAS_T_ORTHO, to);
       TCK(cudaMemcpyAsync(col.data(), h->sc, sizeof(double) * 64, cudaMemcpyDeviceToHost, h->st));
       TCK(cudaStreamSynchronize(h->st));
       const double hn = sqrt(col[63]);
@@ -520,7 +610,9 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     if (rc) return rc;
   }
   TCK(tusas::vcopy(N, h->Un, h->U, h->st));
+  size_t t0 = tbeg(h);
   TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->U, h->Un, nullptr, h->F, h->lin, h->st));
+  tend(h, exact ? TUSAS_T_RESIDUAL_LIN : TUSAS_T_RESIDUAL, t0);
   S.residual_evals = 1;
   double fn;
   rc = host_norm(h, h->F, &fn);
@@ -538,7 +630,9 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     if (l == p.newton_maxit) break;
     const double eta = forcing(p, l, S.fnorm, fprev, eta_prev);
     if (p.precond > 0) {
+      t0 = tbeg(h);
       TCK(h->pc.setup(h->ec, p.theta, h->U, h->Un, h->st));
+      tend(h, TUSAS_T_PC_SETUP, t0);
       h->pc_ready = true;
     }
     if (!exact) TCK(norm2_dev(h, h->U, 210));
@@ -554,8 +648,10 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     bool accepted = false;
     for (int ls = 0; ls <= p.linesearch_max; ++ls) {
       TCK(tusas::vxpay(N, h->U, lam, nullptr, h->dU, h->Ut, h->st));
+      t0 = tbeg(h);
       TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t,
                           h->st));
+      tend(h, exact ? TUSAS_T_RESIDUAL_LIN : TUSAS_T_RESIDUAL, t0);
       S.residual_evals++;
       rc = host_norm(h, h->Ft, &ftn);
       if (rc) return rc;
@@ -578,6 +674,10 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
   }
   S.converged = converged ? 1 : 0;
   if (stats) *stats = S;
+  if (h->timers_on) {
+    TCK(cudaStreamSynchronize(h->st));
+    tcollect(h);
+  }
   if (!converged) return fail(h, TUSAS_ENOCONV, "Newton did not converge");
   TCK(tusas::vcopy(N, h->U, h->Un, h->st));
   TCK(cudaStreamSynchronize(h->st));

@@ -7,6 +7,10 @@
 
 namespace tusas {
 
+// kernels launched by the library (instrumentation)
+void count_launches(long long n);
+long long launches();
+
 enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5 };
 
 struct ElemCtx {

@@ -612,31 +612,58 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
     if (blocks <= 0) continue;
     if (m.dim == 3) {
       if (c.P.model == 0)
-        k_stencil_fill<3, 0, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+        {
+          k_stencil_fill<3, 0, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+          count_launches(1);
+        }
       else
-        k_stencil_fill<3, 1, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+        {
+          k_stencil_fill<3, 1, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+          count_launches(1);
+        }
     } else {
       if (c.P.model == 0)
-        k_stencil_fill<2, 0, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+        {
+          k_stencil_fill<2, 0, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+          count_launches(1);
+        }
       else
-        k_stencil_fill<2, 1, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+        {
+          k_stencil_fill<2, 1, T><<<(unsigned)blocks, 128, 0, st>>>(A);
+          count_launches(1);
+        }
     }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   for (size_t l = 1; l < lv.size(); ++l) {
     if (m.dim == 3)
-      k_rap<3, T><<<grid_nodes(lv[l].nn), 128, 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
+      {
+        k_rap<3, T><<<grid_nodes(lv[l].nn), 128, 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
+        count_launches(1);
+      }
     else
-      k_rap<2, T><<<grid_nodes(lv[l].nn), 128, 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
+      {
+        k_rap<2, T><<<grid_nodes(lv[l].nn), 128, 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
+        count_launches(1);
+      }
   }
   for (size_t l = 0; l < lv.size(); ++l) {
     const int nb = grid_nodes(lv[l].nn);
     if (m.dim == 3)
-      k_gersh<3, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
+      {
+        k_gersh<3, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
+        count_launches(1);
+      }
     else
-      k_gersh<2, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
-    k_max_partials<<<1, 32, 0, st>>>(nb, gersh_partials, lmax_dev + 2 * l);
+      {
+        k_gersh<2, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
+        count_launches(1);
+      }
+    {
+      k_max_partials<<<1, 32, 0, st>>>(nb, gersh_partials, lmax_dev + 2 * l);
+      count_launches(1);
+    }
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -674,11 +701,17 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   }
   const bool d3 = L.m.dim == 3;
   if (d3)
-    k_cheb_init<3, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
+    {
+      k_cheb_init<3, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
                                            (T*)L.r, (T*)L.d, it);
+      count_launches(1);
+    }
   else
-    k_cheb_init<2, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
+    {
+      k_cheb_init<2, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
                                            (T*)L.r, (T*)L.d, it);
+      count_launches(1);
+    }
   T* dcur = (T*)L.d;
   T* dnext = (T*)L.d2;
   for (int kk = 0; kk < degree; ++kk) {
@@ -690,11 +723,17 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
       rho[b] = rn;
     }
     if (d3)
-      k_cheb_step<3, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
+      {
+        k_cheb_step<3, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
                                              last);
+        count_launches(1);
+      }
     else
-      k_cheb_step<2, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
+      {
+        k_cheb_step<2, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
                                              last);
+        count_launches(1);
+      }
     T* tmp = dcur;
     dcur = dnext;
     dnext = tmp;
@@ -712,18 +751,36 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   PrecondLevel& C = lv[l + 1];
   const bool d3 = F.m.dim == 3;
   if (d3) {
-    k_resid<3, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
-    k_restrict<3, T><<<grid_nodes(C.nn), 256, 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+    {
+      k_resid<3, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      count_launches(1);
+    }
+    {
+      k_restrict<3, T><<<grid_nodes(C.nn), 256, 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+      count_launches(1);
+    }
   } else {
-    k_resid<2, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
-    k_restrict<2, T><<<grid_nodes(C.nn), 256, 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+    {
+      k_resid<2, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      count_launches(1);
+    }
+    {
+      k_restrict<2, T><<<grid_nodes(C.nn), 256, 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+      count_launches(1);
+    }
   }
   e = vcycle<T>(l + 1, st);
   if (e != cudaSuccess) return e;
   if (d3)
-    k_prolong<3, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
+    {
+      k_prolong<3, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
+      count_launches(1);
+    }
   else
-    k_prolong<2, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
+    {
+      k_prolong<2, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
+      count_launches(1);
+    }
   return cheb<T>(l, false, cheb_degree, st);
 }
 
@@ -732,13 +789,22 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
   PrecondLevel& L0 = lv[0];
   const i64 n = 2 * L0.nn;
   if (kind == 1) {
-    k_jacobi<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.dinv, r, z);
+    {
+      k_jacobi<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.dinv, r, z);
+      count_launches(1);
+    }
     return cudaGetLastError();
   }
-  k_to_t<T><<<grid_nodes(n), 256, 0, st>>>(n, r, (T*)L0.b);
+  {
+    k_to_t<T><<<grid_nodes(n), 256, 0, st>>>(n, r, (T*)L0.b);
+    count_launches(1);
+  }
   cudaError_t e = vcycle<T>(0, st);
   if (e != cudaSuccess) return e;
-  k_from_t<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.x, z);
+  {
+    k_from_t<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.x, z);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 

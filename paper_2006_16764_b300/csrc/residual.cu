@@ -347,6 +347,7 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
     const long long blocks = (long long)a.ctx * a.cty * a.ctz;
     if (blocks <= 0) continue;
     elem_kernel<DIM, MODEL, MODE><<<(unsigned)blocks, NE, 0, st>>>(a);
+    count_launches(1);
   }
   return cudaGetLastError();
 }

@@ -45,30 +45,48 @@ __global__ void k_fill(i64 n, double v, double* __restrict__ y) {
 }
 
 cudaError_t vaxpy(i64 n, double a, const double* x, double* y, cudaStream_t st) {
-  k_axpy<<<grid_for(n), VT, 0, st>>>(n, a, x, y);
+  {
+    k_axpy<<<grid_for(n), VT, 0, st>>>(n, a, x, y);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 cudaError_t vxpay(i64 n, const double* x, double a, const double* ad, const double* y, double* z, cudaStream_t st) {
-  k_xpay<<<grid_for(n), VT, 0, st>>>(n, x, a, ad, y, z);
+  {
+    k_xpay<<<grid_for(n), VT, 0, st>>>(n, x, a, ad, y, z);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 cudaError_t vfdq(i64 n, const double* x, double* y, const double* ainv, cudaStream_t st) {
-  k_fdq<<<grid_for(n), VT, 0, st>>>(n, x, y, ainv);
+  {
+    k_fdq<<<grid_for(n), VT, 0, st>>>(n, x, y, ainv);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 cudaError_t vscale_dev(i64 n, const double* x, double* y, const double* s, int invert, cudaStream_t st) {
-  k_scale_dev<<<grid_for(n), VT, 0, st>>>(n, x, y, s, invert);
+  {
+    k_scale_dev<<<grid_for(n), VT, 0, st>>>(n, x, y, s, invert);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 cudaError_t vcopy(i64 n, const double* x, double* y, cudaStream_t st) {
   return cudaMemcpyAsync(y, x, sizeof(double) * n, cudaMemcpyDeviceToDevice, st);
 }
 cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st) {
-  k_scal<<<grid_for(n), VT, 0, st>>>(n, a, y);
+  {
+    k_scal<<<grid_for(n), VT, 0, st>>>(n, a, y);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st) {
-  k_fill<<<grid_for(n), VT, 0, st>>>(n, v, y);
+  {
+    k_fill<<<grid_for(n), VT, 0, st>>>(n, v, y);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -125,21 +143,39 @@ cudaError_t multidot(i64 n, int k, const double* X, i64 ld, const double* y, dou
   int km;
   if (k == 1) {
     km = 1;
-    k_multidot<1><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+    {
+      k_multidot<1><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+      count_launches(1);
+    }
   } else if (k <= 4) {
     km = 4;
-    k_multidot<4><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+    {
+      k_multidot<4><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+      count_launches(1);
+    }
   } else if (k <= 8) {
     km = 8;
-    k_multidot<8><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+    {
+      k_multidot<8><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+      count_launches(1);
+    }
   } else if (k <= 16) {
     km = 16;
-    k_multidot<16><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+    {
+      k_multidot<16><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+      count_launches(1);
+    }
   } else {
     km = 32;
-    k_multidot<32><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+    {
+      k_multidot<32><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
+      count_launches(1);
+    }
   }
-  k_reduce_partials<<<1, 32, 0, st>>>(RB, k, km, partials, out);
+  {
+    k_reduce_partials<<<1, 32, 0, st>>>(RB, k, km, partials, out);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
@@ -168,13 +204,25 @@ static cudaError_t multi_axpy_sign(i64 n, int k, const double* X, i64 ld, const 
   if (k > 32) return cudaErrorInvalidValue;
   const int g = grid_for(n);
   if (k <= 4)
-    k_multi_axpy<4><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+    {
+      k_multi_axpy<4><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+      count_launches(1);
+    }
   else if (k <= 8)
-    k_multi_axpy<8><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+    {
+      k_multi_axpy<8><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+      count_launches(1);
+    }
   else if (k <= 16)
-    k_multi_axpy<16><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+    {
+      k_multi_axpy<16><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+      count_launches(1);
+    }
   else
-    k_multi_axpy<32><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+    {
+      k_multi_axpy<32><<<g, VT, 0, st>>>(n, k, X, ld, c, sign, y);
+      count_launches(1);
+    }
   return cudaGetLastError();
 }
 
@@ -182,7 +230,10 @@ cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, d
                        cudaStream_t st) {
   cudaError_t e = multi_axpy_sign(n, k, X, ld, c, -1.0, y, st);
   if (e != cudaSuccess || accum_c == nullptr) return e;
-  k_add_small<<<1, 32, 0, st>>>(k, c, accum_c);
+  {
+    k_add_small<<<1, 32, 0, st>>>(k, c, accum_c);
+    count_launches(1);
+  }
   return cudaGetLastError();
 }
 
