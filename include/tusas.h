@@ -149,6 +149,29 @@ int tusas_precond_apply(tusas_handle* h, const double* r, double* z);
  * left unchanged. */
 int tusas_step(tusas_handle* h, tusas_stats* stats);
 
+/* Forward sweep for a discrete adjoint (no counterpart in the paper, whose
+ * solver needs only F and J v): set the state to U0 (host or device) at t0,
+ * take nsteps backward-Euler steps of size dt with tusas_step, and record
+ * U_0, U_c, U_2c, ... (c = ckpt_every) in handle-owned device memory. The
+ * state becomes U_N. *total (if non-NULL) sums the step statistics.
+ * Synchronises. Returns the first failing step's code. */
+int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int nsteps, int ckpt_every,
+                  tusas_stats* total);
+
+/* Discrete adjoint of the last tusas_forward for S = w^T U_N (w a device
+ * vector): J_N^T lam_N = w, J_n^T lam_n = -(dF_{n+1}/dU_n)^T lam_{n+1},
+ * each solved by right-preconditioned FGMRES on J^T (same preconditioner,
+ * which is symmetric) to ||r|| <= adj_rtol ||rhs||; the states are
+ * recomputed segment by segment from the checkpoints (deterministic, so they
+ * equal the forward's). Returns dS/d eps4 = -sum_n lam_n^T dF_n/d eps4 in
+ * *grad_eps4 (host); if grad_dir != NULL, (dS/dU_0) . d0 for the device
+ * direction d0 (NULL gives 0); if g0 != NULL, dS/dU_0 = -(dF_1/dU_0)^T lam_1
+ * (device). The state is restored to U_N. stats->gmres_its counts the adjoint
+ * Krylov iterations, stats->newton_its the adjoint solves. Synchronises;
+ * TUSAS_ENOCONV if a solve misses its tolerance. */
+int tusas_adjoint(tusas_handle* h, const double* w, const double* d0, double* grad_eps4, double* grad_dir,
+                  double* g0, double adj_rtol, tusas_stats* stats);
+
 /* Deterministic FP64 dot product x . y of n doubles (device vectors); the
  * result is written to *result (host pointer). Synchronises. */
 int tusas_dot(tusas_handle* h, const double* x, const double* y, long long n, double* result);

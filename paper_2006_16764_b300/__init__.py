@@ -22,7 +22,7 @@ EXPORTS = ["tusas_create", "tusas_destroy", "tusas_set_stream", "tusas_set_param
            "tusas_set_state", "tusas_get_state", "tusas_time", "tusas_residual", "tusas_jvp",
            "tusas_jvp_fd", "tusas_jtvp", "tusas_jtvp_prev", "tusas_dFdp", "tusas_precond_setup",
            "tusas_precond_apply", "tusas_step", "tusas_dot", "tusas_last_error", "tusas_timers",
-           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak"]
+           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak", "tusas_forward", "tusas_adjoint"]
 
 TIMER_NAMES = ["residual", "residual_lin", "jv", "adjoint", "pc_apply", "pc_setup", "ortho"]
 
@@ -93,6 +93,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tusas_timers": ([vp, ctypes.c_int], ctypes.c_int),
         "tusas_get_timers": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "tusas_kernel_launches": ([], i64),
+        "tusas_forward": ([vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
+                           ctypes.POINTER(CStats)], ctypes.c_int),
+        "tusas_adjoint": ([vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), dp,
+                           ctypes.c_double, ctypes.POINTER(CStats)], ctypes.c_int),
         "tusas_fma_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
@@ -250,6 +254,21 @@ class Tusas:
             return st.as_dict()
         self._check(rc)
         return st.as_dict()
+
+    def forward(self, U0, t0, dt, nsteps, ckpt_every):
+        """nsteps implicit steps from U0 recording checkpoints; returns summed step statistics."""
+        st = CStats()
+        self._check(self._lib.tusas_forward(self._h, _ptr(U0), float(t0), float(dt), int(nsteps),
+                                            int(ckpt_every), ctypes.byref(st)))
+        return st.as_dict()
+
+    def adjoint(self, w, d0=None, g0=None, rtol=1e-10):
+        """(dS/d eps4, dS/dU_0 . d0, stats) for S = w^T U_N of the last forward()."""
+        ge, gd = ctypes.c_double(), ctypes.c_double()
+        st = CStats()
+        self._check(self._lib.tusas_adjoint(self._h, _ptr(w), _ptr(d0), ctypes.byref(ge), ctypes.byref(gd),
+                                            _ptr(g0), float(rtol), ctypes.byref(st)))
+        return ge.value, gd.value, st.as_dict()
 
     def timers(self, enable=True):
         self._check(self._lib.tusas_timers(self._h, int(enable)))

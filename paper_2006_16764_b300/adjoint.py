@@ -1,0 +1,74 @@
+"""Discrete-adjoint gradients of the final solid fraction behind a torch.autograd.Function.
+
+S(eps4, Delta) = int (1 + phi_N)/2 after N backward-Euler steps. The forward
+sweep (tusas_forward) records checkpoints; backward (tusas_adjoint) solves the
+transposed linearised steps in reverse with the library's J^T w kernels and
+contracts with dF/d eps4 and with dU_0/dDelta. Only argument marshalling here.
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import numpy as np
+import torch
+
+
+def solid_fraction_weights(mesh):
+    """(w, c) with int (1 + phi_h)/2 = w^T U + c: w is half the integral of each phi basis
+    function (h^dim times 1/2 per boundary axis), zero on the u block; c = |Omega|/2."""
+    nn = [mesh.nx + 1, mesh.ny + 1] + ([mesh.nz + 1] if mesh.dim == 3 else [])
+    m = None
+    for n in nn:
+        a = np.full(n, mesh.h)
+        a[0] = a[-1] = 0.5 * mesh.h
+        m = a if m is None else np.kron(a, m)
+    nodes = int(np.prod(nn))
+    vol = float(np.prod([mesh.h * (n - 1) for n in nn]))
+    return np.concatenate([0.5 * m, np.zeros(nodes)]), 0.5 * vol
+
+
+class SolidFraction(torch.autograd.Function):
+    """S = SolidFraction.apply(eps4, Delta, problem); eps4 and Delta are 0-d float64 tensors.
+
+    ``problem`` holds the handle, base parameters, the initial state as a
+    function of Delta (device tensor), dU_0/dDelta (device tensor), the
+    weights w (device tensor) and constant c, t0, dt, nsteps, ckpt_every.
+    """
+
+    @staticmethod
+    def forward(ctx, eps4, delta, problem):
+        pb = problem
+        prm = dataclasses.replace(pb.params, eps4=float(eps4), Delta=float(delta))
+        pb.handle.set_params(prm)
+        U0 = pb.initial_state(float(delta))
+        pb.last_forward = pb.handle.forward(U0, pb.t0, pb.dt, pb.nsteps, pb.ckpt_every)
+        UN = torch.empty_like(U0)
+        pb.handle.get_state(UN)
+        S = pb.handle.dot(pb.w, UN) + pb.c
+        ctx.problem = pb
+        return torch.tensor(S, dtype=torch.float64)
+
+    @staticmethod
+    def backward(ctx, gS):
+        pb = ctx.problem
+        ge, gd, st = pb.handle.adjoint(pb.w, pb.dU0_ddelta, rtol=pb.adj_rtol)
+        pb.last_adjoint = st
+        g = gS.detach().to(torch.float64).cpu()
+        return g * ge, g * gd, None
+
+
+@dataclasses.dataclass
+class SolidFractionProblem:
+    handle: object
+    params: object
+    initial_state: object  # Delta -> device tensor U_0
+    dU0_ddelta: torch.Tensor
+    w: torch.Tensor
+    c: float
+    t0: float
+    dt: float
+    nsteps: int
+    ckpt_every: int
+    adj_rtol: float = 1e-10
+    last_forward: dict = None
+    last_adjoint: dict = None

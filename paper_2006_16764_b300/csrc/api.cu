@@ -43,6 +43,14 @@ struct tusas_handle {
   std::vector<std::pair<int, size_t>> marks;
   double t_ms[TUSAS_NTIMERS] = {};
   long long t_cnt[TUSAS_NTIMERS] = {};
+  // discrete adjoint: checkpoints of the last recorded forward sweep
+  std::vector<double*> ckpt;   // states U_0, U_c, U_2c, ...
+  std::vector<double*> seg;    // recomputed states of one segment
+  double* lam = nullptr;       // adjoint variable
+  double* lam_rhs = nullptr;
+  double* Ufinal = nullptr;
+  int fw_steps = 0, fw_every = 0;
+  double fw_t0 = 0.0, fw_dt = 0.0;
 };
 
 namespace {
@@ -292,6 +300,11 @@ void tusas_destroy(tusas_handle* h) {
   for (double* v : vecs)
     if (v) cudaFree(v);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  for (double* p : h->ckpt) cudaFree(p);
+  for (double* p : h->seg) cudaFree(p);
+  if (h->lam) cudaFree(h->lam);
+  if (h->lam_rhs) cudaFree(h->lam_rhs);
+  if (h->Ufinal) cudaFree(h->Ufinal);
   h->pc.destroy();
   delete h;
 }
@@ -482,15 +495,20 @@ const char* tusas_last_error(const tusas_handle* h) {
 // Newton-Krylov step
 // ---------------------------------------------------------------------------
 
-static int jv_apply(tusas_handle* h, bool exact, const double* z, double* out) {
+// Krylov operators: exact tangent (stored linearisation), finite difference, transposed tangent.
+enum { OP_EXACT = 0, OP_FD = 1, OP_TRANS = 2 };
+
+static int jv_apply(tusas_handle* h, int op, const double* z, double* out) {
   const size_t t0 = tbeg(h);
-  if (exact) {
+  if (op == OP_EXACT) {
     TCK(tusas::elem_run(tusas::M_JV, h->ec, nullptr, nullptr, z, out, h->lin, h->st));
+  } else if (op == OP_TRANS) {
+    TCK(tusas::elem_run(tusas::M_JTV, h->ec, nullptr, nullptr, z, out, h->lin, h->st));
   } else {
     int rc = fd_jv(h, h->U, h->F, z, out);
     if (rc) return rc;
   }
-  tend(h, TUSAS_T_JV, t0);
+  tend(h, op == OP_TRANS ? TUSAS_T_ADJOINT : TUSAS_T_JV, t0);
   return TUSAS_OK;
 }
 
@@ -507,8 +525,8 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
 
 // Flexible right-preconditioned restarted GMRES with classical Gram-Schmidt
 // applied twice, x0 = 0; solves J x = b (b = -F) to ||b - J x|| <= tol_abs.
-static int gmres(tusas_handle* h, bool exact, const double* b, double* x, double tol_abs, int* its_out,
-                 tusas_stats* stats) {
+static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol_abs, int* its_out,
+                 tusas_stats* stats, bool* converged = nullptr) {
   const int m = h->prm.gmres_restart;
   const i64 N = h->N;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), col(64);
@@ -534,7 +552,7 @@ static int gmres(tusas_handle* h, bool exact, const double* b, double* x, double
       double* w = h->V + (i64)(j + 1) * N;
       rc = prec_apply(h, Vj, Zj);
       if (rc) return rc;
-      rc = jv_apply(h, exact, Zj, w);
+      rc = jv_apply(h, op, Zj, w);
       if (rc) return rc;
       if (stats) stats->jv_evals++;
       ++its;
@@ -578,7 +596,7 @@ static int gmres(tusas_handle* h, bool exact, const double* b, double* x, double
     TCK(tusas::multi_comb(N, mu, h->Z, N, h->sc + 128, x, h->st));
     if (resid <= tol_abs || its >= h->prm.gmres_maxit) break;
     // restart: r = b - J x
-    rc = jv_apply(h, exact, x, h->tmp);
+    rc = jv_apply(h, op, x, h->tmp);
     if (rc) return rc;
     if (stats) stats->jv_evals++;
     TCK(tusas::vcopy(N, b, r, h->st));
@@ -588,6 +606,7 @@ static int gmres(tusas_handle* h, bool exact, const double* b, double* x, double
     resid = beta;
   }
   *its_out = its;
+  if (converged) *converged = resid <= tol_abs;
   return TUSAS_OK;
 }
 
@@ -640,7 +659,7 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     TCK(tusas::vfill(N, 0.0, h->Ft, h->st));
     TCK(tusas::vaxpy(N, -1.0, h->F, h->Ft, h->st));
     int its = 0;
-    rc = gmres(h, exact, h->Ft, h->dU, eta * S.fnorm, &its, &S);
+    rc = gmres(h, exact ? OP_EXACT : OP_FD, h->Ft, h->dU, eta * S.fnorm, &its, &S);
     if (rc) return rc;
     S.gmres_its += its;
     if (S.newton_its < 32) S.gmres_per_newton[S.newton_its] = its;
@@ -688,3 +707,172 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Discrete adjoint through N implicit steps (not in the paper)
+// ---------------------------------------------------------------------------
+namespace {
+int grow(tusas_handle* h, std::vector<double*>& v, size_t n) {
+  while (v.size() < n) {
+    double* p = nullptr;
+    if (cudaMalloc(&p, sizeof(double) * h->N) != cudaSuccess) return fail(h, TUSAS_ENOMEM, "checkpoint allocation");
+    v.push_back(p);
+  }
+  return TUSAS_OK;
+}
+int ensure_vec(tusas_handle* h, double** p) {
+  if (!*p && cudaMalloc(p, sizeof(double) * h->N) != cudaSuccess) return fail(h, TUSAS_ENOMEM, "vector allocation");
+  return TUSAS_OK;
+}
+int set_state_dev(tusas_handle* h, const double* U, double t) {
+  TCK(cudaMemcpyAsync(h->Un, U, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+  h->t = t;
+  fill_phys(h);
+  h->pc_ready = false;
+  return TUSAS_OK;
+}
+}  // namespace
+
+extern "C" int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int nsteps, int ckpt_every,
+                             tusas_stats* total) {
+  if (!h || !U0 || nsteps < 1 || ckpt_every < 1) return fail(h, TUSAS_EINVAL, "bad forward arguments");
+  int rc = tusas_set_state(h, U0, t0, dt);
+  if (rc) return rc;
+  const size_t nck = (size_t)(nsteps + ckpt_every - 1) / ckpt_every + 1;
+  rc = grow(h, h->ckpt, nck);
+  if (rc) return rc;
+  tusas_stats T = {};
+  T.converged = 1;
+  TCK(cudaMemcpyAsync(h->ckpt[0], h->Un, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+  for (int n = 1; n <= nsteps; ++n) {
+    tusas_stats S = {};
+    rc = tusas_step(h, &S);
+    T.newton_its += S.newton_its;
+    T.gmres_its += S.gmres_its;
+    T.residual_evals += S.residual_evals;
+    T.jv_evals += S.jv_evals;
+    T.linesearch_halvings += S.linesearch_halvings;
+    if (n == 1) T.fnorm0 = S.fnorm0;
+    T.fnorm = S.fnorm;
+    if (rc) {
+      T.converged = 0;
+      if (total) *total = T;
+      return rc;
+    }
+    if (n % ckpt_every == 0)
+      TCK(cudaMemcpyAsync(h->ckpt[n / ckpt_every], h->Un, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+  }
+  rc = ensure_vec(h, &h->Ufinal);
+  if (rc) return rc;
+  TCK(cudaMemcpyAsync(h->Ufinal, h->Un, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  h->fw_steps = nsteps;
+  h->fw_every = ckpt_every;
+  h->fw_t0 = t0;
+  h->fw_dt = dt;
+  if (total) *total = T;
+  return TUSAS_OK;
+}
+
+extern "C" int tusas_adjoint(tusas_handle* h, const double* w, const double* d0, double* grad_eps4, double* grad_dir,
+                             double* g0, double adj_rtol, tusas_stats* stats) {
+  if (!h || !w || !grad_eps4) return fail(h, TUSAS_EINVAL, "null argument");
+  if (h->fw_steps < 1) return fail(h, TUSAS_EINVAL, "call tusas_forward first");
+  if (!(adj_rtol > 0.0)) return fail(h, TUSAS_EINVAL, "adj_rtol must be positive");
+  const int N = h->fw_steps, c = h->fw_every;
+  const double t0 = h->fw_t0, dt = h->fw_dt;
+  const i64 n2 = h->N;
+  int rc = ensure_lin(h, false);
+  if (rc) return rc;
+  if ((rc = ensure_vec(h, &h->lam)) || (rc = ensure_vec(h, &h->lam_rhs))) return rc;
+  rc = grow(h, h->seg, (size_t)c + 2);  // seg[0..c]: one segment; seg[c+1]: U_{n+1} at a segment end
+  if (rc) return rc;
+  tusas_stats S = {};
+  S.converged = 1;
+  double geps = 0.0;
+  const int nseg = (N + c - 1) / c;
+  for (int k = nseg - 1; k >= 0; --k) {
+    // recompute U_{kc} .. U_{min((k+1)c, N)} from checkpoint k
+    const int n0 = k * c, n1 = std::min((k + 1) * c, N);
+    TCK(cudaMemcpyAsync(h->seg[0], h->ckpt[k], sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->st));
+    for (int n = n0 + 1; n <= n1; ++n) {
+      rc = set_state_dev(h, h->seg[n - 1 - n0], t0 + (n - 1) * dt);
+      if (rc) return rc;
+      tusas_stats fs;
+      rc = tusas_step(h, &fs);
+      if (rc) return rc;
+      TCK(cudaMemcpyAsync(h->seg[n - n0], h->Un, sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->st));
+    }
+    for (int n = n1; n > n0; --n) {
+      const double* Un_ = h->seg[n - n0];
+      const double* Uprev = h->seg[n - 1 - n0];
+      // rhs_n = w (n = N) or -(dF_{n+1}/dU_n)^T lam_{n+1}
+      if (n == N) {
+        TCK(tusas::vcopy(n2, w, h->lam_rhs, h->st));
+      } else {
+        // state pair (U_{n+1}, U_n): U_{n+1} is seg[n+1-n0] or, at a segment end, the first state of the next segment
+        const double* Unext = (n + 1 - n0 <= c) ? h->seg[n + 1 - n0] : h->seg[c + 1];
+        rc = set_state_dev(h, Un_, t0 + n * dt);
+        if (rc) return rc;
+        const size_t ta = tbeg(h);
+        TCK(tusas::elem_run(tusas::M_PREV_T, h->ec, Unext, h->Un, h->lam, h->lam_rhs, nullptr, h->st));
+        tend(h, TUSAS_T_ADJOINT, ta);
+        TCK(tusas::vscal(n2, -1.0, h->lam_rhs, h->st));
+      }
+      // J_n^T lam_n = rhs_n at (U_n, U_{n-1})
+      rc = set_state_dev(h, Uprev, t0 + (n - 1) * dt);
+      if (rc) return rc;
+      size_t ta = tbeg(h);
+      TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, Un_, h->Un, nullptr, h->tmp, h->lin, h->st));
+      tend(h, TUSAS_T_RESIDUAL_LIN, ta);
+      if (h->prm.precond > 0) {
+        ta = tbeg(h);
+        TCK(h->pc.setup(h->ec, h->prm.theta, Un_, h->Un, h->st));
+        tend(h, TUSAS_T_PC_SETUP, ta);
+        h->pc_ready = true;
+      }
+      double bn;
+      rc = host_norm(h, h->lam_rhs, &bn);
+      if (rc) return rc;
+      int its = 0;
+      bool ok = true;
+      rc = gmres(h, OP_TRANS, h->lam_rhs, h->lam, adj_rtol * bn, &its, &S, &ok);
+      if (rc) return rc;
+      S.gmres_its += its;
+      if (S.newton_its < 32) S.gmres_per_newton[S.newton_its] = its;
+      S.newton_its++;  // counts adjoint solves
+      if (!ok) return fail(h, TUSAS_ENOCONV, "adjoint GMRES did not converge");
+      // grad_eps4 -= lam_n . dF_n/d eps4
+      ta = tbeg(h);
+      TCK(tusas::elem_run(tusas::M_DEPS, h->ec, Un_, h->Un, nullptr, h->tmp, nullptr, h->st));
+      tend(h, TUSAS_T_ADJOINT, ta);
+      double d;
+      TCK(tusas::multidot(n2, 1, h->lam, 0, h->tmp, h->partials, h->sc + 200, h->st));
+      TCK(cudaMemcpyAsync(&d, h->sc + 200, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+      TCK(cudaStreamSynchronize(h->st));
+      geps -= d;
+    }
+    // keep U_{n0+1} for the right-hand side of step n0 in the previous segment
+    if (k > 0) TCK(cudaMemcpyAsync(h->seg[c + 1], h->seg[1], sizeof(double) * n2, cudaMemcpyDeviceToDevice, h->st));
+  }
+  // dS/dU_0 = -(dF_1/dU_0)^T lam_1; segment 0 left U_0 in seg[0] and U_1 in seg[1]
+  rc = set_state_dev(h, h->seg[0], t0);
+  if (rc) return rc;
+  TCK(tusas::elem_run(tusas::M_PREV_T, h->ec, h->seg[1], h->Un, h->lam, h->tmp, nullptr, h->st));
+  TCK(tusas::vscal(n2, -1.0, h->tmp, h->st));
+  if (g0) TCK(tusas::vcopy(n2, h->tmp, g0, h->st));
+  if (grad_dir) {
+    *grad_dir = 0.0;
+    if (d0) {
+      TCK(tusas::multidot(n2, 1, h->tmp, 0, d0, h->partials, h->sc + 200, h->st));
+      TCK(cudaMemcpyAsync(grad_dir, h->sc + 200, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    }
+  }
+  // restore the forward's final state
+  rc = set_state_dev(h, h->Ufinal, t0 + N * dt);
+  if (rc) return rc;
+  TCK(cudaStreamSynchronize(h->st));
+  *grad_eps4 = geps;
+  if (stats) *stats = S;
+  return TUSAS_OK;
+}

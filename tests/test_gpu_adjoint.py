@@ -1,0 +1,89 @@
+"""Discrete adjoint through N implicit steps on the GPU against the oracle adjoint
+(direct solves) and central differences; checkpoint invariance; autograd wrapper."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import synth
+from synth import Mesh, Params
+from oracle import adjoint as OA
+from tests.gpu_util import dev, handle, host
+
+pytestmark = pytest.mark.gpu
+
+
+def _problem(kind):
+    if kind == "pure":
+        mesh = Mesh(2, 10, 10, 0, 2.0)
+        prm = Params(model=0, eps4=0.04, lam=3.19, D=2.0, Delta=0.6, precond=1, jvp_mode=1, newton_rtol=1e-13)
+        U0f = lambda p: synth.seed_state(mesh, p, radius=6.0)
+        return mesh, prm, U0f, 0.5, 3
+    mesh = Mesh(2, 10, 10, 0, 1.2, -6.0, -6.0)
+    prm = Params(model=1, k=0.15, eps4=0.03, lam=3.19, D=2.0, Delta=0.5, precond=1, jvp_mode=1, newton_rtol=1e-13)
+    U0f = lambda p: synth.seed_state(mesh, p, radius=3.0, centred=True)
+    return mesh, prm, U0f, 0.3, 2
+
+
+@pytest.mark.parametrize("kind", ["pure", "alloy"])
+def test_adjoint_matches_oracle_adjoint(kind):
+    mesh, prm, U0f, dt, n = _problem(kind)
+    U0 = U0f(prm)
+    states = OA.forward(mesh, prm, U0, 0.0, dt, n)
+    w, c = OA.solid_fraction_weights(mesh)
+    g_eps, g0 = OA.gradient(mesh, prm, states, 0.0, dt, w)
+    nn = mesh.n_nodes
+    d0 = np.concatenate([np.zeros(nn), -np.ones(nn)])
+    h = handle(mesh, prm)
+    st = h.forward(dev(U0), 0.0, dt, n, 2)
+    assert st["converged"]
+    UN = host(h.get_state(dev(np.zeros_like(U0))))
+    assert np.abs(UN - states[-1]).max() <= 1e-9 * np.abs(states[-1]).max()
+    tg0 = dev(np.zeros_like(U0))
+    ge, gd, ast = h.adjoint(dev(w), dev(d0), tg0, rtol=1e-12)
+    assert abs(ge - g_eps) <= 1e-7 * abs(g_eps)
+    assert abs(gd - g0 @ d0) <= 1e-7 * abs(g0 @ d0)
+    assert np.abs(host(tg0) - g0).max() <= 1e-7 * np.abs(g0).max()
+    # the state is restored to U_N
+    assert np.array_equal(host(h.get_state(dev(np.zeros_like(U0)))), UN)
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient():
+    mesh, prm, U0f, dt, _ = _problem("pure")
+    U0 = dev(U0f(prm))
+    w, _ = OA.solid_fraction_weights(mesh)
+    h = handle(mesh, prm)
+    res = []
+    for every in (1, 2, 3, 5):
+        h.forward(U0, 0.0, dt, 5, every)
+        ge, gd, _ = h.adjoint(dev(w), None, None, rtol=1e-12)
+        res.append(ge)
+    assert max(res) - min(res) == 0.0, res
+
+
+def test_autograd_function_matches_central_differences():
+    import torch
+
+    from paper_2006_16764_b300.adjoint import SolidFraction, SolidFractionProblem, solid_fraction_weights
+
+    mesh, prm, U0f, dt, n = _problem("alloy")
+    w, c = solid_fraction_weights(mesh)
+    wo, co = OA.solid_fraction_weights(mesh)
+    assert np.abs(w - wo).max() < 1e-15 and abs(c - co) < 1e-12
+    h = handle(mesh, prm)
+    nn = mesh.n_nodes
+    pb = SolidFractionProblem(h, prm, lambda d: dev(U0f(dataclasses.replace(prm, Delta=d))),
+                              dev(np.concatenate([np.zeros(nn), -np.ones(nn)])), dev(w), c, 0.0, dt, n, 1, 1e-12)
+    eps = torch.tensor(prm.eps4, dtype=torch.float64, requires_grad=True)
+    dl = torch.tensor(prm.Delta, dtype=torch.float64, requires_grad=True)
+    S = SolidFraction.apply(eps, dl, pb)
+    ge, gd = torch.autograd.grad(S, (eps, dl))
+    hh = 1e-5
+
+    def S_at(e, d):
+        return float(SolidFraction.apply(torch.tensor(e, dtype=torch.float64), torch.tensor(d, dtype=torch.float64), pb))
+
+    fd_e = (S_at(prm.eps4 + hh, prm.Delta) - S_at(prm.eps4 - hh, prm.Delta)) / (2 * hh)
+    fd_d = (S_at(prm.eps4, prm.Delta + hh) - S_at(prm.eps4, prm.Delta - hh)) / (2 * hh)
+    assert abs(float(ge) - fd_e) <= 1e-5 * abs(fd_e)
+    assert abs(float(gd) - fd_d) <= 1e-5 * abs(fd_d)

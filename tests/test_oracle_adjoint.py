@@ -1,0 +1,63 @@
+"""Pins of the oracle's discrete adjoint against central differences of the forward solve."""
+import dataclasses
+
+import numpy as np
+
+import synth
+from synth import Mesh, Params
+from oracle import adjoint as OA
+
+
+def _S(mesh, prm, U0, dt, n):
+    w, c = OA.solid_fraction_weights(mesh)
+    return w @ OA.forward(mesh, prm, U0, 0.0, dt, n)[-1] + c
+
+
+def test_solid_fraction_weights_integrate_exactly():
+    mesh = Mesh(2, 5, 3, 0, 0.7)
+    w, c = OA.solid_fraction_weights(mesh)
+    n = mesh.n_nodes
+    U = np.concatenate([np.ones(n), np.zeros(n)])  # phi = 1 everywhere: S = |Omega|
+    assert abs(w @ U + c - 5 * 3 * 0.49) < 1e-12
+    U[:n] = -1.0
+    assert abs(w @ U + c) < 1e-12
+
+
+def test_adjoint_gradient_matches_central_differences():
+    mesh = Mesh(2, 10, 10, 0, 2.0)
+    prm = Params(model=0, eps4=0.04, lam=3.19, D=2.0, Delta=0.6)
+    dt, n = 0.5, 3
+    U0 = synth.seed_state(mesh, prm, radius=6.0)
+    states = OA.forward(mesh, prm, U0, 0.0, dt, n)
+    w, _ = OA.solid_fraction_weights(mesh)
+    g_eps, g0 = OA.gradient(mesh, prm, states, 0.0, dt, w)
+    h = 1e-6
+    fd = (_S(mesh, dataclasses.replace(prm, eps4=prm.eps4 + h), U0, dt, n)
+          - _S(mesh, dataclasses.replace(prm, eps4=prm.eps4 - h), U0, dt, n)) / (2 * h)
+    assert abs(g_eps - fd) <= 1e-5 * abs(fd)
+    # Delta enters through u(x, 0) = -Delta only
+    nn = mesh.n_nodes
+    dU0 = np.concatenate([np.zeros(nn), -np.ones(nn)])
+    pD = lambda d: synth.seed_state(mesh, dataclasses.replace(prm, Delta=d), radius=6.0)
+    fdD = (_S(mesh, prm, pD(prm.Delta + h), dt, n) - _S(mesh, prm, pD(prm.Delta - h), dt, n)) / (2 * h)
+    assert abs(g0 @ dU0 - fdD) <= 1e-5 * abs(fdD)
+
+
+def test_alloy_adjoint_matches_central_differences():
+    """Isothermal alloy (frozen gradient off) around a curved seed, antitrapping on."""
+    mesh = Mesh(2, 10, 10, 0, 1.2, -6.0, -6.0)
+    prm = Params(model=1, k=0.15, eps4=0.03, lam=3.19, D=2.0, Delta=0.5)
+    dt, n = 0.3, 2
+    U0 = synth.seed_state(mesh, prm, radius=3.0, centred=True)
+    states = OA.forward(mesh, prm, U0, 0.0, dt, n)
+    w, _ = OA.solid_fraction_weights(mesh)
+    g_eps, g0 = OA.gradient(mesh, prm, states, 0.0, dt, w)
+    h = 1e-5
+    fd = (_S(mesh, dataclasses.replace(prm, eps4=prm.eps4 + h), U0, dt, n)
+          - _S(mesh, dataclasses.replace(prm, eps4=prm.eps4 - h), U0, dt, n)) / (2 * h)
+    assert abs(g_eps - fd) <= 1e-5 * abs(fd)
+    nn = mesh.n_nodes
+    dU0 = np.concatenate([np.zeros(nn), -np.ones(nn)])
+    pD = lambda d: synth.seed_state(mesh, dataclasses.replace(prm, Delta=d), radius=3.0, centred=True)
+    fdD = (_S(mesh, prm, pD(prm.Delta + h), dt, n) - _S(mesh, prm, pD(prm.Delta - h), dt, n)) / (2 * h)
+    assert abs(g0 @ dU0 - fdD) <= 1e-5 * abs(fdD)
