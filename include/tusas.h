@@ -201,6 +201,28 @@ long long tusas_kernel_launches(void);
  * Allocates and frees a small device buffer. Synchronises the device. */
 int tusas_fma_peak(double* fp64_flops, double* fp32_flops);
 
+/* ---- Reductions without device allocation (no counterpart in the paper) ----
+ * For callers that cannot allocate device memory at the point where they need
+ * a reduction (all device memory handed to their own pool allocator, a loop
+ * that cannot afford the implicit synchronisation of cudaMalloc/cudaFree, or
+ * code that must not create a handle, which allocates workspaces):
+ * out[j] = X_j . y for j < k, X_j = X + j*ld, n doubles each (device
+ * vectors), with the same deterministic partition and summation order as
+ * tusas_dot, so k = 1 returns tusas_dot's value. Results go to the host array
+ * out[k]. The partial sums live in a fixed device array of the library
+ * (TUSAS_NOALLOC_MAX_K x 296 + TUSAS_NOALLOC_MAX_K doubles, about 76 KB per
+ * GPU, held until the process exits); nothing is allocated or freed. The
+ * first call on a device looks up that array's address (cudaGetSymbolAddress
+ * with the device current); make that first call before any stream capture.
+ * All calls share the array: calls that overlap on the GPU race and must be
+ * serialised by the caller. Works on `stream` (a cudaStream_t, NULL = legacy
+ * default) and synchronises it. Returns TUSAS_EINVAL for k < 1,
+ * k > TUSAS_NOALLOC_MAX_K, n < 0, null pointers or ld < n when k > 1;
+ * TUSAS_ECUDA if a CUDA call fails. */
+#define TUSAS_NOALLOC_MAX_K 32
+int tusas_multidot_noalloc(const double* X, long long ld, int k, const double* y, long long n, double* out,
+                           void* stream);
+
 /* Description of the last error on this handle (never NULL). */
 const char* tusas_last_error(const tusas_handle* h);
 

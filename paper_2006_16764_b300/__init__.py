@@ -22,7 +22,7 @@ EXPORTS = ["tusas_create", "tusas_destroy", "tusas_set_stream", "tusas_set_param
            "tusas_set_state", "tusas_get_state", "tusas_time", "tusas_residual", "tusas_jvp",
            "tusas_jvp_fd", "tusas_jtvp", "tusas_jtvp_prev", "tusas_dFdp", "tusas_precond_setup",
            "tusas_precond_apply", "tusas_step", "tusas_dot", "tusas_last_error", "tusas_timers",
-           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak", "tusas_forward", "tusas_adjoint"]
+           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak", "tusas_forward", "tusas_adjoint", "tusas_multidot_noalloc"]
 
 TIMER_NAMES = ["residual", "residual_lin", "jv", "adjoint", "pc_apply", "pc_setup", "ortho"]
 
@@ -93,6 +93,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tusas_timers": ([vp, ctypes.c_int], ctypes.c_int),
         "tusas_get_timers": ([vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_longlong)], ctypes.c_int),
         "tusas_kernel_launches": ([], i64),
+        "tusas_multidot_noalloc": ([dp, i64, ctypes.c_int, dp, i64, ctypes.POINTER(ctypes.c_double), vp],
+                                   ctypes.c_int),
         "tusas_forward": ([vp, dp, ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int,
                            ctypes.POINTER(CStats)], ctypes.c_int),
         "tusas_adjoint": ([vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), dp,
@@ -128,6 +130,23 @@ def fma_peak():
     if rc != OK:
         raise TusasError(rc, "tusas_fma_peak failed")
     return a.value, b.value
+
+
+NOALLOC_MAX_K = 32
+
+
+def multidot_noalloc(X, k, y, n, ld=None, stream=None):
+    """[X_j . y for j < k] without any device allocation (see tusas_multidot_noalloc).
+
+    X: device tensor holding k vectors of stride ``ld`` (default n); y: device
+    tensor of n doubles. Serialise overlapping calls: they share one scratch array.
+    """
+    out = (ctypes.c_double * max(int(k), 1))()
+    raw = None if stream is None else ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    rc = lib().tusas_multidot_noalloc(_ptr(X), int(n if ld is None else ld), int(k), _ptr(y), int(n), out, raw)
+    if rc != OK:
+        raise TusasError(rc, "tusas_multidot_noalloc failed")
+    return [out[j] for j in range(int(k))]
 
 
 class TusasError(RuntimeError):
