@@ -242,26 +242,47 @@ __global__ void __launch_bounds__(Tile<DIM>::X * Tile<DIM>::Y * Tile<DIM>::Z) k_
 // ---------------------------------------------------------------------------
 // stencil helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void node_xyz(const DevMesh& m, i64 i, int& x, int& y, int& z) {
-  x = (int)(i % m.nnx);
-  const i64 r = i / m.nnx;
-  y = (int)(r % m.nny);
-  z = (int)(r / m.nny);
+
+// Node of the calling thread in a 3D launch (x fastest); false outside the mesh.
+__device__ __forceinline__ bool node3(const DevMesh& m, int& ix, int& iy, int& iz, i64& node) {
+  ix = blockIdx.x * blockDim.x + threadIdx.x;
+  iy = blockIdx.y * blockDim.y + threadIdx.y;
+  iz = blockIdx.z * blockDim.z + threadIdx.z;
+  if (ix >= m.nnx || iy >= m.nny || iz >= m.nnz) return false;
+  node = ix + (i64)m.nnx * (iy + (i64)m.nny * iz);
+  return true;
 }
 
+// sum_o A[o] x[node + o] in offset order; interior nodes skip the bounds tests
 template <int DIM, typename T>
 __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __restrict__ x, const DevMesh& m, i64 node,
                                            int ix, int iy, int iz) {
   constexpr int NS = Pow3<DIM>::V;
+  const i64 sy = m.nnx, sz = (i64)m.nnx * m.nny;
   T s = T(0);
+  const bool interior = ix > 0 && ix < m.nnx - 1 && iy > 0 && iy < m.nny - 1 && (DIM == 2 || (iz > 0 && iz < m.nnz - 1));
+  if (interior) {
 #pragma unroll
-  for (int o = 0; o < NS; ++o) {
-    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
-    const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
-    if (jx < 0 || jx >= m.nnx || jy < 0 || jy >= m.nny || jz < 0 || jz >= m.nnz) continue;
-    s += st[o * m.nn + node] * x[node + ox + (i64)m.nnx * (oy + (i64)m.nny * oz)];
+    for (int o = 0; o < NS; ++o) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
+      s += __ldg(st + o * m.nn + node) * __ldg(x + node + ox + sy * oy + sz * oz);
+    }
+  } else {
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
+      const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+      if (jx < 0 || jx >= m.nnx || jy < 0 || jy >= m.nny || jz < 0 || jz >= m.nnz) continue;
+      s += st[o * m.nn + node] * x[node + ox + sy * oy + sz * oz];
+    }
   }
   return s;
+}
+
+static dim3 block3(const DevMesh& m) { return m.dim == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1); }
+static dim3 grid3(const DevMesh& m) {
+  const dim3 b = block3(m);
+  return dim3((m.nnx + b.x - 1) / b.x, (m.nny + b.y - 1) / b.y, (m.nnz + b.z - 1) / b.z);
 }
 
 static int grid_nodes(i64 n) {
@@ -274,9 +295,10 @@ static int grid_nodes(i64 n) {
 template <int DIM, typename T>
 __global__ void k_rap(DevMesh mf, DevMesh mc, const T* __restrict__ stf, T* __restrict__ stc) {
   constexpr int NS = Pow3<DIM>::V;
-  for (i64 I = blockIdx.x * (i64)blockDim.x + threadIdx.x; I < mc.nn; I += (i64)gridDim.x * blockDim.x) {
+  {
     int cx, cy, cz;
-    node_xyz(mc, I, cx, cy, cz);
+    i64 I;
+    if (!node3(mc, cx, cy, cz, I)) return;
     for (int blk = 0; blk < 2; ++blk) {
       T acc[NS];
 #pragma unroll
@@ -383,9 +405,10 @@ template <int DIM, typename T>
 __global__ void k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
   constexpr int NS = Pow3<DIM>::V;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < m.nn; i += (i64)gridDim.x * blockDim.x) {
+  {
     int ix, iy, iz;
-    node_xyz(m, i, ix, iy, iz);
+    i64 i;
+    if (!node3(m, ix, iy, iz, i)) return;
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
       T v = bvec[blk * m.nn + i];
@@ -405,9 +428,10 @@ template <int DIM, typename T>
 __global__ void k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
   constexpr int NS = Pow3<DIM>::V;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < m.nn; i += (i64)gridDim.x * blockDim.x) {
+  {
     int ix, iy, iz;
-    node_xyz(m, i, ix, iy, iz);
+    i64 i;
+    if (!node3(m, ix, iy, iz, i)) return;
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
       const i64 k = blk * m.nn + i;
@@ -427,9 +451,10 @@ template <int DIM, typename T>
 __global__ void k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
   constexpr int NS = Pow3<DIM>::V;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < m.nn; i += (i64)gridDim.x * blockDim.x) {
+  {
     int ix, iy, iz;
-    node_xyz(m, i, ix, iy, iz);
+    i64 i;
+    if (!node3(m, ix, iy, iz, i)) return;
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk)
       res[blk * m.nn + i] =
@@ -441,9 +466,10 @@ __global__ void k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict
 template <int DIM, typename T>
 __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T* __restrict__ bc) {
   constexpr int NS = Pow3<DIM>::V;
-  for (i64 I = blockIdx.x * (i64)blockDim.x + threadIdx.x; I < mc.nn; I += (i64)gridDim.x * blockDim.x) {
+  {
     int cx, cy, cz;
-    node_xyz(mc, I, cx, cy, cz);
+    i64 I;
+    if (!node3(mc, cx, cy, cz, I)) return;
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
       T s = T(0);
@@ -463,9 +489,10 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
 // x_f(i) += sum_J P(i, J) x_c(J)
 template <int DIM, typename T>
 __global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, T* __restrict__ xf) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < mf.nn; i += (i64)gridDim.x * blockDim.x) {
+  {
     int fx, fy, fz;
-    node_xyz(mf, i, fx, fy, fz);
+    i64 i;
+    if (!node3(mf, fx, fy, fz, i)) return;
     const int f[3] = {fx, fy, fz};
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
@@ -639,12 +666,12 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
   for (size_t l = 1; l < lv.size(); ++l) {
     if (m.dim == 3)
       {
-        k_rap<3, T><<<grid_nodes(lv[l].nn), 128, 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
+        k_rap<3, T><<<grid3(lv[l].m), block3(lv[l].m), 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
         count_launches(1);
       }
     else
       {
-        k_rap<2, T><<<grid_nodes(lv[l].nn), 128, 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
+        k_rap<2, T><<<grid3(lv[l].m), block3(lv[l].m), 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
         count_launches(1);
       }
   }
@@ -687,7 +714,6 @@ cudaError_t Precond::setup(const ElemCtx& c, double theta, const double* U, cons
 template <typename T>
 cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   PrecondLevel& L = lv[l];
-  const int nb = grid_nodes(L.nn);
   Coef2<T> it, cc;
   double theta[2], delta[2], sigma[2], rho[2];
   for (int b = 0; b < 2; ++b) {
@@ -702,13 +728,13 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   const bool d3 = L.m.dim == 3;
   if (d3)
     {
-      k_cheb_init<3, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
+      k_cheb_init<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
                                            (T*)L.r, (T*)L.d, it);
       count_launches(1);
     }
   else
     {
-      k_cheb_init<2, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
+      k_cheb_init<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
                                            (T*)L.r, (T*)L.d, it);
       count_launches(1);
     }
@@ -724,13 +750,13 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
     }
     if (d3)
       {
-        k_cheb_step<3, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
+        k_cheb_step<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
                                              last);
         count_launches(1);
       }
     else
       {
-        k_cheb_step<2, T><<<nb, 256, 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
+        k_cheb_step<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
                                              last);
         count_launches(1);
       }
@@ -752,20 +778,20 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   const bool d3 = F.m.dim == 3;
   if (d3) {
     {
-      k_resid<3, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      k_resid<3, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
       count_launches(1);
     }
     {
-      k_restrict<3, T><<<grid_nodes(C.nn), 256, 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+      k_restrict<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
       count_launches(1);
     }
   } else {
     {
-      k_resid<2, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      k_resid<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
       count_launches(1);
     }
     {
-      k_restrict<2, T><<<grid_nodes(C.nn), 256, 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+      k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
       count_launches(1);
     }
   }
@@ -773,12 +799,12 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   if (e != cudaSuccess) return e;
   if (d3)
     {
-      k_prolong<3, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
+      k_prolong<3, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
       count_launches(1);
     }
   else
     {
-      k_prolong<2, T><<<grid_nodes(F.nn), 256, 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
+      k_prolong<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
       count_launches(1);
     }
   return cheb<T>(l, false, cheb_degree, st);
