@@ -61,6 +61,9 @@ def parse():
     ap.add_argument("--fd-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--report", default=None, choices=synth.WORKLOADS,
+                    help="run one workload's full protocol (step counts, precision / tangent comparisons, "
+                         "adjoint gradients) and print a JSON summary")
     ap.add_argument("--kernels", action="store_true",
                     help="profiling case: a few residual / linearisation / tangent passes on a 256x192x64 "
                          "sub-box of the alloy workload (inputs > L2, about 5 GB on the device)")
@@ -94,6 +97,175 @@ def run_kernels():
 
 
 # ----------------------------------------------------------------------------
+def _timed_steps(h, n, stream):
+    import torch
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = [h.step() for _ in range(n)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / 1e3, st
+
+
+def _run_variant(w, prm, U0, nsteps, stream):
+    """nsteps implicit steps; stops at the first step that does not converge and says so."""
+    import torch
+
+    import paper_2006_16764_b300 as pkg
+
+    h = pkg.Tusas(w.mesh, prm, stream=stream)
+    h.set_state(U0, 0.0, w.dt)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    st = []
+    failed = None
+    for i in range(nsteps):
+        s = h.step(allow_noconv=True)
+        st.append(s)
+        if not s["converged"]:
+            failed = i + 1
+            break
+    e1.record(stream)
+    torch.cuda.synchronize()
+    secs = e0.elapsed_time(e1) / 1e3
+    U = torch.empty_like(U0)
+    h.get_state(U)
+    h.close()
+    return {"s_per_step": secs / len(st), "steps_done": len(st), "newton_its": [s["newton_its"] for s in st],
+            "gmres_its": [s["gmres_its"] for s in st], "converged": failed is None,
+            "first_failed_step": failed}, U
+
+
+def run_report(name):
+    """Each workload's protocol: step counts, tangent / precision comparisons, adjoint gradients."""
+    import dataclasses
+
+    import torch
+
+    import paper_2006_16764_b300 as pkg
+
+    w = synth.workload(name)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    U0 = torch.tensor(synth.initial_state(w), device=dev)
+    out = {"report": name, "dofs": w.mesh.n_dofs, "dt": w.dt, "steps": w.steps,
+           "kappa": 2 * w.dt * (w.params.D / (1 + w.params.k)) / w.mesh.h ** 2}
+    if name == "dendrite2d_128":
+        r, U = _run_variant(w, w.params, U0, w.steps, stream)
+        out["fd_jfnk_jacobi_fp64"] = r
+        Ur, Un = synth.random_fields(w.mesh, 42)
+        h = pkg.Tusas(w.mesh, w.params, stream=stream)
+        h.set_state(torch.tensor(Un, device=dev), 0.0, w.dt)
+        tU = torch.tensor(Ur, device=dev)
+        F = torch.empty_like(tU)
+        h.residual(tU, F)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(100):
+            h.residual(tU, F)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 100
+        out["residual_100_evals"] = {"ms_per_eval": ms, "Mdof_evals_per_s": w.mesh.n_dofs / ms / 1e3}
+        h.close()
+    elif name == "dendrite2d_1024":
+        sweep = []
+        for n in (128, 256, 512, 1024, 2048, 4096):
+            ws = synth.scaled(w, n, n)
+            ws.mesh.h = 400.0 / n
+            h = pkg.Tusas(ws.mesh, dataclasses.replace(w.params, precond=0, gmres_restart=1), stream=stream)
+            Us = torch.tensor(synth.initial_state(ws), device=dev)
+            h.set_state(Us, 0.0, w.dt)
+            F = torch.empty_like(Us)
+            for _ in range(3):
+                h.residual(Us, F)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            reps = 20
+            e0.record(stream)
+            for _ in range(reps):
+                h.residual(Us, F)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            sweep.append({"n": n, "dofs": ws.mesh.n_dofs, "ms": ms, "Mdof_evals_per_s": ws.mesh.n_dofs / ms / 1e3})
+            h.close()
+            del Us, F
+        out["residual_sweep"] = sweep
+        base = dataclasses.replace(w.params, newton_maxit=30)
+        r32, U32 = _run_variant(w, dataclasses.replace(base, smoother_fp32=1), U0, w.steps, stream)
+        r64, U64 = _run_variant(w, dataclasses.replace(base, smoother_fp32=0), U0, w.steps, stream)
+        rex, Uex = _run_variant(w, dataclasses.replace(base, smoother_fp32=1, jvp_mode=1), U0, w.steps, stream)
+        out["fd_jfnk_gmg_fp32"] = r32
+        out["fd_jfnk_gmg_fp64"] = r64
+        out["exact_jfnk_gmg_fp32"] = rex
+        out["fp32_vs_fp64_solution_rel_inf"] = float((U32 - U64).abs().max() / U64.abs().max())
+    elif name == "dendrite3d_192":
+        r32, U32 = _run_variant(w, dataclasses.replace(w.params, smoother_fp32=1), U0, w.steps, stream)
+        r64, U64 = _run_variant(w, dataclasses.replace(w.params, smoother_fp32=0), U0, w.steps, stream)
+        out["exact_jfnk_gmg_fp32"] = r32
+        out["exact_jfnk_gmg_fp64"] = r64
+        out["fp32_vs_fp64_solution_rel_inf"] = float((U32 - U64).abs().max() / U64.abs().max())
+    elif name == "alloy3d_256x256x128":
+        rex, Uex = _run_variant(w, dataclasses.replace(w.params, jvp_mode=1, smoother_fp32=1), U0, w.steps, stream)
+        rfd, Ufd = _run_variant(w, dataclasses.replace(w.params, jvp_mode=0, smoother_fp32=1), U0, w.steps, stream)
+        rfd64, Ufd64 = _run_variant(w, dataclasses.replace(w.params, jvp_mode=0, smoother_fp32=0), U0, w.steps, stream)
+        out["exact_jv_gmg_fp32"] = rex
+        out["fd_jv_gmg_fp32"] = rfd
+        out["fd_jv_gmg_fp64"] = rfd64
+        out["exact_vs_fd_solution_rel_inf"] = float((Uex - Ufd).abs().max() / Ufd.abs().max())
+        out["exact_fp32_vs_fd_fp64_solution_rel_inf"] = float((Uex - Ufd64).abs().max() / Ufd64.abs().max())
+    elif name == "adjoint2d_512":
+        from paper_2006_16764_b300.adjoint import SolidFraction, SolidFractionProblem, solid_fraction_weights
+
+        wts, c = solid_fraction_weights(w.mesh)
+        nn = w.mesh.n_nodes
+        # tight Newton tolerance for the finite-difference check (1e-13 and 1e-12 are at the
+        # FP64 roundoff floor of ||F|| at this size: ||F||/||F0|| stalls near 5e-13 on some steps)
+        prm = dataclasses.replace(w.params, jvp_mode=1, newton_rtol=1e-11)
+        h = pkg.Tusas(w.mesh, prm, stream=stream)
+        pb = SolidFractionProblem(
+            h, prm, lambda d: torch.tensor(synth.initial_state(
+                synth.Workload(w.name, w.mesh, dataclasses.replace(prm, Delta=d), w.dt, w.steps)), device=dev),
+            torch.tensor(np.concatenate([np.zeros(nn), -np.ones(nn)]), device=dev),
+            torch.tensor(wts, device=dev), c, 0.0, w.dt, w.steps, 10, 1e-12)
+        r = synth.uniform01(3, 16)
+        samples = []
+        for i in range(8):
+            e4 = 0.02 + 0.04 * r[2 * i]
+            dl = 0.45 + 0.30 * r[2 * i + 1]
+            te = torch.tensor(e4, dtype=torch.float64, requires_grad=True)
+            td = torch.tensor(dl, dtype=torch.float64, requires_grad=True)
+            t0 = time.perf_counter()
+            S = SolidFraction.apply(te, td, pb)
+            t1 = time.perf_counter()
+            ge, gd = torch.autograd.grad(S, (te, td))
+            t2 = time.perf_counter()
+            samples.append({"eps4": e4, "Delta": dl, "S": float(S), "dS_deps4": float(ge), "dS_dDelta": float(gd),
+                            "forward_s": t1 - t0, "adjoint_s": t2 - t1,
+                            "forward_gmres": pb.last_forward["gmres_its"], "adjoint_gmres": pb.last_adjoint["gmres_its"]})
+        out["samples"] = samples
+        # central differences (h = 1e-6) for the first sample, Newton tolerance 1e-13
+        hh = 1e-6
+        s0 = samples[0]
+        out["newton_rtol"] = prm.newton_rtol
+
+        def S_at(e4, dl):
+            return float(SolidFraction.apply(torch.tensor(e4, dtype=torch.float64), torch.tensor(dl, dtype=torch.float64), pb))
+
+        fd_e = (S_at(s0["eps4"] + hh, s0["Delta"]) - S_at(s0["eps4"] - hh, s0["Delta"])) / (2 * hh)
+        fd_d = (S_at(s0["eps4"], s0["Delta"] + hh) - S_at(s0["eps4"], s0["Delta"] - hh)) / (2 * hh)
+        out["fd_check"] = {"h": hh, "dS_deps4_fd": fd_e, "dS_dDelta_fd": fd_d,
+                           "rel_err_eps4": abs(s0["dS_deps4"] - fd_e) / abs(fd_e),
+                           "rel_err_Delta": abs(s0["dS_dDelta"] - fd_d) / abs(fd_d)}
+        h.close()
+    print(json.dumps(out), flush=True)
+
+
 def cpu_oracle_rate(seconds, warm=0):
     """Oracle residual evaluations on the bounded sample; Mdof-evals/s on 1 host core."""
     from oracle import residual as OR
@@ -387,6 +559,9 @@ def main():
     args = parse()
     if args.kernels:
         run_kernels()
+        return
+    if args.report:
+        run_report(args.report)
         return
     ws, rank, local = dist_setup(args)
     if args.impl == "reference":

@@ -556,17 +556,20 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       if (rc) return rc;
       if (stats) stats->jv_evals++;
       ++its;
-      // CGS2: h = V^T w; w -= V h; h2 = V^T w; w -= V h2; h += h2
+      // classical Gram-Schmidt applied twice (CGS2): h = V^T w; w -= V h; h2 = V^T w;
+      // w -= V h2 fused with ||w||^2; h += h2
       const size_t to = tbeg(h);
       TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc, h->st));
       TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc, w, nullptr, h->st));
       TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc + 64, h->st));
-      TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc + 64, w, h->sc, h->st));
-      TCK(norm2_dev(h, w, 63));
-      tend(h, TUSAS_T_ORTHO, to);
+      TCK(tusas::multi_axpy_norm(N, j + 1, h->V, N, h->sc + 64, w, h->partials, h->sc + 63, h->st));
+      std::vector<double> col2(64);
       TCK(cudaMemcpyAsync(col.data(), h->sc, sizeof(double) * 64, cudaMemcpyDeviceToHost, h->st));
+      TCK(cudaMemcpyAsync(col2.data(), h->sc + 64, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->st));
       TCK(cudaStreamSynchronize(h->st));
+      for (int i = 0; i <= j; ++i) col[i] += col2[i];
       const double hn = sqrt(col[63]);
+      tend(h, TUSAS_T_ORTHO, to);
       if (!isfinite(hn)) return fail(h, TUSAS_ENONFINITE, "non-finite Krylov vector");
       for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
       H[(j + 1) * m + j] = hn;

@@ -229,7 +229,7 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
 #pragma unroll
     for (int d = 0; d < DIM; ++d) o.fu[d] = fma(Dq, g[d], jn * p[d]);
   }
-  if (!LIN) return;
+  if constexpr (LIN) {
   // ---- pointwise Jacobian -------------------------------------------------
   double ap[DIM];  // da/dp_i = 16 eps n_i (n_i^2 - sn) / |p|
 #pragma unroll
@@ -272,6 +272,7 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
     L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                                        // kappa2
 #pragma unroll
     for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];                                      // nvec
+  }
   }
 }
 

@@ -52,6 +52,9 @@ cudaError_t multidot(i64 n, int k, const double* X, i64 ld, const double* y, dou
 // != nullptr, accum_c[j] += c[j] as well.
 cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* accum_c,
                        cudaStream_t st);
+// y -= sum_j c[j] X_j fused with the deterministic norm: *out_norm2 = ||y||^2
+cudaError_t multi_axpy_norm(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* partials,
+                            double* out_norm2, cudaStream_t st);
 // x = sum_j c[j] X_j + x (c on host memory passed by value through a device array)
 cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st);
 

@@ -265,7 +265,11 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __
 #pragma unroll
     for (int o = 0; o < NS; ++o) {
       const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
-      s += __ldg(st + o * m.nn + node) * __ldg(x + node + ox + sy * oy + sz * oz);
+      const i64 off = ox + sy * oy + sz * oz;
+      // symmetric operator: a backward entry A(i, i+o) is read as A(i+o, i), the neighbour's
+      // forward entry, so only the 14 forward / centre coefficient arrays are streamed
+      const T a = o < NS / 2 ? __ldg(st + (NS - 1 - o) * m.nn + node + off) : __ldg(st + o * m.nn + node);
+      s += a * __ldg(x + node + off);
     }
   } else {
 #pragma unroll
@@ -273,7 +277,9 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __
       const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
       const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
       if (jx < 0 || jx >= m.nnx || jy < 0 || jy >= m.nny || jz < 0 || jz >= m.nnz) continue;
-      s += st[o * m.nn + node] * x[node + ox + sy * oy + sz * oz];
+      const i64 off = ox + sy * oy + sz * oz;
+      const T a = o < NS / 2 ? st[(NS - 1 - o) * m.nn + node + off] : st[o * m.nn + node];
+      s += a * x[node + off];
     }
   }
   return s;

@@ -41,8 +41,13 @@ __device__ __forceinline__ double gp_last_coord(const DevMesh& m, int e_last, in
   return org + m.h * (e_last + off);
 }
 
+template <int MODE>
+struct MinBlocks {
+  static const int V = MODE == 2 ? 4 : (MODE == 3 ? 3 : 2);  // tangent: 4 CTAs / SM, adjoint: 3
+};
+
 template <int DIM, int MODEL, int MODE>
-__global__ void __launch_bounds__(Tile<DIM>::X * Tile<DIM>::Y * Tile<DIM>::Z)
+__global__ void __launch_bounds__(Tile<DIM>::X * Tile<DIM>::Y * Tile<DIM>::Z, MinBlocks<MODE>::V)
 elem_kernel(const ElemArgs A) {
   constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
   constexpr int NX = TX + 1, NY = TY + 1, NZ = DIM == 3 ? TZ + 1 : 1;

@@ -237,6 +237,58 @@ cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, d
   return cudaGetLastError();
 }
 
+// y -= sum_j c[j] X_j and out_norm2 = ||y||^2 (after the update), deterministic.
+template <int KM>
+__global__ void __launch_bounds__(VT) k_multi_axpy_norm(i64 n, int k, const double* __restrict__ X, i64 ld,
+                                                        const double* __restrict__ c, double* __restrict__ y,
+                                                        double* __restrict__ partials) {
+  __shared__ double red[VT / 32];
+  double cc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) cc[j] = j < k ? -c[j] : 0.0;
+  const i64 chunk = (n + gridDim.x - 1) / gridDim.x;
+  const i64 lo = blockIdx.x * chunk;
+  const i64 hi = lo + chunk < n ? lo + chunk : n;
+  double acc = 0.0;
+  for (i64 i = lo + threadIdx.x; i < hi; i += VT) {
+    double v = y[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) v = fma(cc[j], X[j * ld + i], v);
+    y[i] = v;
+    acc = fma(v, v, acc);
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < VT / 32; ++w) s += red[w];
+    partials[blockIdx.x] = s;
+  }
+}
+
+cudaError_t multi_axpy_norm(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* partials,
+                            double* out_norm2, cudaStream_t st) {
+  if (k < 1 || k > 32) return cudaErrorInvalidValue;
+  const int nb = 148 * 8;  // one partial per block; partials holds RB * 32 >= nb doubles
+  if (k <= 4) {
+    k_multi_axpy_norm<4><<<nb, VT, 0, st>>>(n, k, X, ld, c, y, partials);
+  } else if (k <= 8) {
+    k_multi_axpy_norm<8><<<nb, VT, 0, st>>>(n, k, X, ld, c, y, partials);
+  } else if (k <= 16) {
+    k_multi_axpy_norm<16><<<nb, VT, 0, st>>>(n, k, X, ld, c, y, partials);
+  } else {
+    k_multi_axpy_norm<32><<<nb, VT, 0, st>>>(n, k, X, ld, c, y, partials);
+  }
+  count_launches(1);
+  k_reduce_partials<<<1, 32, 0, st>>>(nb, 1, 1, partials, out_norm2);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st) {
   return multi_axpy_sign(n, k, X, ld, c, 1.0, x, st);
 }

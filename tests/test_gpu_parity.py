@@ -200,3 +200,20 @@ def test_error_codes():
     with pytest.raises(pkg.TusasError) as e:
         h2.step()
     assert e.value.code == pkg.ENOCONV
+
+
+def test_dendrite2d_128_ten_steps_match_oracle():
+    """The 128^2 pure-metal workload, all 10 backward-Euler steps (FD-JFNK, point Jacobi)."""
+    w = synth.workload("dendrite2d_128")
+    U0 = synth.initial_state(w)
+    h = handle(w.mesh, w.params)
+    h.set_state(dev(U0), 0.0, w.dt)
+    Uo, t = U0.copy(), 0.0
+    out = dev(np.zeros_like(U0))
+    for _ in range(w.steps):
+        st = h.step()
+        assert st["converged"]
+        Uo, ratio = OS.newton_direct(w.mesh, w.params, Uo, t, w.dt)
+        assert ratio < 1e-12
+        t += w.dt
+    assert rel(host(h.get_state(out)), Uo) <= 1e-8
