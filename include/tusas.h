@@ -53,7 +53,10 @@ typedef struct tusas_params {
   int model;
   double W0, tau0, eps4, lam, D, k;
   double lT, Vp, zT;     /* frozen gradient G4 = (x_last - zT - Vp t)/lT, model 1, lT != 0 */
-  double theta;          /* must be 1 (backward Euler) */
+  double theta;          /* theta-method weight in [0, 1] (Eqs. dpf, dc): 1 backward Euler, 1/2 Crank-Nicolson */
+  int phihat_form;       /* theta < 1: phihat of the solute source and antitrapping current is
+                            1: (phi^{n+1} - phi^n)/dt (second order at theta = 1/2), or
+                            0: the estimate of Eq. (theta), theta (phi^{n+1}-phi^n)/dt + (1-theta)(phi^n-phi^{n-1})/dt */
   int jat_normalised;    /* 1: antitrapping along grad(phi)/|grad(phi)|, 0: along grad(phi) */
   int time_form;         /* 0: tau0 B a^2 (phi - phi^n)/dt; 1: tau0 ([B a^2 phi]^{n+1} - [..]^n)/dt */
   int jvp_mode;          /* Newton-Krylov Jacobian action: 0 finite difference, 1 exact tangent */
@@ -102,13 +105,19 @@ long long tusas_ndofs(const tusas_handle* h);
  * Synchronises. */
 int tusas_set_state(tusas_handle* h, const double* U, double t, double dt);
 
+/* Set U^{n-1} (host or device pointer) for the Eq. (theta) estimate
+ * (theta < 1, phihat_form 0). tusas_set_state resets it to U^n; tusas_step
+ * shifts it. Synchronises. */
+int tusas_set_history(tusas_handle* h, const double* Unm1);
+
 /* Copy the current state into U (host or device pointer). Synchronises. */
 int tusas_get_state(tusas_handle* h, double* U);
 
 /* Current time t^n of the state. */
 double tusas_time(const tusas_handle* h);
 
-/* F(U) of Eqs. (pf2)/(conc2) at theta = 1 with the stored U^n, t^n, dt:
+/* F(U) of Eqs. (pf2)/(conc2) with the theta-method of Eqs. (dpf)/(dc) and the
+ * stored U^n (and U^{n-1}), t^n, dt:
  * Galerkin residual on the Q1 mesh with the 2^dim-point Gauss rule. U and F
  * are device vectors (may not alias). Deterministic: bitwise identical on
  * repeated calls. */
@@ -127,10 +136,10 @@ int tusas_jvp_fd(tusas_handle* h, const double* U, const double* v, double* Jv);
 int tusas_jtvp(tusas_handle* h, const double* U, const double* w, double* JTw);
 
 /* (dF/dU^n)^T w at U, with the stored U^n: the coupling of consecutive time
- * steps in a discrete adjoint. */
+ * steps in a discrete adjoint. theta = 1 only (TUSAS_EINVAL otherwise). */
 int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* out);
 
-/* dF/dp at U for parameter `which` (0 = eps4, the anisotropy of Eq. gs). */
+/* dF/dp at U for parameter `which` (0 = eps4, the anisotropy of Eq. gs); theta = 1 only. */
 int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF);
 
 /* Build the preconditioner of Eq. (pre) (blocks of Eqs. pref2 / preconc2)

@@ -28,8 +28,8 @@ from .residual import element_residual, gather, residual
 H_CS = 1e-30
 
 
-def jvp(mesh, prm, U, Un, t_n, dt, v):
-    return residual(mesh, prm, U + 1j * H_CS * v, Un, t_n, dt).imag / H_CS
+def jvp(mesh, prm, U, Un, t_n, dt, v, Unm1=None):
+    return residual(mesh, prm, U + 1j * H_CS * v, Un, t_n, dt, Unm1=Unm1).imag / H_CS
 
 
 def dF_deps4(mesh, prm, U, Un, t_n, dt):
@@ -37,7 +37,7 @@ def dF_deps4(mesh, prm, U, Un, t_n, dt):
     return residual(mesh, p, U.astype(complex), Un, t_n, dt).imag / H_CS
 
 
-def element_jacobians(mesh, prm, U, Un, t_n, dt, elems=None, wrt_prev=False):
+def element_jacobians(mesh, prm, U, Un, t_n, dt, elems=None, wrt_prev=False, Unm1=None):
     """dRe/dUe per element: (E, 2, 2^d, 2, 2^d) indexed [field_i, a, field_j, b].
 
     With ``wrt_prev`` the derivative is taken with respect to U^n instead of U.
@@ -47,6 +47,7 @@ def element_jacobians(mesh, prm, U, Un, t_n, dt, elems=None, wrt_prev=False):
     conn = fem.connectivity(mesh, elems)
     phi_e, u_e = gather(mesh, U, conn)
     phin_e, un_e = gather(mesh, Un, conn)
+    pm1_e = gather(mesh, Unm1, conn)[0] if Unm1 is not None else None
     E, nl = conn.shape
     Je = np.zeros((E, 2, nl, 2, nl))
     for fj in range(2):
@@ -56,14 +57,14 @@ def element_jacobians(mesh, prm, U, Un, t_n, dt, elems=None, wrt_prev=False):
             args = [phi_e.astype(complex), u_e.astype(complex), phin_e.astype(complex), un_e.astype(complex)]
             idx = fj + (2 if wrt_prev else 0)
             args[idx] = args[idx] + pert
-            c = element_residual(mesh, prm, elems, *args, t_n, dt)
+            c = element_residual(mesh, prm, elems, *args, t_n, dt, None, pm1_e)
             Je[:, :, :, fj, b] = c.imag / H_CS
     return Je, conn
 
 
-def sparse_jacobian(mesh, prm, U, Un, t_n, dt, wrt_prev=False):
+def sparse_jacobian(mesh, prm, U, Un, t_n, dt, wrt_prev=False, Unm1=None):
     n = mesh.n_nodes
-    Je, conn = element_jacobians(mesh, prm, U, Un, t_n, dt, wrt_prev=wrt_prev)
+    Je, conn = element_jacobians(mesh, prm, U, Un, t_n, dt, wrt_prev=wrt_prev, Unm1=Unm1)
     E, nl = conn.shape
     rows = np.empty((E, 2, nl, 2, nl), dtype=np.int64)
     cols = np.empty_like(rows)
@@ -77,10 +78,10 @@ def sparse_jacobian(mesh, prm, U, Un, t_n, dt, wrt_prev=False):
     return J.tocsr()
 
 
-def jtvp(mesh, prm, U, Un, t_n, dt, w, wrt_prev=False):
+def jtvp(mesh, prm, U, Un, t_n, dt, w, wrt_prev=False, Unm1=None):
     """(dF/dU)^T w, or (dF/dU^n)^T w with ``wrt_prev``, summed element by element."""
     n = mesh.n_nodes
-    Je, conn = element_jacobians(mesh, prm, U, Un, t_n, dt, wrt_prev=wrt_prev)
+    Je, conn = element_jacobians(mesh, prm, U, Un, t_n, dt, wrt_prev=wrt_prev, Unm1=Unm1)
     we = np.stack([w[:n][conn], w[n:][conn]], axis=1)  # (E, 2, nl)
     contrib = np.einsum("eiajb,eia->ejb", Je, we)
     out = np.zeros(2 * n)

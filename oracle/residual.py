@@ -1,9 +1,9 @@
 """Discrete residual F(U) of the coupled phase-field / solute (or temperature) system.
 
 Follows Sec. 4.2, Eqs. (pf2), (lambda), (directional), (conc2), (jat), with the
-four-fold anisotropy of Eq. (gs) and the theta-method of Eqs. (dpf)/(theta) at
-theta = 1 (backward Euler), in Karma-Rappel units W0 = tau0 = 1 (Sec. 4.2, the
-nondimensionalisation paragraph). The pure metal is the same system with k = 1,
+four-fold anisotropy of Eq. (gs) and the theta-method of Eqs. (dpf)/(dc)/(theta)
+(theta = 1 backward Euler, 1/2 Crank-Nicolson), in Karma-Rappel units
+W0 = tau0 = 1 (Sec. 4.2, the nondimensionalisation paragraph). The pure metal is the same system with k = 1,
 mobility q = 1, no antitrapping current and no frozen gradient (Karma-Rappel
 phi + dimensionless temperature u).
 
@@ -19,6 +19,19 @@ phihat = (phi - phi^n)/dt, B(u) = 1 + (1-k) u:
            j = W0 B(u) phihat p/|p| / (2 sqrt 2)  (alloy only)
 
 and R_{phi,i} = sum_e sum_g w (s_phi psi_i + f_phi . grad psi_i), likewise R_u.
+
+theta-method (Eqs. dpf, dc, theta): the time terms are evaluated as above
+with (phi^{n+1} - phi^n)/dt; the bulk term and the fluxes D q(phi) grad u and
+f_phi are weighted theta at level n+1 plus (1 - theta) at level n (G4 at the
+level's own time). phihat in the antitrapping current and in the solute
+source: ``phihat_form`` 1 (default), (phi^{n+1} - phi^n)/dt; ``phihat_form`` 0,
+the estimate printed as Eq. (theta),
+  phihat = theta (phi^{n+1} - phi^n)/dt + (1 - theta)(phi^n - phi^{n-1})/dt,
+with phi^{n-1} = phi^n when no earlier level exists. Eq. (theta)'s estimate is
+centred at t^n, so with it theta = 1/2 is only first order in time (pinned),
+while Sec. 4.1.2 reports second order for Crank-Nicolson; form 1 gives second
+order. The antitrapping current and the source take u, grad phi at n+1, as
+printed in Eq. (conc2).
 Readings of garbled or ambiguous passages (switchable where marked):
 
 * anisotropic flux: the variational derivative of the gradient energy with
@@ -69,27 +82,45 @@ def anisotropy(prm, p):
     return a, dadp, q, guard
 
 
-def pointwise(prm, dt, phi, u, p, g, phin, un, G4, pn=None):
-    """Gauss-point integrands (s_phi, f_phi[dim], s_u, f_u[dim])."""
-    k = prm.k
+def spatial(prm, phi, u, p, g, G4):
+    """Level-wise spatial integrands: bulk source (psi part of R_phi), f_phi, D q(phi) grad u."""
     a, dadp, q, guard = anisotropy(prm, p)
     W2 = prm.W0 * prm.W0
     f_phi = [W2 * (a * a * pi + q * a * di) for pi, di in zip(p, dadp)]
-    phihat = (phi - phin) / dt
+    bulk = phi - phi ** 3 - prm.lam * (1.0 - phi * phi) ** 2 * (u + G4)
+    mob = prm.D * (1.0 - phi) / 2.0 if prm.model == 1 else prm.D + 0.0 * phi
+    return -bulk, f_phi, [mob * gi for gi in g], (a, q, guard)
+
+
+def pointwise(prm, dt, phi, u, p, g, phin, un, G4, pn=None, old=None, phihat_old=None):
+    """Gauss-point integrands (s_phi, f_phi[dim], s_u, f_u[dim]).
+
+    ``old`` = (phi^n, u^n, grad phi^n, grad u^n, G4^n) and ``phihat_old`` =
+    (phi^n - phi^{n-1})/dt enter only when theta < 1.
+    """
+    k = prm.k
+    th = prm.theta
+    sb, f_phi, f_diff, (a, q, guard) = spatial(prm, phi, u, p, g, G4)
+    dphidt = (phi - phin) / dt
+    phihat = dphidt if (th == 1.0 or prm.phihat_form == 1) else th * dphidt + (1.0 - th) * phihat_old
     B = 1.0 + (1.0 - k) * u
     if prm.time_form == 0:
-        time_phi = prm.tau0 * B * a * a * phihat
+        time_phi = prm.tau0 * B * a * a * dphidt
     else:
         an, _, _, _ = anisotropy(prm, pn)
         Bn = 1.0 + (1.0 - k) * un
         time_phi = prm.tau0 * (B * a * a * phi - Bn * an * an * phin) / dt
-    bulk = phi - phi ** 3 - prm.lam * (1.0 - phi * phi) ** 2 * (u + G4)
-    s_phi = time_phi - bulk
+    s_phi = time_phi + th * sb
+    f_phi = [th * fi for fi in f_phi]
+    f_u = [th * fi for fi in f_diff]
+    if th != 1.0:
+        sbo, fpo, fdo, _ = spatial(prm, *old)
+        s_phi = s_phi + (1.0 - th) * sbo
+        f_phi = [fi + (1.0 - th) * fo for fi, fo in zip(f_phi, fpo)]
+        f_u = [fi + (1.0 - th) * fo for fi, fo in zip(f_u, fdo)]
     A = ((1.0 + k) - (1.0 - k) * phin) / 2.0
     s_u = A * (u - un) / dt - 0.5 * phihat * B
     if prm.model == 1:
-        mob = prm.D * (1.0 - phi) / 2.0
-        f_u = [mob * gi for gi in g]
         c = INV_2SQRT2 * prm.W0 * B * phihat
         if prm.jat_normalised:
             qs = np.where(guard, 1.0, q)
@@ -97,8 +128,6 @@ def pointwise(prm, dt, phi, u, p, g, phin, un, G4, pn=None):
             f_u = [fi + c * pi * inv for fi, pi in zip(f_u, p)]
         else:
             f_u = [fi + c * pi for fi, pi in zip(f_u, p)]
-    else:
-        f_u = [prm.D * gi for gi in g]
     return s_phi, f_phi, s_u, f_u
 
 
@@ -109,12 +138,13 @@ def frozen_gradient(prm, xlast, t_new):
     return 0.0 * xlast
 
 
-def element_residual(mesh, prm, elems, phi_e, u_e, phin_e, un_e, t_n, dt, source=None):
+def element_residual(mesh, prm, elems, phi_e, u_e, phin_e, un_e, t_n, dt, source=None, phinm1_e=None):
     """Element contributions (E, 2, 2^dim): [:,0] to R_phi, [:,1] to R_u.
 
     ``phi_e`` etc. are nodal values per element (E, 2^dim); ``elems`` the
     per-axis element indices (dim, E). ``source(xs) -> (S_phi, S_u)`` is an
     optional manufactured-solution source subtracted as (S, psi_i).
+    ``phinm1_e``: phi^{n-1} per element (theta < 1; default phi^n).
     """
     dim, h = mesh.dim, mesh.h
     t_new = t_n + dt
@@ -130,10 +160,17 @@ def element_residual(mesh, prm, elems, phi_e, u_e, phin_e, un_e, t_n, dt, source
         un = un_e @ N
         p = [phi_e @ G[d] for d in range(dim)]
         g = [u_e @ G[d] for d in range(dim)]
-        pn = [phin_e @ G[d] for d in range(dim)] if prm.time_form == 1 else None
+        need_pn = prm.time_form == 1 or prm.theta != 1.0
+        pn = [phin_e @ G[d] for d in range(dim)] if need_pn else None
         xs = [origin[d] + (elems[d] + xi[d]) * h for d in range(dim)]
         G4 = frozen_gradient(prm, xs[-1], t_new)
-        s_phi, f_phi, s_u, f_u = pointwise(prm, dt, phi, u, p, g, phin, un, G4, pn)
+        old = phihat_old = None
+        if prm.theta != 1.0:
+            gn = [un_e @ G[d] for d in range(dim)]
+            old = (phin, un, pn, gn, frozen_gradient(prm, xs[-1], t_n))
+            pm1 = phin_e if phinm1_e is None else phinm1_e
+            phihat_old = (phin - pm1 @ N) / dt
+        s_phi, f_phi, s_u, f_u = pointwise(prm, dt, phi, u, p, g, phin, un, G4, pn, old, phihat_old)
         if source is not None:
             S_phi, S_u = source(xs)
             s_phi = s_phi - S_phi
@@ -148,8 +185,10 @@ def gather(mesh, U, conn):
     return U[:n][conn], U[n:][conn]
 
 
-def residual(mesh, prm, U, Un, t_n, dt, source=None, chunk=1 << 18):
-    """Global residual F(U) (2 N_nodes,), field-major [R_phi ; R_u]; t_n is the time of U^n."""
+def residual(mesh, prm, U, Un, t_n, dt, source=None, chunk=1 << 18, Unm1=None):
+    """Global residual F(U) (2 N_nodes,), field-major [R_phi ; R_u]; t_n is the time of U^n.
+
+    ``Unm1`` is U^{n-1} (theta < 1 only; default U^n)."""
     n = mesh.n_nodes
     dtype = np.result_type(U, Un, prm.eps4)
     F = np.zeros(2 * n, dtype=dtype)
@@ -160,7 +199,8 @@ def residual(mesh, prm, U, Un, t_n, dt, source=None, chunk=1 << 18):
         conn = fem.connectivity(mesh, elems)
         phi_e, u_e = gather(mesh, U, conn)
         phin_e, un_e = gather(mesh, Un, conn)
-        c = element_residual(mesh, prm, elems, phi_e, u_e, phin_e, un_e, t_n, dt, source)
+        pm1_e = gather(mesh, Unm1, conn)[0] if Unm1 is not None else None
+        c = element_residual(mesh, prm, elems, phi_e, u_e, phin_e, un_e, t_n, dt, source, pm1_e)
         F[:n] += fem.scatter_add(n, conn, c[:, 0, :])
         F[n:] += fem.scatter_add(n, conn, c[:, 1, :])
     return F

@@ -116,11 +116,11 @@ def fd_step(unorm, vnorm):
     return math.sqrt((1.0 + unorm) * EPS_MACH) / vnorm
 
 
-def newton_step(mesh, prm, Un, t_n, dt, U0=None, exact=None):
-    """Solve F(U; U^n) = 0 by JFNK starting from U0 (default U^n). Returns (U, stats)."""
+def newton_step(mesh, prm, Un, t_n, dt, U0=None, exact=None, Unm1=None):
+    """Solve F(U; U^n[, U^{n-1}]) = 0 by JFNK starting from U0 (default U^n). Returns (U, stats)."""
     U = (Un if U0 is None else U0).copy()
     exact = bool(prm.jvp_mode) if exact is None else exact
-    F = residual(mesh, prm, U, Un, t_n, dt)
+    F = residual(mesh, prm, U, Un, t_n, dt, Unm1=Unm1)
     st = StepStats(residual_evals=1)
     st.fnorm0 = st.fnorm = np.linalg.norm(F)
     tol = prm.newton_rtol * st.fnorm0 + prm.newton_atol
@@ -136,7 +136,7 @@ def newton_step(mesh, prm, Un, t_n, dt, U0=None, exact=None):
         M = precond.Preconditioner(mesh, prm, U, Un, dt)
         if exact:
             def mv(v, U=U):
-                return jacobian.jvp(mesh, prm, U, Un, t_n, dt, v)
+                return jacobian.jvp(mesh, prm, U, Un, t_n, dt, v, Unm1=Unm1)
         else:
             unorm = np.linalg.norm(U)
 
@@ -145,7 +145,7 @@ def newton_step(mesh, prm, Un, t_n, dt, U0=None, exact=None):
                 if vn == 0.0:
                     return np.zeros_like(v)
                 e = fd_step(unorm, vn)
-                return (residual(mesh, prm, U + e * v, Un, t_n, dt) - F) / e
+                return (residual(mesh, prm, U + e * v, Un, t_n, dt, Unm1=Unm1) - F) / e
         dU, its, _ = gmres(mv, M.apply, -F, eta * st.fnorm, prm.gmres_restart, prm.gmres_maxit)
         st.gmres_its += its
         st.gmres_per_newton.append(its)
@@ -153,7 +153,7 @@ def newton_step(mesh, prm, Un, t_n, dt, U0=None, exact=None):
         accepted = False
         for _ in range(prm.linesearch_max + 1):
             Ut = U + lam * dU
-            Ft = residual(mesh, prm, Ut, Un, t_n, dt)
+            Ft = residual(mesh, prm, Ut, Un, t_n, dt, Unm1=Unm1)
             st.residual_evals += 1
             if np.linalg.norm(Ft) <= st.fnorm:
                 accepted = True
@@ -170,23 +170,23 @@ def newton_step(mesh, prm, Un, t_n, dt, U0=None, exact=None):
     return U, st
 
 
-def newton_direct(mesh, prm, Un, t_n, dt, U0=None, rtol=1e-13, maxit=30, source=None):
+def newton_direct(mesh, prm, Un, t_n, dt, U0=None, rtol=1e-13, maxit=30, source=None, Unm1=None):
     """Newton with a sparse LU of the complex-step Jacobian; reference solution of F = 0.
 
     Returns (U, ||F||/||F0||). Backtracking as in Eq. (glob) guards the first steps.
     """
     U = (Un if U0 is None else U0).copy()
-    F = residual(mesh, prm, U, Un, t_n, dt, source=source)
+    F = residual(mesh, prm, U, Un, t_n, dt, source=source, Unm1=Unm1)
     f0 = np.linalg.norm(F)
     fn = f0
     for _ in range(maxit):
         if fn <= rtol * f0 or fn == 0.0:
             break
-        J = jacobian.sparse_jacobian(mesh, prm, U, Un, t_n, dt)
+        J = jacobian.sparse_jacobian(mesh, prm, U, Un, t_n, dt, Unm1=Unm1)
         dU = spla.spsolve(J.tocsc(), -F)
         lam = 1.0
         for _ in range(30):
-            Ft = residual(mesh, prm, U + lam * dU, Un, t_n, dt, source=source)
+            Ft = residual(mesh, prm, U + lam * dU, Un, t_n, dt, source=source, Unm1=Unm1)
             if np.linalg.norm(Ft) <= fn:
                 break
             lam *= 0.5
@@ -197,16 +197,18 @@ def newton_direct(mesh, prm, Un, t_n, dt, U0=None, rtol=1e-13, maxit=30, source=
 
 
 def run_steps(mesh, prm, U0, dt, nsteps, t0=0.0, direct=False):
-    """nsteps backward-Euler steps; returns (U_final, per-step stats or residual ratios)."""
+    """nsteps theta-method steps (U^{-1} = U^0); returns (U_final, per-step stats or residual ratios)."""
     U = U0.copy()
+    Uprev = U0.copy()
     t = t0
     hist = []
     for _ in range(nsteps):
         if direct:
-            U, ratio = newton_direct(mesh, prm, U, t, dt)
+            Unew, ratio = newton_direct(mesh, prm, U, t, dt, Unm1=Uprev)
             hist.append(ratio)
         else:
-            U, st = newton_step(mesh, prm, U, t, dt)
+            Unew, st = newton_step(mesh, prm, U, t, dt, Unm1=Uprev)
             hist.append(st)
+        Uprev, U = U, Unew
         t += dt
     return U, hist

@@ -19,7 +19,7 @@ ERROR_NAMES = {EINVAL: "TUSAS_EINVAL", ECUDA: "TUSAS_ECUDA", ENOMEM: "TUSAS_ENOM
                ENOCONV: "TUSAS_ENOCONV", ENONFINITE: "TUSAS_ENONFINITE"}
 
 EXPORTS = ["tusas_create", "tusas_destroy", "tusas_set_stream", "tusas_set_params", "tusas_ndofs",
-           "tusas_set_state", "tusas_get_state", "tusas_time", "tusas_residual", "tusas_jvp",
+           "tusas_set_state", "tusas_set_history", "tusas_get_state", "tusas_time", "tusas_residual", "tusas_jvp",
            "tusas_jvp_fd", "tusas_jtvp", "tusas_jtvp_prev", "tusas_dFdp", "tusas_precond_setup",
            "tusas_precond_apply", "tusas_step", "tusas_dot", "tusas_last_error", "tusas_timers",
            "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak", "tusas_forward", "tusas_adjoint", "tusas_multidot_noalloc"]
@@ -37,7 +37,7 @@ _PARAM_FIELDS = [
     ("W0", ctypes.c_double), ("tau0", ctypes.c_double), ("eps4", ctypes.c_double), ("lam", ctypes.c_double),
     ("D", ctypes.c_double), ("k", ctypes.c_double),
     ("lT", ctypes.c_double), ("Vp", ctypes.c_double), ("zT", ctypes.c_double),
-    ("theta", ctypes.c_double),
+    ("theta", ctypes.c_double), ("phihat_form", ctypes.c_int),
     ("jat_normalised", ctypes.c_int), ("time_form", ctypes.c_int),
     ("jvp_mode", ctypes.c_int), ("precond", ctypes.c_int), ("smoother_fp32", ctypes.c_int),
     ("gmres_restart", ctypes.c_int), ("gmres_maxit", ctypes.c_int), ("newton_maxit", ctypes.c_int),
@@ -78,6 +78,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tusas_ndofs": ([vp], i64),
         "tusas_set_state": ([vp, dp, ctypes.c_double, ctypes.c_double], ctypes.c_int),
         "tusas_get_state": ([vp, dp], ctypes.c_int),
+        "tusas_set_history": ([vp, dp], ctypes.c_int),
         "tusas_time": ([vp], ctypes.c_double),
         "tusas_residual": ([vp, dp, dp], ctypes.c_int),
         "tusas_jvp": ([vp, dp, dp, dp], ctypes.c_int),
@@ -226,6 +227,9 @@ class Tusas:
 
     def set_state(self, U, t, dt):
         self._check(self._lib.tusas_set_state(self._h, _ptr(U), float(t), float(dt)))
+
+    def set_history(self, Unm1):
+        self._check(self._lib.tusas_set_history(self._h, _ptr(Unm1)))
 
     def get_state(self, out):
         self._check(self._lib.tusas_get_state(self._h, _ptr(out)))

@@ -51,6 +51,10 @@ struct tusas_handle {
   double* Ufinal = nullptr;
   int fw_steps = 0, fw_every = 0;
   double fw_t0 = 0.0, fw_dt = 0.0;
+  // theta-method: U^{n-1}, the (1 - theta)-weighted level-n spatial vector and the
+  // nodal (phi^n - phi^{n-1})/dt of the Eq. (theta) estimate
+  double *Unm1 = nullptr, *Fold = nullptr, *phold = nullptr;
+  bool old_valid = false;
 };
 
 namespace {
@@ -129,8 +133,8 @@ int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
     why = "the pure-metal model needs k = 1";
     return TUSAS_EINVAL;
   }
-  if (p->theta != 1.0) {
-    why = "only theta = 1 (backward Euler) is implemented";
+  if (!(p->theta >= 0.0 && p->theta <= 1.0) || (p->phihat_form != 0 && p->phihat_form != 1)) {
+    why = "theta must be in [0, 1], phihat_form 0 or 1";
     return TUSAS_EINVAL;
   }
   if (!(p->W0 > 0) || !(p->tau0 > 0) || !(p->D >= 0) || !(p->eps4 >= 0 && p->eps4 < 0.25)) {
@@ -177,8 +181,29 @@ void fill_phys(tusas_handle* h) {
   P.idt = h->dt > 0 ? 1.0 / h->dt : 0.0;
   P.t_new = h->t + h->dt;
   P.has_g4 = p.model == 1 && p.lT != 0.0;
+  P.theta = p.theta;
+  P.thW2 = p.theta * p.W0 * p.W0;
+  P.thD = p.theta * p.D;
+  P.phihat_old = (p.theta != 1.0 && p.phihat_form == 0) ? 1 : 0;
+  P.dphat = P.phihat_old ? p.theta * P.idt : P.idt;
   tusas::elem_ctx_init(h->ec, h->dm, P);
+  h->old_valid = false;
 }
+
+// Level-n quantities of the theta-method for the current state (once per state / dt).
+int ensure_old(tusas_handle* h) {
+  if (h->prm.theta == 1.0 || h->old_valid) return TUSAS_OK;
+  TCK(tusas::elem_run(tusas::M_OLD, h->ec, h->Un, h->Un, nullptr, h->Fold, nullptr, h->st));
+  if (h->ec.P.phihat_old) {
+    TCK(tusas::vxpay(h->nn, h->Un, -1.0, nullptr, h->Unm1, h->phold, h->st));
+    TCK(tusas::vscal(h->nn, h->ec.P.idt, h->phold, h->st));
+  }
+  h->old_valid = true;
+  return TUSAS_OK;
+}
+
+const double* old_init(tusas_handle* h) { return h->prm.theta == 1.0 ? nullptr : h->Fold; }
+const double* old_ph(tusas_handle* h) { return h->ec.P.phihat_old ? h->phold : nullptr; }
 
 int ensure_lin(tusas_handle* h, bool trial) {
   if (!h->lin) {
@@ -227,7 +252,7 @@ int fd_jv(tusas_handle* h, const double* U, const double* F0, const double* v, d
   k_fd_eps<<<1, 1, 0, h->st>>>(h->sc + 210, h->sc + 211, h->sc + 212);
   tusas::count_launches(1);
   TCK(tusas::vxpay(h->N, U, 0.0, h->sc + 212, v, h->tmp2, h->st));
-  TCK(tusas::elem_run(tusas::M_RES, h->ec, h->tmp2, h->Un, nullptr, Jv, nullptr, h->st));
+  TCK(tusas::elem_run(tusas::M_RES, h->ec, h->tmp2, h->Un, nullptr, Jv, nullptr, h->st, old_init(h), old_ph(h)));
   TCK(tusas::vfdq(h->N, F0, Jv, h->sc + 213, h->st));
   return TUSAS_OK;
 }
@@ -263,7 +288,7 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   h->nn = d.nn;
   h->N = 2 * d.nn;
   fill_phys(h);
-  double** vecs[] = {&h->Un, &h->U, &h->F, &h->Ft, &h->dU, &h->Ut, &h->tmp, &h->tmp2};
+  double** vecs[] = {&h->Un, &h->U, &h->F, &h->Ft, &h->dU, &h->Ut, &h->tmp, &h->tmp2, &h->Unm1, &h->Fold, &h->phold};
   for (double** v : vecs) {
     cudaError_t e = cudaMalloc(v, sizeof(double) * h->N);
     if (e != cudaSuccess) {
@@ -296,7 +321,7 @@ void tusas_destroy(tusas_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   cudaDeviceSynchronize();
   double* vecs[] = {h->Un, h->U, h->F, h->Ft, h->dU, h->Ut, h->tmp, h->tmp2, h->lin, h->lin_t, h->V, h->Z,
-                    h->partials, h->sc};
+                    h->partials, h->sc, h->Unm1, h->Fold, h->phold};
   for (double* v : vecs)
     if (v) cudaFree(v);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
@@ -339,12 +364,23 @@ int tusas_set_state(tusas_handle* h, const double* U, double t, double dt) {
   if (!h || !U) return TUSAS_EINVAL;
   if (!(dt > 0) || !isfinite(dt) || !isfinite(t)) return fail(h, TUSAS_EINVAL, "dt must be positive, t finite");
   TCK(cudaMemcpyAsync(h->Un, U, sizeof(double) * h->N, cudaMemcpyDefault, h->st));
+  TCK(cudaMemcpyAsync(h->Unm1, h->Un, sizeof(double) * h->N, cudaMemcpyDeviceToDevice, h->st));
   TCK(cudaStreamSynchronize(h->st));
   h->t = t;
   h->dt = dt;
   h->have_state = true;
   h->pc_ready = false;
   fill_phys(h);
+  return TUSAS_OK;
+}
+
+int tusas_set_history(tusas_handle* h, const double* Unm1) {
+  int rc = ready(h);
+  if (rc) return rc;
+  if (!Unm1) return fail(h, TUSAS_EINVAL, "null vector");
+  TCK(cudaMemcpyAsync(h->Unm1, Unm1, sizeof(double) * h->N, cudaMemcpyDefault, h->st));
+  TCK(cudaStreamSynchronize(h->st));
+  h->old_valid = false;
   return TUSAS_OK;
 }
 
@@ -360,8 +396,9 @@ int tusas_residual(tusas_handle* h, const double* U, double* F) {
   int rc = ready(h);
   if (rc) return rc;
   if (!U || !F || U == F) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  if ((rc = ensure_old(h))) return rc;
   const size_t t0 = tbeg(h);
-  TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, F, nullptr, h->st));
+  TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, F, nullptr, h->st, old_init(h), old_ph(h)));
   tend(h, TUSAS_T_RESIDUAL, t0);
   return TUSAS_OK;
 }
@@ -372,8 +409,9 @@ int tusas_jvp(tusas_handle* h, const double* U, const double* v, double* Jv) {
   if (!U || !v || !Jv || Jv == U || Jv == v) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   rc = ensure_lin(h, false);
   if (rc) return rc;
+  if ((rc = ensure_old(h))) return rc;
   size_t t0 = tbeg(h);
-  TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st));
+  TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st, old_init(h), old_ph(h)));
   tend(h, TUSAS_T_RESIDUAL_LIN, t0);
   t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_JV, h->ec, nullptr, nullptr, v, Jv, h->lin, h->st));
@@ -385,7 +423,8 @@ int tusas_jvp_fd(tusas_handle* h, const double* U, const double* v, double* Jv) 
   int rc = ready(h);
   if (rc) return rc;
   if (!U || !v || !Jv || Jv == U || Jv == v) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
-  TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, h->tmp, nullptr, h->st));
+  if ((rc = ensure_old(h))) return rc;
+  TCK(tusas::elem_run(tusas::M_RES, h->ec, U, h->Un, nullptr, h->tmp, nullptr, h->st, old_init(h), old_ph(h)));
   TCK(norm2_dev(h, U, 210));
   return fd_jv(h, U, h->tmp, v, Jv);
 }
@@ -396,8 +435,9 @@ int tusas_jtvp(tusas_handle* h, const double* U, const double* w, double* JTw) {
   if (!U || !w || !JTw || JTw == U || JTw == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   rc = ensure_lin(h, false);
   if (rc) return rc;
+  if ((rc = ensure_old(h))) return rc;
   size_t t0 = tbeg(h);
-  TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st));
+  TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, U, h->Un, nullptr, h->tmp, h->lin, h->st, old_init(h), old_ph(h)));
   tend(h, TUSAS_T_RESIDUAL_LIN, t0);
   t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_JTV, h->ec, nullptr, nullptr, w, JTw, h->lin, h->st));
@@ -409,6 +449,7 @@ int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* o
   int rc = ready(h);
   if (rc) return rc;
   if (!U || !w || !out || out == U || out == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
+  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "(dF/dU^n)^T w is implemented for theta = 1 only");
   const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_PREV_T, h->ec, U, h->Un, w, out, nullptr, h->st));
   tend(h, TUSAS_T_ADJOINT, t0);
@@ -420,6 +461,7 @@ int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF) {
   if (rc) return rc;
   if (!U || !dF || U == dF) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   if (which != 0) return fail(h, TUSAS_EINVAL, "only which = 0 (eps4) is available");
+  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "dF/dp is implemented for theta = 1 only");
   const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_DEPS, h->ec, U, h->Un, nullptr, dF, nullptr, h->st));
   tend(h, TUSAS_T_ADJOINT, t0);
@@ -632,8 +674,10 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     if (rc) return rc;
   }
   TCK(tusas::vcopy(N, h->Un, h->U, h->st));
+  if ((rc = ensure_old(h))) return rc;
   size_t t0 = tbeg(h);
-  TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->U, h->Un, nullptr, h->F, h->lin, h->st));
+  TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->U, h->Un, nullptr, h->F, h->lin, h->st,
+                      old_init(h), old_ph(h)));
   tend(h, exact ? TUSAS_T_RESIDUAL_LIN : TUSAS_T_RESIDUAL, t0);
   S.residual_evals = 1;
   double fn;
@@ -672,7 +716,7 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
       TCK(tusas::vxpay(N, h->U, lam, nullptr, h->dU, h->Ut, h->st));
       t0 = tbeg(h);
       TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t,
-                          h->st));
+                          h->st, old_init(h), old_ph(h)));
       tend(h, exact ? TUSAS_T_RESIDUAL_LIN : TUSAS_T_RESIDUAL, t0);
       S.residual_evals++;
       rc = host_norm(h, h->Ft, &ftn);
@@ -701,6 +745,7 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     tcollect(h);
   }
   if (!converged) return fail(h, TUSAS_ENOCONV, "Newton did not converge");
+  TCK(tusas::vcopy(N, h->Un, h->Unm1, h->st));
   TCK(tusas::vcopy(N, h->U, h->Un, h->st));
   TCK(cudaStreamSynchronize(h->st));
   h->t += h->dt;
@@ -739,6 +784,7 @@ int set_state_dev(tusas_handle* h, const double* U, double t) {
 extern "C" int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int nsteps, int ckpt_every,
                              tusas_stats* total) {
   if (!h || !U0 || nsteps < 1 || ckpt_every < 1) return fail(h, TUSAS_EINVAL, "bad forward arguments");
+  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "the discrete adjoint is implemented for theta = 1 only");
   int rc = tusas_set_state(h, U0, t0, dt);
   if (rc) return rc;
   const size_t nck = (size_t)(nsteps + ckpt_every - 1) / ckpt_every + 1;
@@ -781,6 +827,7 @@ extern "C" int tusas_adjoint(tusas_handle* h, const double* w, const double* d0,
                              double* g0, double adj_rtol, tusas_stats* stats) {
   if (!h || !w || !grad_eps4) return fail(h, TUSAS_EINVAL, "null argument");
   if (h->fw_steps < 1) return fail(h, TUSAS_EINVAL, "call tusas_forward first");
+  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "the discrete adjoint is implemented for theta = 1 only");
   if (!(adj_rtol > 0.0)) return fail(h, TUSAS_EINVAL, "adj_rtol must be positive");
   const int N = h->fw_steps, c = h->fw_every;
   const double t0 = h->fw_t0, dt = h->fw_dt;

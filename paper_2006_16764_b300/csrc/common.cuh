@@ -27,6 +27,11 @@ struct DevPhys {
   double dt, idt;        // time step and its reciprocal
   double t_new;          // t^{n+1}, used by the frozen gradient
   int has_g4;            // model 1 and lT != 0
+  // theta-method: spatial terms weighted theta at n+1 and (1 - theta) at n
+  double theta;
+  double thW2, thD;      // theta W0^2, theta D
+  double dphat;          // d phihat / d phi^{n+1}: 1/dt, or theta/dt with the Eq. (theta) estimate
+  int phihat_old;        // 1: phihat includes (1 - theta)(phi^n - phi^{n-1})/dt
 };
 
 // Tile shape of the element kernels: one thread per element.

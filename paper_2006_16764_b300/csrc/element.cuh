@@ -186,18 +186,18 @@ __host__ __device__ constexpr int sym_index(int i, int j) {
 // (c-th coefficient of this Gauss point; stride given by the caller's writer).
 template <int DIM, int MODEL, bool LIN>
 __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u, double dphi, double du,
-                                          const double* p, const double* g, const double* pn, double G4,
-                                          GPOut<DIM>& o, double* L) {
+                                          double phold, const double* p, const double* g, const double* pn,
+                                          double G4, GPOut<DIM>& o, double* L) {
   Aniso<DIM> A;
   A.eval(p, P.eps4);
   const double eps = P.eps4;
-  const double W2 = P.W0 * P.W0;
   const double c16 = 16.0 * eps;
-  // anisotropic flux f = W0^2 a p_i (a + 16 eps (n_i^2 - sn))
-  const double W2a = W2 * A.a;
+  // anisotropic flux f = theta W0^2 a p_i (a + 16 eps (n_i^2 - sn))
+  const double W2a = P.thW2 * A.a;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, A.n2[d] - A.sn, A.a);
-  const double phihat = dphi * P.idt;
+  const double dphidt = dphi * P.idt;  // time term
+  const double phihat = P.phihat_old ? fma(P.theta, dphidt, (1.0 - P.theta) * phold) : dphidt;  // source, j
   const double omk = 1.0 - P.k;
   const double B = fma(omk, u, 1.0);
   const double a2 = A.a * A.a;
@@ -207,7 +207,7 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
   double time;
   double an2 = 0.0, Bn = 0.0, phin = phi - dphi;
   if (P.time_form == 0) {
-    time = P.tau0 * B * a2 * phihat;
+    time = P.tau0 * B * a2 * dphidt;
   } else {
     Aniso<DIM> An;
     An.eval(pn, eps);
@@ -215,15 +215,15 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
     Bn = fma(omk, u - du, 1.0);
     time = P.tau0 * (B * a2 * phi - Bn * an2 * phin) * P.idt;
   }
-  o.sphi = time - (phi * om - P.lam * om * om * ug);
+  o.sphi = fma(-P.theta, phi * om - P.lam * om * om * ug, time);
   const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - omk * phin);
   o.su = Acoef * du * P.idt - 0.5 * phihat * B;
-  double Dq = P.D, jn = 0.0;
+  double Dq = P.thD, jn = 0.0;
   if (MODEL == 0) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o.fu[d] = P.D * g[d];
+    for (int d = 0; d < DIM; ++d) o.fu[d] = P.thD * g[d];
   } else {
-    Dq = 0.5 * P.D * (1.0 - phi);
+    Dq = 0.5 * P.thD * (1.0 - phi);
     const double cj = TUSAS_INV_2SQRT2 * P.W0 * B * phihat;
     jn = P.jat_norm ? cj * A.r : cj;
 #pragma unroll
@@ -235,13 +235,13 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
 #pragma unroll
   for (int d = 0; d < DIM; ++d) ap[d] = c16 * A.n[d] * (A.n2[d] - A.sn) * A.r;
   const double dbulk = (1.0 - 3.0 * phi2) + 4.0 * P.lam * phi * om * ug;
-  const double tfac = P.time_form == 0 ? phihat : phi * P.idt;  // multiplies d(B a^2)
-  L[0] = P.tau0 * B * a2 * P.idt - dbulk;                       // alpha_phi
-  L[1] = P.tau0 * omk * a2 * tfac + P.lam * om * om;            // alpha_u
+  const double tfac = P.time_form == 0 ? dphidt : phi * P.idt;  // multiplies d(B a^2)
+  L[0] = fma(-P.theta, dbulk, P.tau0 * B * a2 * P.idt);           // alpha_phi
+  L[1] = fma(P.theta * P.lam, om * om, P.tau0 * omk * a2 * tfac);  // alpha_u
   const double c2a = 2.0 * P.tau0 * B * tfac * A.a;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * ap[d];         // alpha_p
-  // H = W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn))
+  // H = theta W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn))
   //            + n_i n_j (32 eps a (sn - n_i^2 - n_j^2) + 256 eps^2 (n_i^2 - sn)(n_j^2 - sn)) ]
   const double e32a = 32.0 * eps * A.a, e256 = 256.0 * eps * eps, e16a = 16.0 * eps * A.a;
 #pragma unroll
@@ -251,12 +251,12 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
       const double mi = A.n2[i] - A.sn, mj = A.n2[j] - A.sn;
       double v = A.n[i] * A.n[j] * (e32a * (A.sn - A.n2[i] - A.n2[j]) + e256 * mi * mj);
       if (i == j) v += a2 + e16a * (3.0 * A.n2[i] - A.sn);
-      L[2 + DIM + sym_index<DIM>(i, j)] = W2 * v;
+      L[2 + DIM + sym_index<DIM>(i, j)] = P.thW2 * v;
     }
   }
   if (MODEL == 1) {
     constexpr int o0 = NLin<DIM, 1>::PHI;
-    L[o0 + 0] = -0.5 * B * P.idt;                    // beta_phi
+    L[o0 + 0] = -0.5 * B * P.dphat;                  // beta_phi
     L[o0 + 1] = Acoef * P.idt - 0.5 * phihat * omk;  // beta_u
     // direction of the antitrapping current and its derivative factors
     const double cw = TUSAS_INV_2SQRT2 * P.W0;
@@ -265,15 +265,35 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
     for (int d = 0; d < DIM; ++d) nv[d] = P.jat_norm ? A.n[d] : p[d];
     const double kap = P.jat_norm ? cw * B * phihat * A.r : cw * B * phihat;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(-0.5 * P.D, g[d], cw * B * P.idt * nv[d]);  // gamma_phi
-    L[o0 + 2 + DIM] = cw * omk * phihat;                                                             // c_u
-    L[o0 + 3 + DIM] = Dq;                                                                            // gamma_g
-    L[o0 + 4 + DIM] = kap;                                                                           // kappa1
-    L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                                        // kappa2
+    for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(-0.5 * P.thD, g[d], cw * B * P.dphat * nv[d]);  // gamma_phi
+    L[o0 + 2 + DIM] = cw * omk * phihat;                                                              // c_u
+    L[o0 + 3 + DIM] = Dq;                                                                             // gamma_g
+    L[o0 + 4 + DIM] = kap;                                                                            // kappa1
+    L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                                         // kappa2
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];                                      // nvec
+    for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];                                       // nvec
   }
   }
+}
+
+// Level-n spatial integrands weighted (1 - theta) (theta-method, Eqs. dpf / dc):
+// -(1-theta) bulk(phi^n, u^n, G4(t^n)), (1-theta) f_phi(grad phi^n), (1-theta) D q(phi^n) grad u^n.
+template <int DIM, int MODEL>
+__device__ __forceinline__ void spatial_old(const DevPhys& P, double phi, double u, const double* p, const double* g,
+                                            double G4, GPOut<DIM>& o) {
+  const double w = 1.0 - P.theta;
+  Aniso<DIM> A;
+  A.eval(p, P.eps4);
+  const double c16 = 16.0 * P.eps4;
+  const double W2a = w * P.W0 * P.W0 * A.a;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, A.n2[d] - A.sn, A.a);
+  const double om = 1.0 - phi * phi;
+  o.sphi = -w * (phi * om - P.lam * om * om * (u + G4));
+  o.su = 0.0;
+  const double Dq = MODEL == 0 ? w * P.D : 0.5 * w * P.D * (1.0 - phi);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) o.fu[d] = Dq * g[d];
 }
 
 // Apply the stored pointwise Jacobian (TRANS = false) or its transpose.
@@ -299,9 +319,9 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
 #pragma unroll
     for (int d = 0; d < DIM; ++d) o.fphi[d] = Hx[d];
     if (MODEL == 0) {
-      o.su = (x1 - 0.5 * x0) * P.idt;
+      o.su = fma(-0.5 * P.dphat, x0, x1 * P.idt);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) o.fu[d] = P.D * xg[d];
+      for (int d = 0; d < DIM; ++d) o.fu[d] = P.thD * xg[d];
     } else {
       constexpr int o0 = NLin<DIM, 1>::PHI;
       o.su = fma(L[o0], x0, L[o0 + 1] * x1);
@@ -320,10 +340,10 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
 #pragma unroll
     for (int d = 0; d < DIM; ++d) o.fphi[d] = fma(L[2 + d], x0, Hx[d]);
     if (MODEL == 0) {
-      s0 = fma(-0.5 * P.idt, x1, s0);
+      s0 = fma(-0.5 * P.dphat, x1, s0);
       s1 = fma(P.idt, x1, s1);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) o.fu[d] = P.D * xg[d];
+      for (int d = 0; d < DIM; ++d) o.fu[d] = P.thD * xg[d];
     } else {
       constexpr int o0 = NLin<DIM, 1>::PHI;
       const double* nv = L + o0 + 6 + DIM;

@@ -11,7 +11,7 @@ namespace tusas {
 void count_launches(long long n);
 long long launches();
 
-enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5 };
+enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5, M_OLD = 6 };
 
 struct ElemCtx {
   DevMesh m;
@@ -25,9 +25,10 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P);
 // Doubles of the linearisation store for this mesh / model.
 size_t elem_lin_doubles(const ElemCtx& c);
 // Element-tile pass: out = (mode-dependent) assembled vector; out is zeroed
-// first, then the 2^dim tile colours accumulate in a fixed order.
+// (or set to `init`) first, then the 2^dim tile colours accumulate in a fixed
+// order. `phold`: nodal (phi^n - phi^{n-1})/dt when the Eq. (theta) estimate is used.
 cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
-                     double* lin, cudaStream_t st);
+                     double* lin, cudaStream_t st, const double* init = nullptr, const double* phold = nullptr);
 
 // ---- FP64 vector kernels (deterministic) ----------------------------------
 // y = a*x + y

@@ -28,6 +28,7 @@ struct ElemArgs {
   const double* V;
   double* out;
   double* lin;
+  const double* phold;  // nodal (phi^n - phi^{n-1})/dt for the Eq. (theta) estimate, or null
   int color;
   int ctx, cty, ctz;  // tiles of this colour per axis
   int ntx, nty;       // tiles per axis (for the tile id)
@@ -58,10 +59,10 @@ elem_kernel(const ElemArgs A) {
   constexpr int NC = NLin<DIM, MODEL>::VALUE;
   constexpr bool needU = MODE != M_JV && MODE != M_JTV;
   constexpr bool needV = MODE == M_JV || MODE == M_JTV || MODE == M_PREV_T;
-  constexpr int NUF = needU ? 5 : 1;
+  constexpr int NUF = needU ? 6 : 1;
   constexpr int NVF = needV ? 2 : 1;
 
-  __shared__ double sU[NUF][NT];  // phi, u, phi - phi^n, u - u^n, phi^n
+  __shared__ double sU[NUF][NT];  // phi, u, phi - phi^n, u - u^n, phi^n, phihat_old
   __shared__ double sV[NVF][NT];
   __shared__ double sC[2 * NN][NE];
 
@@ -95,7 +96,8 @@ elem_kernel(const ElemArgs A) {
       sU[1][s] = u;
       sU[2][s] = phi - phin;
       sU[3][s] = u - un;
-      sU[NUF - 1][s] = phin;
+      sU[4][s] = phin;
+      sU[NUF - 1][s] = (A.phold && ok) ? A.phold[node] : 0.0;
     }
     if (needV) {
       sV[0][s] = ok ? A.V[node] : 0.0;
@@ -166,8 +168,18 @@ elem_kernel(const ElemArgs A) {
       if (tf1) {
         double npn[NN], vpn[NN];
 #pragma unroll
-        for (int a = 0; a < NN; ++a) npn[a] = sU[NUF - 1][sidx[a]];
+        for (int a = 0; a < NN; ++a) npn[a] = sU[4][sidx[a]];
         interp<DIM, true>(npn, vpn, gpn, A.S);
+      }
+      double pho[NN];
+      if ((MODE == M_RES || MODE == M_RES_LIN) && A.P.phihat_old) {
+        double npo[NN];
+#pragma unroll
+        for (int a = 0; a < NN; ++a) npo[a] = sU[NUF - 1][sidx[a]];
+        interp<DIM, false, double>(npo, pho, nullptr, A.S);
+      } else {
+#pragma unroll
+        for (int a = 0; a < NN; ++a) pho[a] = 0.0;
       }
       double w0[NN], w1[NN], gw0[DIM][NH], gw1[DIM][NH];
       if (MODE == M_PREV_T) {
@@ -191,11 +203,15 @@ elem_kernel(const ElemArgs A) {
           pn[d] = tf1 ? gpn[d][remove_bit(g, d)] : 0.0;
         }
         double G4 = 0.0;
-        if (MODEL == 1 && A.P.has_g4)
-          G4 = (gp_last_coord<DIM>(m, e_last, g) - A.P.zT - A.P.Vp * A.P.t_new) / A.P.lT;
-        if (MODE == M_RES || MODE == M_RES_LIN) {
+        if (MODEL == 1 && A.P.has_g4) {
+          const double tl = MODE == M_OLD ? A.P.t_new - A.P.dt : A.P.t_new;
+          G4 = (gp_last_coord<DIM>(m, e_last, g) - A.P.zT - A.P.Vp * tl) / A.P.lT;
+        }
+        if (MODE == M_OLD) {
+          spatial_old<DIM, MODEL>(A.P, phi[g], u[g], p, gg, G4, o);
+        } else if (MODE == M_RES || MODE == M_RES_LIN) {
           double L[MODE == M_RES_LIN ? NC : 1];
-          pointwise<DIM, MODEL, MODE == M_RES_LIN>(A.P, phi[g], u[g], dphi[g], du[g], p, gg, pn, G4, o, L);
+          pointwise<DIM, MODEL, MODE == M_RES_LIN>(A.P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L);
           if (MODE == M_RES_LIN) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) linp[(c * NN + g) * NE] = L[c];
@@ -366,13 +382,15 @@ static cudaError_t dispatch_mode(int mode, const ElemCtx& c, const ElemArgs& a, 
     case M_JTV: return run_colours<DIM, MODEL, M_JTV>(c, a, st);
     case M_DEPS: return run_colours<DIM, MODEL, M_DEPS>(c, a, st);
     case M_PREV_T: return run_colours<DIM, MODEL, M_PREV_T>(c, a, st);
+    case M_OLD: return run_colours<DIM, MODEL, M_OLD>(c, a, st);
   }
   return cudaErrorInvalidValue;
 }
 
 cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
-                     double* lin, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)c.m.nn, st);
+                     double* lin, cudaStream_t st, const double* init, const double* phold) {
+  cudaError_t e = init ? cudaMemcpyAsync(out, init, sizeof(double) * 2 * (size_t)c.m.nn, cudaMemcpyDeviceToDevice, st)
+                       : cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)c.m.nn, st);
   if (e != cudaSuccess) return e;
   ElemArgs a;
   a.m = c.m;
@@ -383,6 +401,7 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
   a.V = V;
   a.out = out;
   a.lin = lin;
+  a.phold = phold;
   a.ntx = c.ntx;
   a.nty = c.nty;
   a.color = 0;

@@ -119,6 +119,7 @@ class Params:
     zT: float = 0.0            # frozen-gradient origin: G4 = (x_last - zT - Vp t)/lT
     Delta: float = 0.65
     theta: float = 1.0
+    phihat_form: int = 1       # theta < 1: 1 (phi^{n+1} - phi^n)/dt, 0 the estimate of Eq. (theta)
     jat_normalised: int = 1
     time_form: int = 0
     # solver controls

@@ -217,3 +217,55 @@ def test_dendrite2d_128_ten_steps_match_oracle():
         assert ratio < 1e-12
         t += w.dt
     assert rel(host(h.get_state(out)), Uo) <= 1e-8
+
+
+THETA_CASES = [
+    ("2d-pure-cn", Mesh(2, 21, 13, 0, 0.9), dataclasses.replace(PURE, theta=0.5, phihat_form=1)),
+    ("2d-alloy-cn-eqtheta", Mesh(2, 19, 11, 0, 0.8), dataclasses.replace(ALLOY, theta=0.5, phihat_form=0)),
+    ("3d-alloy-theta0.7", Mesh(3, 9, 6, 7, 0.8), dataclasses.replace(ALLOY, theta=0.7, phihat_form=0)),
+    ("3d-pure-cn-literal", Mesh(3, 7, 5, 6, 0.9), dataclasses.replace(PURE, theta=0.5, phihat_form=1, time_form=1)),
+]
+
+
+@pytest.mark.parametrize("name,mesh,prm", THETA_CASES, ids=[c[0] for c in THETA_CASES])
+def test_theta_method_residual_tangent_adjoint(name, mesh, prm):
+    """theta-method (Eqs. dpf, dc, theta): level-n spatial terms, U^{n-1} history, tangent and J^T."""
+    import paper_2006_16764_b300 as pkg
+
+    U, Un = _inputs(mesh, 13)
+    Unm1 = synth.random_vector(mesh, 14)
+    v = synth.random_vector(mesh, 15)
+    w = synth.random_vector(mesh, 16)
+    dt, tn = 0.33, 0.9
+    h = handle(mesh, prm)
+    h.set_state(dev(Un), tn, dt)
+    h.set_history(dev(Unm1))
+    tU = dev(U)
+    out = dev(np.zeros_like(U))
+    h.residual(tU, out)
+    assert rel(host(out), OR.residual(mesh, prm, U, Un, tn, dt, Unm1=Unm1)) <= 1e-12
+    h.jvp(tU, dev(v), out)
+    assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v, Unm1=Unm1)) <= 1e-12
+    h.jtvp(tU, dev(w), out)
+    assert rel(host(out), OJ.jtvp(mesh, prm, U, Un, tn, dt, w, Unm1=Unm1)) <= 1e-12
+    with pytest.raises(pkg.TusasError):
+        h.dFdp(tU, out, 0)
+
+
+@pytest.mark.parametrize("form", [1, 0])
+def test_crank_nicolson_steps_match_oracle(form):
+    w = synth.scaled(synth.workload("dendrite2d_1024"), 32, 32)
+    prm = dataclasses.replace(w.params, theta=0.5, phihat_form=form, jvp_mode=1, precond=2)
+    U0 = synth.initial_state(w)
+    h = handle(w.mesh, prm)
+    h.set_state(dev(U0), 0.0, w.dt)
+    Uo, Uprev, t = U0.copy(), U0.copy(), 0.0
+    out = dev(np.zeros_like(U0))
+    for _ in range(3):
+        st = h.step()
+        assert st["converged"]
+        Unew, ratio = OS.newton_direct(w.mesh, prm, Uo, t, w.dt, Unm1=Uprev)
+        assert ratio < 1e-12
+        Uprev, Uo = Uo, Unew
+        t += w.dt
+        assert rel(host(h.get_state(out)), Uo) <= 1e-8

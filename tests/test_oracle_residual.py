@@ -305,3 +305,23 @@ def test_antitrapping_current_boundary_flux(dim, p, norm):
                 if e != d:
                     face &= (ijk[e] > 0) & (ijk[e] < nmax[e])
             assert np.allclose(rest[face], sgn * j[d] * mesh.h ** (dim - 1), rtol=1e-12, atol=1e-15)
+
+
+@pytest.mark.parametrize("theta", [0.5, 0.25])
+def test_theta_method_linear_parts_are_textbook(theta):
+    """Pure metal, theta-method (Eqs. dc, theta): R_u = M (u - u^n)/dt + theta D K u +
+    (1 - theta) D K u^n - M phihat / 2, phihat = theta (phi - phi^n)/dt + (1 - theta)(phi^n - phi^{n-1})/dt."""
+    mesh = Mesh(2, 6, 5, 0, 0.8)
+    prm = Params(model=0, eps4=0.05, lam=3.0, D=1.3, theta=theta, phihat_form=0)
+    U, Un = synth.random_fields(mesh, 31)
+    Unm1 = synth.random_vector(mesh, 32)
+    n = mesh.n_nodes
+    dt = 0.3
+    F = R.residual(mesh, prm, U, Un, 0.0, dt, Unm1=Unm1)
+    M, K = tb.mass(mesh), tb.stiffness(mesh)
+    phihat = theta * (U[:n] - Un[:n]) / dt + (1 - theta) * (Un[:n] - Unm1[:n]) / dt
+    want = M @ (U[n:] - Un[n:]) / dt + prm.D * (K @ (theta * U[n:] + (1 - theta) * Un[n:])) - 0.5 * (M @ phihat)
+    assert np.abs(F[n:] - want).max() <= 1e-13 * np.abs(want).max()
+    # theta = 1 ignores U^{n-1}
+    p1 = dataclasses.replace(prm, theta=1.0)
+    assert np.array_equal(R.residual(mesh, p1, U, Un, 0.0, dt, Unm1=Unm1), R.residual(mesh, p1, U, Un, 0.0, dt))

@@ -142,3 +142,25 @@ def test_backward_euler_is_first_order_in_time():
         U, _ = S.run_steps(mesh, prm, U0, T / m, m, direct=True)
         errs.append(np.linalg.norm(U - ref))
     assert 1.7 < errs[0] / errs[1] < 2.3 and 1.8 < errs[1] / errs[2] < 2.2, errs
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("form", [1, 0])
+def test_crank_nicolson_temporal_order(form):
+    """theta = 1/2 against a dt/256 reference: second order with phihat = (phi^{n+1} - phi^n)/dt
+    (Sec. 4.1.2 reports second order for Crank-Nicolson); first order with the estimate printed
+    as Eq. (theta), which is centred at t^n."""
+    mesh = Mesh(2, 10, 10, 0, 1.2)
+    prm = Params(model=0, eps4=0.05, lam=3.19, D=2.0, Delta=0.65, theta=0.5, phihat_form=form)
+    U0 = synth.seed_state(mesh, prm, radius=5.0)
+    T = 1.0
+    ref, _ = S.run_steps(mesh, prm, U0, T / 256, 256, direct=True)
+    errs = []
+    for m in (8, 16, 32):
+        U, _ = S.run_steps(mesh, prm, U0, T / m, m, direct=True)
+        errs.append(np.linalg.norm(U - ref))
+    r = [errs[0] / errs[1], errs[1] / errs[2]]
+    if form == 1:
+        assert r[0] > 3.3 and r[1] > 3.3, errs
+    else:
+        assert 1.7 < r[0] < 2.6 and 1.7 < r[1] < 2.6, errs
