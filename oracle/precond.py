@@ -49,10 +49,10 @@ def gp_coefficients(mesh, prm, U, Un, dt):
     phi_e, u_e = gather(mesh, U, conn)
     phin_e, _ = gather(mesh, Un, conn)
     E = conn.shape[0]
-    out = np.zeros((4, E, 2 ** dim))
+    out = np.zeros((4, E, len(fem.gauss_rule(dim, fem.order(mesh)))))
     k = prm.k
-    for gi, (xi, _) in enumerate(fem.gauss_rule(dim)):
-        N, G = fem.basis(dim, xi, h)
+    for gi, (xi, _) in enumerate(fem.gauss_rule(dim, fem.order(mesh))):
+        N, G = fem.basis(dim, xi, h, fem.order(mesh))
         phi = phi_e @ N
         u = u_e @ N
         phin = phin_e @ N
@@ -72,11 +72,11 @@ def assemble(mesh, cm, ck, conn):
     """sum_e sum_g w (cm N N^T + ck G^T G) as a CSR matrix (N_nodes square)."""
     dim, h = mesh.dim, mesh.h
     n = mesh.n_nodes
-    nl = 2 ** dim
+    nl = conn.shape[1]
     E = conn.shape[0]
     Ke = np.zeros((E, nl, nl))
-    for gi, (xi, wref) in enumerate(fem.gauss_rule(dim)):
-        N, G = fem.basis(dim, xi, h)
+    for gi, (xi, wref) in enumerate(fem.gauss_rule(dim, fem.order(mesh))):
+        N, G = fem.basis(dim, xi, h, fem.order(mesh))
         w = wref * h ** dim
         Ke += w * (cm[:, gi, None, None] * np.outer(N, N)[None] + ck[:, gi, None, None] * (G.T @ G)[None])
     rows = np.repeat(conn[:, :, None], nl, axis=2)
@@ -99,7 +99,7 @@ def coarse_mesh(mesh):
 
 
 def can_coarsen(mesh):
-    return all(n % 2 == 0 and n >= 2 for n in fem.n_elems_axis(mesh))
+    return fem.order(mesh) == 1 and all(n % 2 == 0 and n >= 2 for n in fem.n_elems_axis(mesh))
 
 
 def prolongation(mesh):

@@ -150,9 +150,9 @@ def element_residual(mesh, prm, elems, phi_e, u_e, phin_e, un_e, t_n, dt, source
     t_new = t_n + dt
     origin = [mesh.x0, mesh.y0, mesh.z0][:dim]
     dtype = np.result_type(phi_e, u_e, phin_e, un_e, prm.eps4)
-    out = np.zeros((phi_e.shape[0], 2, 2 ** dim), dtype=dtype)
-    for xi, wref in fem.gauss_rule(dim):
-        N, G = fem.basis(dim, xi, h)
+    out = np.zeros((phi_e.shape[0], 2, phi_e.shape[1]), dtype=dtype)
+    for xi, wref in fem.gauss_rule(dim, fem.order(mesh)):
+        N, G = fem.basis(dim, xi, h, fem.order(mesh))
         w = wref * h ** dim
         phi = phi_e @ N
         u = u_e @ N

@@ -62,7 +62,11 @@ def uniform_pm1(seed: int, n: int) -> np.ndarray:
 
 @dataclasses.dataclass
 class Mesh:
-    """Structured box of Q1 elements; nz = 0 in 2D. Node (i,j,k) sits at x0 + i*h."""
+    """Structured box of nx x ny (x nz) elements of size h; nz = 0 in 2D.
+
+    order 1: Q1 elements, node (i,j,k) at x0 + i*h; order 2: Q2 (biquadratic,
+    2D only), node (i,j) at x0 + i*h/2.
+    """
     dim: int
     nx: int
     ny: int
@@ -71,12 +75,14 @@ class Mesh:
     x0: float = 0.0
     y0: float = 0.0
     z0: float = 0.0
+    order: int = 1
 
     @property
     def shape_nodes(self):
+        p = self.order
         if self.dim == 2:
-            return (self.nx + 1, self.ny + 1)
-        return (self.nx + 1, self.ny + 1, self.nz + 1)
+            return (p * self.nx + 1, p * self.ny + 1)
+        return (p * self.nx + 1, p * self.ny + 1, p * self.nz + 1)
 
     @property
     def n_nodes(self) -> int:
@@ -92,12 +98,10 @@ class Mesh:
 
     def coords(self):
         """Per-axis node coordinates."""
-        xs = self.x0 + self.h * np.arange(self.nx + 1)
-        ys = self.y0 + self.h * np.arange(self.ny + 1)
-        if self.dim == 2:
-            return xs, ys
-        zs = self.z0 + self.h * np.arange(self.nz + 1)
-        return xs, ys, zs
+        nn = self.shape_nodes
+        hn = self.h / self.order
+        out = [o + hn * np.arange(n) for o, n in zip((self.x0, self.y0, self.z0), nn)]
+        return tuple(out)
 
 
 @dataclasses.dataclass

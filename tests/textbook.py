@@ -57,3 +57,31 @@ def node_ijk(mesh):
     nn = list(mesh.shape_nodes)
     grids = np.meshgrid(*[np.arange(n) for n in nn], indexing="ij")
     return [np.ascontiguousarray(g.transpose()).reshape(-1) for g in grids]
+
+
+def _assemble_1d(n, Ke):
+    p = Ke.shape[0] - 1
+    N = p * n + 1
+    A = np.zeros((N, N))
+    for e in range(n):
+        A[p * e:p * e + p + 1, p * e:p * e + p + 1] += Ke
+    return sp.csr_matrix(A)
+
+
+def mass1_q2(n, h):
+    """1D quadratic Lagrange mass matrix, element (h/30)[[4,2,-1],[2,16,2],[-1,2,4]]."""
+    return _assemble_1d(n, (h / 30.0) * np.array([[4.0, 2.0, -1.0], [2.0, 16.0, 2.0], [-1.0, 2.0, 4.0]]))
+
+
+def stiff1_q2(n, h):
+    """1D quadratic Lagrange stiffness matrix, element (1/(3h))[[7,-8,1],[-8,16,-8],[1,-8,7]]."""
+    return _assemble_1d(n, (1.0 / (3.0 * h)) * np.array([[7.0, -8.0, 1.0], [-8.0, 16.0, -8.0], [1.0, -8.0, 7.0]]))
+
+
+def mass_q2(mesh):
+    return sp.kron(mass1_q2(mesh.ny, mesh.h), mass1_q2(mesh.nx, mesh.h)).tocsr()
+
+
+def stiffness_q2(mesh):
+    return (sp.kron(mass1_q2(mesh.ny, mesh.h), stiff1_q2(mesh.nx, mesh.h))
+            + sp.kron(stiff1_q2(mesh.ny, mesh.h), mass1_q2(mesh.nx, mesh.h))).tocsr()
