@@ -37,13 +37,20 @@ enum {
   TUSAS_ENONFINITE = -5  /* a NaN or Inf appeared in a residual norm          */
 };
 
-/* Structured box of Q1 elements; dim 2 (nz = 0) or 3. Node (i,j,k) sits at
- * (x0 + i h, y0 + j h, z0 + k h). */
+/* Structured box of nx x ny (x nz) Lagrange elements of size h; dim 2 (nz = 0)
+ * or 3 (Sec. 2.1.1). order 0 or 1: Q1 elements with the 2^dim-point Gauss
+ * rule, node (i,j,k) at (x0 + i h, y0 + j h, z0 + k h). order 2: biquadratic
+ * Q2 elements with the 3 x 3 Gauss rule (2D only; the higher-order elements of
+ * the tip-velocity study, Sec. 4.1), node (i,j) at (x0 + i h/2, y0 + j h/2),
+ * (2 nx + 1)(2 ny + 1) nodes; Q2 handles take precond 0 or 1 (point Jacobi
+ * on the diagonals of M11, M22), and tusas_create returns TUSAS_EINVAL for
+ * precond 2 or order 2 in 3D. Nodes are numbered x fastest in every case. */
 typedef struct tusas_mesh {
   int dim;
   int nx, ny, nz;
   double h;
   double x0, y0, z0;
+  int order;
 } tusas_mesh;
 
 /* Model and solver parameters, nondimensional (Sec. 4.2: W0 = tau0 = 1).

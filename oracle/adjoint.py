@@ -26,18 +26,26 @@ from .solver import newton_direct
 
 
 def solid_fraction_weights(mesh):
-    """(w, c): S = w^T U + c equals int (1 + phi_h)/2 over the box."""
-    nn = fem.n_nodes_axis(mesh)
+    """(w, c): S = w^T U + c equals int (1 + phi_h)/2 over the box.
+
+    The integral of each nodal basis function is a product of 1D integrals:
+    per element [h/2, h/2] for Q1 (trapezoid), [h/6, 2h/3, h/6] for Q2
+    (Simpson), summed over the elements that share a node.
+    """
+    p = fem.order(mesh)
+    elem_w = [0.5, 0.5] if p == 1 else [1.0 / 6.0, 2.0 / 3.0, 1.0 / 6.0]
     one_d = []
-    for n in nn:
-        m = np.ones(n)
-        m[0] = m[-1] = 0.5
-        one_d.append(m * mesh.h)
+    for ne in fem.n_elems_axis(mesh):
+        m = np.zeros(p * ne + 1)
+        for e in range(ne):
+            for a, wa in enumerate(elem_w):
+                m[p * e + a] += wa * mesh.h
+        one_d.append(m)
     mrow = one_d[0]
     for m in one_d[1:]:
         mrow = np.kron(m, mrow)  # x fastest
     w = np.concatenate([0.5 * mrow, np.zeros(mesh.n_nodes)])
-    vol = np.prod([mesh.h * (n - 1) for n in nn])
+    vol = np.prod([mesh.h * ne for ne in fem.n_elems_axis(mesh)])
     return w, 0.5 * vol
 
 

@@ -29,7 +29,8 @@ TIMER_NAMES = ["residual", "residual_lin", "jv", "adjoint", "pc_apply", "pc_setu
 
 class CMesh(ctypes.Structure):
     _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double)]
+                ("h", ctypes.c_double), ("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("order", ctypes.c_int)]
 
 
 _PARAM_FIELDS = [
@@ -158,7 +159,7 @@ class TusasError(RuntimeError):
 
 def make_mesh(mesh) -> CMesh:
     return CMesh(int(mesh.dim), int(mesh.nx), int(mesh.ny), int(mesh.nz if mesh.dim == 3 else 0),
-                 float(mesh.h), float(mesh.x0), float(mesh.y0), float(mesh.z0))
+                 float(mesh.h), float(mesh.x0), float(mesh.y0), float(mesh.z0), int(getattr(mesh, "order", 1)))
 
 
 def make_params(prm) -> CParams:

@@ -15,15 +15,24 @@ import torch
 
 def solid_fraction_weights(mesh):
     """(w, c) with int (1 + phi_h)/2 = w^T U + c: w is half the integral of each phi basis
-    function (h^dim times 1/2 per boundary axis), zero on the u block; c = |Omega|/2."""
-    nn = [mesh.nx + 1, mesh.ny + 1] + ([mesh.nz + 1] if mesh.dim == 3 else [])
+    function, zero on the u block; c = |Omega|/2. Basis integrals are products of 1D
+    node weights: h inside and h/2 at the ends for Q1; for Q2 (order 2) the Simpson
+    weights h/3 at shared vertices, 2h/3 at midpoints, h/6 at the ends."""
+    order = int(getattr(mesh, "order", 1))
+    ne = [mesh.nx, mesh.ny] + ([mesh.nz] if mesh.dim == 3 else [])
     m = None
-    for n in nn:
-        a = np.full(n, mesh.h)
-        a[0] = a[-1] = 0.5 * mesh.h
+    for n in ne:
+        if order == 2:
+            a = np.empty(2 * n + 1)
+            a[1::2] = 2.0 * mesh.h / 3.0
+            a[0::2] = mesh.h / 3.0
+            a[0] = a[-1] = mesh.h / 6.0
+        else:
+            a = np.full(n + 1, mesh.h)
+            a[0] = a[-1] = 0.5 * mesh.h
         m = a if m is None else np.kron(a, m)
-    nodes = int(np.prod(nn))
-    vol = float(np.prod([mesh.h * (n - 1) for n in nn]))
+    nodes = m.size
+    vol = float(np.prod([mesh.h * n for n in ne]))
     return np.concatenate([0.5 * m, np.zeros(nodes)]), 0.5 * vol
 
 

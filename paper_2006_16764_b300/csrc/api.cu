@@ -120,7 +120,16 @@ int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
     why = "h must be positive and finite";
     return TUSAS_EINVAL;
   }
-  const double nodes = (double)(m->nx + 1) * (m->ny + 1) * (m->dim == 3 ? m->nz + 1 : 1);
+  if (m->order < 0 || m->order > 2 || (m->order == 2 && m->dim != 2)) {
+    why = "order must be 0 or 1 (Q1) or 2 (Q2, 2D only)";
+    return TUSAS_EINVAL;
+  }
+  if (m->order == 2 && p->precond == 2) {
+    why = "Q2 meshes take precond 0 or 1 (no multigrid hierarchy for Q2)";
+    return TUSAS_EINVAL;
+  }
+  const int po = m->order == 2 ? 2 : 1;
+  const double nodes = (double)(po * m->nx + 1) * (po * m->ny + 1) * (m->dim == 3 ? m->nz + 1 : 1);
   if (nodes > 2.0e9) {
     why = "mesh too large (more than 2e9 nodes)";
     return TUSAS_EINVAL;
@@ -273,11 +282,12 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   TCK(cudaGetDevice(&h->device));
   tusas::DevMesh& d = h->dm;
   d.dim = mesh->dim;
+  d.order = mesh->order == 2 ? 2 : 1;
   d.nx = mesh->nx;
   d.ny = mesh->ny;
   d.nz = mesh->dim == 3 ? mesh->nz : 0;
-  d.nnx = mesh->nx + 1;
-  d.nny = mesh->ny + 1;
+  d.nnx = d.order * mesh->nx + 1;
+  d.nny = d.order * mesh->ny + 1;
   d.nnz = mesh->dim == 3 ? mesh->nz + 1 : 1;
   d.nn = (i64)d.nnx * d.nny * d.nnz;
   d.ne = (i64)d.nx * d.ny * (mesh->dim == 3 ? d.nz : 1);

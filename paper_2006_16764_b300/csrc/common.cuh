@@ -7,9 +7,11 @@ namespace tusas {
 
 typedef long long i64;
 
-// Structured box of Q1 elements (node (i,j,k) at x0 + i h, index i + nnx (j + nny k)).
+// Structured box of Lagrange elements of order 1 (Q1) or 2 (Q2, 2D only): node
+// (i,j,k) at x0 + i h / order, index i + nnx (j + nny k), nnx = order nx + 1.
 struct DevMesh {
   int dim;
+  int order;
   int nx, ny, nz;        // elements per axis (nz = 0 in 2D)
   int nnx, nny, nnz;     // nodes per axis (nnz = 1 in 2D)
   i64 nn;                // number of nodes

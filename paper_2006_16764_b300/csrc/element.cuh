@@ -296,6 +296,80 @@ __device__ __forceinline__ void spatial_old(const DevPhys& P, double phi, double
   for (int d = 0; d < DIM; ++d) o.fu[d] = Dq * g[d];
 }
 
+// d(integrands)/d eps4 at one Gauss point (Eq. gs differentiated in eps4, through
+// the flux and the tau(n) time term). tf1: difference-of-products time term.
+template <int DIM>
+__device__ __forceinline__ void gp_deps(const DevPhys& P, bool tf1, double phi, double u, double dphi, double du,
+                                        const double* p, const double* pn, GPOut<DIM>& o) {
+  Aniso<DIM> An;
+  An.eval(p, P.eps4);
+  const double ae = An.r == 0.0 ? 0.0 : fma(4.0, An.sn, -3.0);
+  const double W2 = P.W0 * P.W0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double md = An.n2[d] - An.sn;
+    o.fphi[d] = W2 * p[d] * (ae * fma(16.0 * P.eps4, md, An.a) + An.a * fma(16.0, md, ae));
+    o.fu[d] = 0.0;
+  }
+  const double B = fma(1.0 - P.k, u, 1.0);
+  if (!tf1) {
+    o.sphi = P.tau0 * B * dphi * P.idt * 2.0 * An.a * ae;
+  } else {
+    Aniso<DIM> Ao;
+    Ao.eval(pn, P.eps4);
+    const double aoe = Ao.r == 0.0 ? 0.0 : fma(4.0, Ao.sn, -3.0);
+    const double Bn = fma(1.0 - P.k, u - du, 1.0);
+    o.sphi = P.tau0 * P.idt * 2.0 * (B * An.a * ae * phi - Bn * Ao.a * aoe * (phi - dphi));
+  }
+  o.su = 0.0;
+}
+
+// Integrands of (dF/dU^n)^T w at one Gauss point: (w0, w1) the values of the
+// two adjoint fields there, gw1 the gradient of w1.
+template <int DIM, int MODEL>
+__device__ __forceinline__ void gp_prev_t(const DevPhys& P, bool tf1, double phi, double u, double dphi, double du,
+                                          const double* p, const double* pn, double w0, double w1,
+                                          const double* gw1, GPOut<DIM>& o) {
+  Aniso<DIM> An;
+  An.eval(p, P.eps4);
+  const double omk = 1.0 - P.k;
+  const double B = fma(omk, u, 1.0);
+  const double phin = phi - dphi;
+  double ds_dpn, ds_dun = 0.0, cpn = 0.0, apn[DIM];
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) apn[d] = 0.0;
+  if (!tf1) {
+    ds_dpn = -P.tau0 * B * An.a * An.a * P.idt;
+  } else {
+    Aniso<DIM> Ao;
+    Ao.eval(pn, P.eps4);
+    const double Bn = fma(omk, u - du, 1.0);
+    ds_dpn = -P.tau0 * Bn * Ao.a * Ao.a * P.idt;
+    ds_dun = -P.tau0 * omk * Ao.a * Ao.a * phin * P.idt;
+    cpn = -2.0 * P.tau0 * Bn * phin * P.idt * Ao.a;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) apn[d] = 16.0 * P.eps4 * Ao.n[d] * (Ao.n2[d] - Ao.sn) * Ao.r;
+  }
+  const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - omk * phin);
+  const double dsu_dpn = -0.5 * omk * du * P.idt + 0.5 * B * P.idt;
+  const double dsu_dun = -Acoef * P.idt;
+  double jp = 0.0;
+  if (MODEL == 1) {
+    const double cw = -TUSAS_INV_2SQRT2 * P.W0 * B * P.idt;
+    double nfu = 0.0;
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) nfu = fma(P.jat_norm ? An.n[d] : p[d], gw1[d], nfu);
+    jp = cw * nfu;
+  }
+  o.sphi = ds_dpn * w0 + dsu_dpn * w1 + jp;
+  o.su = ds_dun * w0 + dsu_dun * w1;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    o.fphi[d] = cpn * apn[d] * w0;
+    o.fu[d] = 0.0;
+  }
+}
+
 // Apply the stored pointwise Jacobian (TRANS = false) or its transpose.
 // Inputs (x0, x1, xp, xg): forward = (dphi, du, dp, dg);
 // transpose = (s_phi, s_u, f_phi, f_u) test-side quantities.

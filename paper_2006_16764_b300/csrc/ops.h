@@ -11,12 +11,23 @@ namespace tusas {
 void count_launches(long long n);
 long long launches();
 
-enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5, M_OLD = 6 };
+// M_DIAG (Q2 only): the diagonals of the preconditioner blocks M11, M22.
+enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5, M_OLD = 6, M_DIAG = 7 };
+
+// 1D tables of the biquadratic element with the 3-point Gauss rule (g Gauss
+// point, a local node): B = Lagrange values, G = physical derivatives (1/h);
+// BW = h w_g B, GW = h w_g G (test side, w_g the unit-interval weights);
+// BB = h w_g B^2, GG = h w_g G^2 (diagonal of mass / stiffness forms);
+// xg = Gauss points in [0, 1].
+struct Q2Tab {
+  double B[3][3], G[3][3], BW[3][3], GW[3][3], BB[3][3], GG[3][3], xg[3];
+};
 
 struct ElemCtx {
   DevMesh m;
   DevPhys P;
   Scales S;
+  Q2Tab q2;
   int ntx, nty, ntz;  // tiles per axis
   int nlin;           // linearisation coefficients per Gauss point
 };
@@ -29,6 +40,10 @@ size_t elem_lin_doubles(const ElemCtx& c);
 // order. `phold`: nodal (phi^n - phi^{n-1})/dt when the Eq. (theta) estimate is used.
 cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
                      double* lin, cudaStream_t st, const double* init = nullptr, const double* phold = nullptr);
+// The same pass on a 2D Q2 box (out already zeroed or initialised by elem_run).
+cudaError_t q2_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
+                   double* lin, cudaStream_t st, const double* phold);
+void q2_tables(Q2Tab& T, double h);
 
 // ---- FP64 vector kernels (deterministic) ----------------------------------
 // y = a*x + y

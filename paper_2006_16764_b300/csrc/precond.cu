@@ -536,6 +536,11 @@ __global__ void k_from_t(i64 n, const T* __restrict__ x, double* __restrict__ z)
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) z[i] = (double)x[i];
 }
 template <typename T>
+__global__ void k_recip(i64 n, const double* __restrict__ d, T* __restrict__ dinv) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    dinv[i] = (T)(1.0 / d[i]);
+}
+template <typename T>
 __global__ void k_jacobi(i64 n, const T* __restrict__ dinv, const double* __restrict__ r, double* __restrict__ z) {
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     z[i] = (double)dinv[i] * r[i];
@@ -572,6 +577,17 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
   bytes = 0;
   if (kind == 0) return cudaSuccess;
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
+  if (m.order == 2) {
+    if (kind != 1) return cudaErrorInvalidValue;
+    PrecondLevel L = {};
+    L.m = m;
+    L.nn = m.nn;
+    cudaError_t e = cudaMalloc(&L.dinv, esz * 2 * m.nn);
+    if (e != cudaSuccess) return e;
+    lv.push_back(L);
+    bytes += (esz + sizeof(double)) * 2 * m.nn;
+    return cudaMalloc(&diag, sizeof(double) * 2 * m.nn);
+  }
   const int NS = m.dim == 3 ? 27 : 9;
   const int nlev = kind == 1 ? 1 : (levels < 1 ? 1 : levels);
   DevMesh cur = m;
@@ -607,7 +623,8 @@ void Precond::destroy() {
   lv.clear();
   if (gersh_partials) cudaFree(gersh_partials);
   if (lmax_dev) cudaFree(lmax_dev);
-  gersh_partials = lmax_dev = nullptr;
+  if (diag) cudaFree(diag);
+  gersh_partials = lmax_dev = diag = nullptr;
 }
 
 template <typename T>
@@ -615,6 +632,14 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
   const DevMesh& m = c.m;
   const int NS = m.dim == 3 ? 27 : 9;
   PrecondLevel& L0 = lv[0];
+  if (m.order == 2) {
+    // point Jacobi: element pass for diag(M11), diag(M22), then the reciprocals
+    cudaError_t e = elem_run(M_DIAG, c, U, Un, nullptr, diag, nullptr, st);
+    if (e != cudaSuccess) return e;
+    k_recip<T><<<grid_nodes(2 * m.nn), 256, 0, st>>>(2 * m.nn, diag, (T*)L0.dinv);
+    count_launches(1);
+    return cudaGetLastError();
+  }
   cudaError_t e = cudaMemsetAsync(L0.st, 0, sizeof(T) * 2 * NS * m.nn, st);
   if (e != cudaSuccess) return e;
   FillArgs<T> A;

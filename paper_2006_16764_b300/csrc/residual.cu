@@ -217,69 +217,12 @@ elem_kernel(const ElemArgs A) {
             for (int c = 0; c < NC; ++c) linp[(c * NN + g) * NE] = L[c];
           }
         } else if (MODE == M_DEPS) {
-          const DevPhys& P = A.P;
-          Aniso<DIM> An;
-          An.eval(p, P.eps4);
-          const double ae = An.r == 0.0 ? 0.0 : fma(4.0, An.sn, -3.0);
-          const double W2 = P.W0 * P.W0;
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            const double md = An.n2[d] - An.sn;
-            o.fphi[d] = W2 * p[d] * (ae * fma(16.0 * P.eps4, md, An.a) + An.a * fma(16.0, md, ae));
-            o.fu[d] = 0.0;
-          }
-          const double B = fma(1.0 - P.k, u[g], 1.0);
-          if (!tf1) {
-            o.sphi = P.tau0 * B * dphi[g] * P.idt * 2.0 * An.a * ae;
-          } else {
-            Aniso<DIM> Ao;
-            Ao.eval(pn, P.eps4);
-            const double aoe = Ao.r == 0.0 ? 0.0 : fma(4.0, Ao.sn, -3.0);
-            const double Bn = fma(1.0 - P.k, u[g] - du[g], 1.0);
-            o.sphi = P.tau0 * P.idt * 2.0 * (B * An.a * ae * phi[g] - Bn * Ao.a * aoe * (phi[g] - dphi[g]));
-          }
-          o.su = 0.0;
+          gp_deps<DIM>(A.P, tf1, phi[g], u[g], dphi[g], du[g], p, pn, o);
         } else {  // M_PREV_T
-          const DevPhys& P = A.P;
-          Aniso<DIM> An;
-          An.eval(p, P.eps4);
-          const double omk = 1.0 - P.k;
-          const double B = fma(omk, u[g], 1.0);
-          const double phin = phi[g] - dphi[g];
-          double ds_dpn, ds_dun = 0.0, cpn = 0.0, apn[DIM];
+          double gw[DIM];
 #pragma unroll
-          for (int d = 0; d < DIM; ++d) apn[d] = 0.0;
-          if (!tf1) {
-            ds_dpn = -P.tau0 * B * An.a * An.a * P.idt;
-          } else {
-            Aniso<DIM> Ao;
-            Ao.eval(pn, P.eps4);
-            const double Bn = fma(omk, u[g] - du[g], 1.0);
-            ds_dpn = -P.tau0 * Bn * Ao.a * Ao.a * P.idt;
-            ds_dun = -P.tau0 * omk * Ao.a * Ao.a * phin * P.idt;
-            cpn = -2.0 * P.tau0 * Bn * phin * P.idt * Ao.a;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d) apn[d] = 16.0 * P.eps4 * Ao.n[d] * (Ao.n2[d] - Ao.sn) * Ao.r;
-          }
-          const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - omk * phin);
-          const double dsu_dpn = -0.5 * omk * du[g] * P.idt + 0.5 * B * P.idt;
-          const double dsu_dun = -Acoef * P.idt;
-          double jp = 0.0;
-          if (MODEL == 1) {
-            const double cw = -TUSAS_INV_2SQRT2 * P.W0 * B * P.idt;
-            double nfu = 0.0;
-#pragma unroll
-            for (int d = 0; d < DIM; ++d)
-              nfu = fma(P.jat_norm ? An.n[d] : p[d], gw1[d][remove_bit(g, d)], nfu);
-            jp = cw * nfu;
-          }
-          o.sphi = ds_dpn * w0[g] + dsu_dpn * w1[g] + jp;
-          o.su = ds_dun * w0[g] + dsu_dun * w1[g];
-#pragma unroll
-          for (int d = 0; d < DIM; ++d) {
-            o.fphi[d] = cpn * apn[d] * w0[g];
-            o.fu[d] = 0.0;
-          }
+          for (int d = 0; d < DIM; ++d) gw[d] = gw1[d][remove_bit(g, d)];
+          gp_prev_t<DIM, MODEL>(A.P, tf1, phi[g], u[g], dphi[g], du[g], p, pn, w0[g], w1[g], gw, o);
         }
         s0[g] = o.sphi;
         s1[g] = o.su;
@@ -347,12 +290,13 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
     c.ntz = 1;
     c.nlin = P.model == 0 ? NLin<2, 0>::VALUE : NLin<2, 1>::VALUE;
   }
+  if (m.order == 2) q2_tables(c.q2, m.h);
 }
 
 size_t elem_lin_doubles(const ElemCtx& c) {
   const int dim = c.m.dim;
   const size_t ne_tile = dim == 3 ? Tile<3>::X * Tile<3>::Y * Tile<3>::Z : Tile<2>::X * Tile<2>::Y;
-  const size_t ng = dim == 3 ? 8 : 4;
+  const size_t ng = c.m.order == 2 ? 9 : (dim == 3 ? 8 : 4);
   return (size_t)c.ntx * c.nty * c.ntz * ne_tile * ng * c.nlin;
 }
 
@@ -392,6 +336,7 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
   cudaError_t e = init ? cudaMemcpyAsync(out, init, sizeof(double) * 2 * (size_t)c.m.nn, cudaMemcpyDeviceToDevice, st)
                        : cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)c.m.nn, st);
   if (e != cudaSuccess) return e;
+  if (c.m.order == 2) return q2_run(mode, c, U, Un, V, out, lin, st, phold);
   ElemArgs a;
   a.m = c.m;
   a.P = c.P;

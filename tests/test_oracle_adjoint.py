@@ -61,3 +61,16 @@ def test_alloy_adjoint_matches_central_differences():
     pD = lambda d: synth.seed_state(mesh, dataclasses.replace(prm, Delta=d), radius=3.0, centred=True)
     fdD = (_S(mesh, prm, pD(prm.Delta + h), dt, n) - _S(mesh, prm, pD(prm.Delta - h), dt, n)) / (2 * h)
     assert abs(g0 @ dU0 - fdD) <= 1e-5 * abs(fdD)
+
+
+def test_q2_solid_fraction_weights_are_simpson():
+    """Q2 interpolates phi = x^2 y exactly, so S = w^T U + c must equal the exact integral
+    of (1 + x^2 y)/2 (trapezoid weights would not)."""
+    mesh = Mesh(2, 3, 2, 0, 0.5, 1.0, 0.0, order=2)
+    w, c = OA.solid_fraction_weights(mesh)
+    xs, ys = np.meshgrid(*mesh.coords(), indexing="ij")
+    phi = (xs ** 2 * ys).T.reshape(-1)
+    U = np.concatenate([phi, np.zeros(mesh.n_nodes)])
+    x0, x1, y0, y1 = 1.0, 2.5, 0.0, 1.0
+    exact = 0.5 * ((x1 - x0) * (y1 - y0) + (x1 ** 3 - x0 ** 3) / 3 * (y1 ** 2 - y0 ** 2) / 2)
+    assert abs(w @ U + c - exact) < 1e-13

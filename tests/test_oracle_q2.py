@@ -80,3 +80,18 @@ def test_q2_manufactured_solution_converges_third_order(model, eps):
         assert r1 > 12.0 and r2 > 12.0, errs
     else:
         assert r1 > 4.5 and r2 > 4.5, errs
+
+
+def test_q2_sampled_node_residual_matches_full_residual():
+    """The one-node-at-a-time residual (used at full workload sizes) agrees with the full
+    assembly on vertex, edge-midpoint and element-centre nodes of a Q2 box."""
+    mesh = Mesh(2, 5, 4, 0, 0.7, 1.0, -2.0, order=2)
+    prm = Params(model=1, k=0.15, eps4=0.02, lam=3.0, D=2.0, lT=40.0, Vp=0.1, zT=-3.0)
+    U, Un = synth.random_fields(mesh, 31)
+    F = R.residual(mesh, prm, U, Un, 0.4, 0.3)
+    n = mesh.n_nodes
+    nnx = 2 * mesh.nx + 1
+    nodes = np.array([0, 1, 2, nnx, nnx + 1, 3 * nnx + 4, 5 * nnx + 7, n - 1, n - 2, n // 2])
+    rp, ru = R.residual_at_nodes(mesh, prm, U, Un, 0.4, 0.3, nodes)
+    assert np.abs(rp - F[nodes]).max() <= 1e-13 * np.abs(F).max()
+    assert np.abs(ru - F[n + nodes]).max() <= 1e-13 * np.abs(F).max()
