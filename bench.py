@@ -61,27 +61,37 @@ def parse():
     ap.add_argument("--fd-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--report", default=None, choices=synth.WORKLOADS,
+    ap.add_argument("--report", default=None, choices=synth.WORKLOADS + ["q2"],
                     help="run one workload's full protocol (step counts, precision / tangent comparisons, "
-                         "adjoint gradients) and print a JSON summary")
-    ap.add_argument("--kernels", action="store_true",
+                         "adjoint gradients) and print a JSON summary; q2: biquadratic vs Q1 elements on "
+                         "the dendrite2d_1024 box")
+    ap.add_argument("--kernels", nargs="?", const="alloy3d", default=None, choices=["alloy3d", "q2"],
                     help="profiling case: a few residual / linearisation / tangent passes on a 256x192x64 "
-                         "sub-box of the alloy workload (inputs > L2, about 5 GB on the device)")
+                         "sub-box of the alloy workload (inputs > L2, about 5 GB on the device), or (q2) on "
+                         "a 1536^2 Q2 box of the 2D dendrite (about 2 GB)")
     return ap.parse_args()
 
 
-def run_kernels():
-    """Small case for detailed counters: 2 residuals, 2 linearisations, 2 tangent actions."""
+def run_kernels(kind="alloy3d"):
+    """Small case for detailed counters: 2 residuals, then 2 tangent actions (each a
+    linearisation pass and a tangent pass); every pass is one launch per tile colour."""
     import dataclasses
 
     import torch
 
     import paper_2006_16764_b300 as pkg
 
-    w = synth.scaled(synth.workload(WORKLOAD), 256, 192, 64)
+    if kind == "q2":
+        base = synth.workload("dendrite2d_1024")
+        mesh = synth.Mesh(2, 1536, 1536, 0, 400.0 / 1536, order=2)
+        w = synth.Workload("dendrite2d_q2_1536", mesh, base.params, base.dt, 1)
+        U0h = synth.seed_state(mesh, base.params, radius=8.0)
+    else:
+        w = synth.scaled(synth.workload(WORKLOAD), 256, 192, 64)
+        U0h = synth.initial_state(w)
     prm = dataclasses.replace(w.params, gmres_restart=2, precond=0)
     dev = torch.device("cuda", 0)
-    U0 = torch.tensor(synth.initial_state(w), device=dev)
+    U0 = torch.tensor(U0h, device=dev)
     U = U0 + 0.01 * torch.tensor(synth.uniform_pm1(3, w.mesh.n_dofs), device=dev)
     v = torch.tensor(synth.uniform_pm1(4, w.mesh.n_dofs), device=dev)
     h = pkg.Tusas(w.mesh, prm)
@@ -92,7 +102,7 @@ def run_kernels():
     for _ in range(2):
         h.jvp(U, v, F)
     torch.cuda.synchronize()
-    print(json.dumps({"kernels": "ok", "dofs": w.mesh.n_dofs, "elems": w.mesh.n_elems}))
+    print(json.dumps({"kernels": kind, "dofs": w.mesh.n_dofs, "elems": w.mesh.n_elems}))
     h.close()
 
 
@@ -139,6 +149,75 @@ def _run_variant(w, prm, U0, nsteps, stream):
             "first_failed_step": failed}, U
 
 
+def _operator_rates(mesh, prm, stream, reps=20):
+    """ms per residual, linearisation (residual + stored pointwise Jacobian) and tangent pass."""
+    import dataclasses
+
+    import torch
+
+    import paper_2006_16764_b300 as pkg
+
+    dev = torch.device("cuda", 0)
+    h = pkg.Tusas(mesh, dataclasses.replace(prm, precond=0, gmres_restart=1), stream=stream)
+    U0 = torch.tensor(synth.seed_state(mesh, prm, radius=8.0), device=dev)
+    U = U0 + 0.01 * torch.tensor(synth.uniform_pm1(3, mesh.n_dofs), device=dev)
+    v = torch.tensor(synth.uniform_pm1(4, mesh.n_dofs), device=dev)
+    h.set_state(U0, 0.0, 0.5)
+    F = torch.empty_like(U)
+    for _ in range(3):
+        h.residual(U, F)
+        h.jvp(U, v, F)
+    h.timers(True)
+    for _ in range(reps):
+        h.residual(U, F)
+        h.jvp(U, v, F)
+    t = h.get_timers()
+    h.timers(False)
+    h.close()
+    out = {"dofs": mesh.n_dofs, "elems": mesh.n_elems}
+    for k in ("residual", "residual_lin", "jv"):
+        ms = t[k][0] / max(t[k][1], 1)
+        out[k] = {"ms": ms, "Mdof_evals_per_s": mesh.n_dofs / ms / 1e3}
+    return out
+
+
+def run_q2_report(stream):
+    """Biquadratic (Q2, 3x3 Gauss) against Q1 elements on the 400 x 400 box of the 2D dendrite.
+
+    Kernel rates at equal node counts (Q2 with n elements per axis vs Q1 with 2n), and
+    backward-Euler JFNK steps of the dendrite seed with the same node spacing:
+    Q2 512^2 (point Jacobi, the preconditioner Q2 handles take) against Q1 1024^2 with
+    point Jacobi and with the GMG V-cycle.
+    """
+    import dataclasses
+
+    import torch
+
+    w = synth.workload("dendrite2d_1024")
+    out = {"report": "q2"}
+    rates = []
+    for n in (256, 512, 1024, 2048):
+        m2 = synth.Mesh(2, n, n, 0, 400.0 / n, order=2)
+        m1 = synth.Mesh(2, 2 * n, 2 * n, 0, 200.0 / n)
+        rates.append({"q2_elems_per_axis": n, "q2": _operator_rates(m2, w.params, stream),
+                      "q1_same_nodes": _operator_rates(m1, w.params, stream)})
+    out["operator_rates"] = rates
+    dev = torch.device("cuda", 0)
+    nsteps = 10
+    m2 = synth.Mesh(2, 512, 512, 0, 400.0 / 512, order=2)
+    variants = [("q2_512_exact_jacobi", m2, dict(precond=1, jvp_mode=1)),
+                ("q2_512_fd_jacobi", m2, dict(precond=1, jvp_mode=0)),
+                ("q1_1024_exact_jacobi", w.mesh, dict(precond=1, jvp_mode=1)),
+                ("q1_1024_exact_gmg_fp32", w.mesh, dict(precond=2, jvp_mode=1, smoother_fp32=1))]
+    for name, mesh, opts in variants:
+        prm = dataclasses.replace(w.params, newton_maxit=30, **opts)
+        U0 = torch.tensor(synth.seed_state(mesh, prm, radius=8.0), device=dev)
+        ws = synth.Workload(name, mesh, prm, w.dt, nsteps)
+        r, _ = _run_variant(ws, prm, U0, nsteps, stream)
+        out[name] = r
+    print(json.dumps(out), flush=True)
+
+
 def run_report(name):
     """Each workload's protocol: step counts, tangent / precision comparisons, adjoint gradients."""
     import dataclasses
@@ -147,6 +226,8 @@ def run_report(name):
 
     import paper_2006_16764_b300 as pkg
 
+    if name == "q2":
+        return run_q2_report(torch.cuda.current_stream(torch.device("cuda", 0)))
     w = synth.workload(name)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)
@@ -535,8 +616,10 @@ def run_ours(args, ws, rank, local):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": args.workload, "mesh": f"{mesh.nx}x{mesh.ny}x{mesh.nz} Q1 hex, h={mesh.h}",
                        "dofs": N, "dt": w.dt, "jvp": "exact (stored pointwise linearisation)",
-                       "precond": "block Jacobi, GMG V-cycle, Chebyshev(2), FP32",
+                       "precond": f"block Jacobi, GMG V-cycle ({prm.mg_levels} levels), "
+                                  f"Chebyshev({prm.cheb_degree}), {'FP32' if prm.smoother_fp32 else 'FP64'}",
                        "newton_rtol": prm.newton_rtol, "gmres_restart": prm.gmres_restart,
+                       "gmres_maxit_per_newton": prm.gmres_maxit,
                        "l2": "inputs larger than L2 (state 136 MB per vector, linearisation 12.3 GB)",
                        "parallelism": f"{ws} independent replica(s)"},
             "roofline": roof,
@@ -558,7 +641,7 @@ def run_ours(args, ws, rank, local):
 def main():
     args = parse()
     if args.kernels:
-        run_kernels()
+        run_kernels(args.kernels)
         return
     if args.report:
         run_report(args.report)
