@@ -65,10 +65,11 @@ def parse():
                     help="run one workload's full protocol (step counts, precision / tangent comparisons, "
                          "adjoint gradients) and print a JSON summary; q2: biquadratic vs Q1 elements on "
                          "the dendrite2d_1024 box")
-    ap.add_argument("--kernels", nargs="?", const="alloy3d", default=None, choices=["alloy3d", "q2"],
+    ap.add_argument("--kernels", nargs="?", const="alloy3d", default=None, choices=["alloy3d", "q2", "pc"],
                     help="profiling case: a few residual / linearisation / tangent passes on a 256x192x64 "
                          "sub-box of the alloy workload (inputs > L2, about 5 GB on the device), or (q2) on "
-                         "a 1536^2 Q2 box of the 2D dendrite (about 2 GB)")
+                         "a 1536^2 Q2 box of the 2D dendrite (about 2 GB), or (pc) 2 preconditioner setups and "
+                         "3 applies (FP32 GMG) on the same alloy sub-box")
     return ap.parse_args()
 
 
@@ -81,6 +82,23 @@ def run_kernels(kind="alloy3d"):
 
     import paper_2006_16764_b300 as pkg
 
+    if kind == "pc":
+        w = synth.scaled(synth.workload(WORKLOAD), 256, 192, 64)
+        dev = torch.device("cuda", 0)
+        U0 = torch.tensor(synth.initial_state(w), device=dev)
+        U = U0 + 0.01 * torch.tensor(synth.uniform_pm1(3, w.mesh.n_dofs), device=dev)
+        r = torch.tensor(synth.uniform_pm1(4, w.mesh.n_dofs), device=dev)
+        h = pkg.Tusas(w.mesh, w.params)
+        h.set_state(U0, 0.0, w.dt)
+        z = torch.empty_like(r)
+        for _ in range(2):
+            h.precond_setup(U)
+        for _ in range(3):
+            h.precond_apply(r, z)
+        torch.cuda.synchronize()
+        print(json.dumps({"kernels": kind, "dofs": w.mesh.n_dofs, "elems": w.mesh.n_elems}))
+        h.close()
+        return
     if kind == "q2":
         base = synth.workload("dendrite2d_1024")
         mesh = synth.Mesh(2, 1536, 1536, 0, 400.0 / 1536, order=2)

@@ -13,6 +13,8 @@
 // equivalent. Operators, smoother and coarse levels run in FP32 or FP64 (T).
 #include <math.h>
 
+#include <utility>
+
 #include "precond.h"
 
 namespace tusas {
@@ -23,7 +25,15 @@ struct Pow3 {
 };
 
 // ---------------------------------------------------------------------------
-// fine-level stencil fill (element tiles, colours, fixed-order node sums)
+// fine-level stencil fill
+//
+// Node-centric gather: a CTA owns a box of nodes (FillTile), first computes
+// the 3^dim "pair-type" element values of both blocks for every element
+// touching the box (shared memory), then each thread sums the contributions of
+// its <= 2^dim elements in a fixed order and writes its full stencil rows once.
+// Elements on the box boundary are evaluated by both neighbouring CTAs (FP32
+// work, cheap); every stencil entry is written exactly once, without a
+// read-modify-write, so no colouring is needed and the result is deterministic.
 // ---------------------------------------------------------------------------
 template <typename T>
 struct FillArgs {
@@ -36,7 +46,18 @@ struct FillArgs {
   const double* U;
   const double* Un;
   T* st;        // [2][NS][nn]
-  int color, ctx, cty, ctz;
+};
+
+// node box of one CTA, one thread per node (256 threads; the 3D FP64 variant halves x, 128
+// threads, to fit its element values in shared memory)
+template <int DIM, typename T>
+struct FillTile {
+  static const int X = (DIM == 3 && sizeof(T) == 8) ? 16 : 32;
+  static const int Y = DIM == 3 ? 4 : 8;
+  static const int Z = DIM == 3 ? 2 : 1;
+  static const int EX = X + 1, EY = Y + 1, EZ = DIM == 3 ? Z + 1 : 1;  // element box
+  static const int NEL = EX * EY * EZ;
+  static const int THREADS = X * Y * Z;
 };
 
 template <typename T>
@@ -77,165 +98,144 @@ __device__ __forceinline__ void contract(const T* c, const T (*tab)[3][2], T* ou
   for (int i = 0; i < Pow3<DIM>::V; ++i) out[i] = cur[i];
 }
 
+// Pair-type values K[blk][p] of element (ex, ey, ez): the element matrix entry of local
+// nodes (a, b) is K[blk][p] with p_d = a_d + b_d per axis (the 1D mass and stiffness
+// factors are symmetric in a_d, b_d). Gauss-point coefficients of Eqs. (pref2), (preconc2).
 template <int DIM, int MODEL, typename T>
-__global__ void __launch_bounds__(Tile<DIM>::X * Tile<DIM>::Y * Tile<DIM>::Z) k_stencil_fill(const FillArgs<T> A) {
-  constexpr int TX = Tile<DIM>::X, TY = Tile<DIM>::Y, TZ = Tile<DIM>::Z;
-  constexpr int NX = TX + 1, NY = TY + 1, NZ = DIM == 3 ? TZ + 1 : 1;
-  constexpr int NT = NX * NY * NZ;
-  constexpr int NE = TX * TY * TZ;
+__device__ __forceinline__ void elem_pair_values(const FillArgs<T>& A, int ex, int ey, int ez, T* K0, T* K1) {
   constexpr int NN = 1 << DIM;
   constexpr int NH = NN / 2;
   constexpr int NS = Pow3<DIM>::V;
-  __shared__ T sphi[NT], su[NT], sphin[NT];
-  __shared__ T sK[NS][NE];  // element stencil values of one block at a time
   const DevMesh& m = A.m;
-  int b = blockIdx.x;
-  const int ix = b % A.ctx;
-  b /= A.ctx;
-  const int iy = b % A.cty;
-  const int iz = b / A.cty;
-  const int tile_x = 2 * ix + (A.color & 1);
-  const int tile_y = 2 * iy + ((A.color >> 1) & 1);
-  const int tile_z = DIM == 3 ? 2 * iz + ((A.color >> 2) & 1) : 0;
-  const int ex0 = tile_x * TX, ey0 = tile_y * TY, ez0 = tile_z * TZ;
-  for (int s = threadIdx.x; s < NT; s += NE) {
-    const int lx = s % NX, ly = (s / NX) % NY, lz = s / (NX * NY);
-    const int gx = ex0 + lx, gy = ey0 + ly, gz = ez0 + lz;
-    const bool ok = gx < m.nnx && gy < m.nny && gz < m.nnz;
-    const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
-    sphi[s] = ok ? (T)A.U[node] : T(0);
-    su[s] = ok ? (T)A.U[m.nn + node] : T(0);
-    sphin[s] = ok ? (T)A.Un[node] : T(0);
+  T nphi[NN], nu[NN], npn[NN];
+#pragma unroll
+  for (int a = 0; a < NN; ++a) {
+    const i64 node = (ex + (a & 1)) + (i64)m.nnx * ((ey + ((a >> 1) & 1)) + (i64)m.nny * (ez + ((a >> 2) & 1)));
+    nphi[a] = (T)__ldg(A.U + node);
+    nu[a] = (T)__ldg(A.U + m.nn + node);
+    npn[a] = (T)__ldg(A.Un + node);
   }
-  __syncthreads();
-  const int t = threadIdx.x;
-  const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-  const int ex = ex0 + lx, ey = ey0 + ly, ez = ez0 + lz;
-  const bool valid = ex < m.nx && ey < m.ny && (DIM == 2 || ez < m.nz);
-  T cmA[NN], ckA[NN], cmB[NN], ckB[NN], tmA[DIM][3][2];
-  if (valid) {
-    T nphi[NN], nu[NN], npn[NN];
+  T phi[NN], u[NN], phin[NN], gp[DIM][NH];
+  interp<DIM, true, T>(nphi, phi, gp, A.S);
+  interp<DIM, false, T>(nu, u, nullptr, A.S);
+  interp<DIM, false, T>(npn, phin, nullptr, A.S);
+  T cm1[NN], ck1[NN], cm2[NN], ck2[NN];
+  const T eps = (T)A.P.eps4, k = (T)A.P.k;
 #pragma unroll
-    for (int a = 0; a < NN; ++a) {
-      const int si = (lx + (a & 1)) + NX * ((ly + ((a >> 1) & 1)) + NY * (lz + ((a >> 2) & 1)));
-      nphi[a] = sphi[si];
-      nu[a] = su[si];
-      npn[a] = sphin[si];
-    }
-    T phi[NN], u[NN], phin[NN], gp[DIM][NH];
-    interp<DIM, true, T>(nphi, phi, gp, A.S);
-    interp<DIM, false, T>(nu, u, nullptr, A.S);
-    interp<DIM, false, T>(npn, phin, nullptr, A.S);
-    T cm1[NN], ck1[NN], cm2[NN], ck2[NN];
-    const T eps = (T)A.P.eps4, k = (T)A.P.k;
-#pragma unroll
-    for (int g = 0; g < NN; ++g) {
-      T q = 0, s4 = 0;
-#pragma unroll
-      for (int d = 0; d < DIM; ++d) {
-        const T pd = gp[d][remove_bit(g, d)];
-        q += pd * pd;
-        s4 += pd * pd * pd * pd;
-      }
-      T a = 1;
-      if ((double)q >= TUSAS_GUARD_Q) {
-        const T iq = t_rsqrt<T>(q) * t_rsqrt<T>(q);
-        a = (T)(1.0 - 3.0 * A.P.eps4) + T(4) * eps * s4 * iq * iq;
-      }
-      const T a2 = a * a;
-      const T B = T(1) + (T(1) - k) * u[g];
-      const T Ac = MODEL == 0 ? T(1) : T(0.5) * ((T(1) + k) - (T(1) - k) * phin[g]);
-      const T mob = MODEL == 0 ? T(1) : T(0.5) * (T(1) - phi[g]);
-      cm1[g] = A.w * (T)A.P.tau0 * B * a2 * (T)A.P.idt;
-      ck1[g] = A.w * A.theta * (T)(A.P.W0 * A.P.W0) * a2;
-      cm2[g] = A.w * Ac * (T)A.P.idt;
-      ck2[g] = A.w * A.theta * (T)A.P.D * mob;
-    }
-    // 1D tables: mass [p][g] and derivative products [p] (p: 0 = (0,0), 1 = (0,1), 2 = (1,1))
-    const T sq = (T)0.57735026918962576;
-    const T xi0 = (T(1) - sq) / T(2), xi1 = (T(1) + sq) / T(2);
-    T tm[DIM][3][2];
+  for (int g = 0; g < NN; ++g) {
+    T q = 0, s4 = 0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
-      tm[d][0][0] = (T(1) - xi0) * (T(1) - xi0);
-      tm[d][0][1] = (T(1) - xi1) * (T(1) - xi1);
-      tm[d][1][0] = xi0 * (T(1) - xi0);
-      tm[d][1][1] = xi1 * (T(1) - xi1);
-      tm[d][2][0] = xi0 * xi0;
-      tm[d][2][1] = xi1 * xi1;
+      const T pd = gp[d][remove_bit(g, d)];
+      q += pd * pd;
+      s4 += pd * pd * pd * pd;
     }
-    // element values K[p] per block, p = pair type per axis; stored one block at a time below
-#pragma unroll
-    for (int g = 0; g < NN; ++g) {
-      cmA[g] = cm1[g];
-      ckA[g] = ck1[g];
-      cmB[g] = cm2[g];
-      ckB[g] = ck2[g];
+    T a = 1;
+    if ((double)q >= TUSAS_GUARD_Q) {
+      const T iq = t_rsqrt<T>(q) * t_rsqrt<T>(q);
+      a = (T)(1.0 - 3.0 * A.P.eps4) + T(4) * eps * s4 * iq * iq;
     }
+    const T a2 = a * a;
+    const T B = T(1) + (T(1) - k) * u[g];
+    const T Ac = MODEL == 0 ? T(1) : T(0.5) * ((T(1) + k) - (T(1) - k) * phin[g]);
+    const T mob = MODEL == 0 ? T(1) : T(0.5) * (T(1) - phi[g]);
+    cm1[g] = A.w * (T)A.P.tau0 * B * a2 * (T)A.P.idt;
+    ck1[g] = A.w * A.theta * (T)(A.P.W0 * A.P.W0) * a2;
+    cm2[g] = A.w * Ac * (T)A.P.idt;
+    ck2[g] = A.w * A.theta * (T)A.P.D * mob;
+  }
+  // 1D tables: mass [p][g] (p: 0 = (0,0), 1 = (0,1), 2 = (1,1)); stiffness +-1/h^2
+  const T sq = (T)0.57735026918962576;
+  const T xi0 = (T(1) - sq) / T(2), xi1 = (T(1) + sq) / T(2);
+  T tm[DIM][3][2];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d)
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        tmA[d][p][0] = tm[d][p][0];
-        tmA[d][p][1] = tm[d][p][1];
-      }
+  for (int d = 0; d < DIM; ++d) {
+    tm[d][0][0] = (T(1) - xi0) * (T(1) - xi0);
+    tm[d][0][1] = (T(1) - xi1) * (T(1) - xi1);
+    tm[d][1][0] = xi0 * (T(1) - xi0);
+    tm[d][1][1] = xi1 * (T(1) - xi1);
+    tm[d][2][0] = xi0 * xi0;
+    tm[d][2][1] = xi1 * xi1;
   }
 #pragma unroll
   for (int blk = 0; blk < 2; ++blk) {
-    if (valid) {
-      const T* cm = blk == 0 ? cmA : cmB;
-      const T* ck = blk == 0 ? ckA : ckB;
-      T K[NS], tmp[NS], tk[DIM][3][2];
-      contract<DIM, T>(cm, tmA, K);
+    const T* cm = blk == 0 ? cm1 : cm2;
+    const T* ck = blk == 0 ? ck1 : ck2;
+    T* K = blk == 0 ? K0 : K1;
+    T tmp[NS], tk[DIM][3][2];
+    contract<DIM, T>(cm, tm, K);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) {
+    for (int d = 0; d < DIM; ++d) {
 #pragma unroll
-        for (int ee = 0; ee < DIM; ++ee) {
+      for (int ee = 0; ee < DIM; ++ee) {
 #pragma unroll
-          for (int p = 0; p < 3; ++p) {
-            const T kv = (p == 1 ? -A.ih2 : A.ih2);
-            tk[ee][p][0] = ee == d ? kv : tmA[ee][p][0];
-            tk[ee][p][1] = ee == d ? kv : tmA[ee][p][1];
-          }
+        for (int p = 0; p < 3; ++p) {
+          const T kv = (p == 1 ? -A.ih2 : A.ih2);
+          tk[ee][p][0] = ee == d ? kv : tm[ee][p][0];
+          tk[ee][p][1] = ee == d ? kv : tm[ee][p][1];
         }
-        contract<DIM, T>(ck, tk, tmp);
-#pragma unroll
-        for (int i = 0; i < NS; ++i) K[i] += tmp[i];
       }
+      contract<DIM, T>(ck, tk, tmp);
 #pragma unroll
-      for (int i = 0; i < NS; ++i) sK[i][t] = K[i];
+      for (int i = 0; i < NS; ++i) K[i] += tmp[i];
+    }
+  }
+}
+
+template <int DIM, int MODEL, typename T>
+__global__ void __launch_bounds__(256) k_stencil_fill(const FillArgs<T> A) {
+  using FT = FillTile<DIM, T>;
+  constexpr int NN = 1 << DIM;
+  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NEL = FT::NEL;
+  extern __shared__ __align__(16) unsigned char fill_smem[];
+  T* sK = reinterpret_cast<T*>(fill_smem);  // [2 NS][NEL]
+  const DevMesh& m = A.m;
+  const int nx0 = blockIdx.x * FT::X, ny0 = blockIdx.y * FT::Y, nz0 = blockIdx.z * FT::Z;
+  // element box: elements nx0 - 1 .. nx0 + X - 1 per axis (those touching the node box)
+  for (int le = threadIdx.x; le < NEL; le += blockDim.x) {
+    const int lx = le % FT::EX, ly = (le / FT::EX) % FT::EY, lz = le / (FT::EX * FT::EY);
+    const int ex = nx0 - 1 + lx, ey = ny0 - 1 + ly, ez = DIM == 3 ? nz0 - 1 + lz : 0;
+    const bool ok = ex >= 0 && ex < m.nx && ey >= 0 && ey < m.ny && (DIM == 2 || (ez >= 0 && ez < m.nz));
+    T K0[NS], K1[NS];
+    if (ok) {
+      elem_pair_values<DIM, MODEL, T>(A, ex, ey, ez, K0, K1);
     } else {
 #pragma unroll
-      for (int i = 0; i < NS; ++i) sK[i][t] = T(0);
+      for (int i = 0; i < NS; ++i) K0[i] = K1[i] = T(0);
     }
-    __syncthreads();
-    for (int s = threadIdx.x; s < NT; s += NE) {
-      const int nx_ = s % NX, ny_ = (s / NX) % NY, nz_ = s / (NX * NY);
-      const int gx = ex0 + nx_, gy = ey0 + ny_, gz = ez0 + nz_;
-      if (gx >= m.nnx || gy >= m.nny || gz >= m.nnz) continue;
-      T acc[NS];
 #pragma unroll
-      for (int o = 0; o < NS; ++o) acc[o] = T(0);
+    for (int i = 0; i < NS; ++i) {
+      sK[i * NEL + le] = K0[i];
+      sK[(NS + i) * NEL + le] = K1[i];
+    }
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % FT::X, ty = (threadIdx.x / FT::X) % FT::Y, tz = threadIdx.x / (FT::X * FT::Y);
+  const int ix = nx0 + tx, iy = ny0 + ty, iz = nz0 + tz;
+  if (ix >= m.nnx || iy >= m.nny || iz >= m.nnz) return;
+  const i64 node = ix + (i64)m.nnx * (iy + (i64)m.nny * iz);
 #pragma unroll
-      for (int a = 0; a < NN; ++a) {
-        const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
-        const int elx = nx_ - ax, ely = ny_ - ay, elz = nz_ - az;
-        if (elx >= 0 && elx < TX && ely >= 0 && ely < TY && elz >= 0 && elz < TZ) {
-          const int e = elx + TX * (ely + TY * elz);
+  for (int blk = 0; blk < 2; ++blk) {
+    T acc[NS];
 #pragma unroll
-          for (int bb = 0; bb < NN; ++bb) {
-            const int bx = bb & 1, by = (bb >> 1) & 1, bz = (bb >> 2) & 1;
-            const int o = (bx - ax + 1) + 3 * (by - ay + 1) + (DIM == 3 ? 9 * (bz - az + 1) : 0);
-            const int p = (ax + bx) + 3 * (ay + by) + (DIM == 3 ? 9 * (az + bz) : 0);
-            acc[o] += sK[p][e];
-          }
-        }
+    for (int o = 0; o < NS; ++o) acc[o] = T(0);
+    // element with local node a = (ax, ay, az) at this node sits at element-box index
+    // (tx + 1 - ax, ty + 1 - ay, tz + 1 - az); out-of-mesh elements hold zeros
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
+      const int ax = a & 1, ay = (a >> 1) & 1, az = (a >> 2) & 1;
+      const int le = (tx + 1 - ax) + FT::EX * ((ty + 1 - ay) + FT::EY * (DIM == 3 ? tz + 1 - az : 0));
+#pragma unroll
+      for (int bb = 0; bb < NN; ++bb) {
+        const int bx = bb & 1, by = (bb >> 1) & 1, bz = (bb >> 2) & 1;
+        const int o = (bx - ax + 1) + 3 * (by - ay + 1) + (DIM == 3 ? 9 * (bz - az + 1) : 0);
+        const int p = (ax + bx) + 3 * (ay + by) + (DIM == 3 ? 9 * (az + bz) : 0);
+        acc[o] += sK[(blk * NS + p) * NEL + le];
       }
-      const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
-#pragma unroll
-      for (int o = 0; o < NS; ++o) A.st[(blk * NS + o) * m.nn + node] += acc[o];
     }
-    __syncthreads();
+#pragma unroll
+    for (int o = 0; o < NS; ++o) A.st[(blk * NS + o) * m.nn + node] = acc[o];
   }
 }
 
@@ -297,62 +297,58 @@ static int grid_nodes(i64 n) {
   return (int)(g < 1 ? 1 : g);
 }
 
-// Galerkin coarse stencil: A_c(I, J) = sum_{i,j} P(i,I) A(i,j) P(j,J)
-template <int DIM, typename T>
-__global__ void k_rap(DevMesh mf, DevMesh mc, const T* __restrict__ stf, T* __restrict__ stc) {
+// Galerkin coarse stencil: A_c(I, J) = sum_{i,j} P(i,I) A(i,j) P(j,J). The fine stencil entry
+// A(i, i+o2) with i = 2I + o1 reaches the coarse offsets J - I of the (one or two per axis)
+// coarse nodes interpolating to 2I + o1 + o2. The offset o1 is a template parameter and the o2
+// loop is unrolled, so every accumulator index is a compile-time constant and the 3^dim
+// accumulators stay in registers.
+template <int DIM, typename T, int O1>
+__device__ __forceinline__ void rap_row(const DevMesh& mf, const T* __restrict__ stf, int cx, int cy, int cz,
+                                        T* acc) {
   constexpr int NS = Pow3<DIM>::V;
-  {
-    int cx, cy, cz;
-    i64 I;
-    if (!node3(mc, cx, cy, cz, I)) return;
-    for (int blk = 0; blk < 2; ++blk) {
-      T acc[NS];
+  constexpr int o1x = O1 % 3 - 1, o1y = (O1 / 3) % 3 - 1, o1z = DIM == 3 ? O1 / 9 - 1 : 0;
+  const int fx = 2 * cx + o1x, fy = 2 * cy + o1y, fz = 2 * cz + o1z;
+  if (fx < 0 || fx >= mf.nnx || fy < 0 || fy >= mf.nny || fz < 0 || fz >= mf.nnz) return;
+  constexpr float w1f = (o1x ? 0.5f : 1.f) * (o1y ? 0.5f : 1.f) * (o1z ? 0.5f : 1.f);
+  const T* sp = stf + fx + (i64)mf.nnx * (fy + (i64)mf.nny * fz);
 #pragma unroll
-      for (int o = 0; o < NS; ++o) acc[o] = T(0);
-      for (int o1 = 0; o1 < NS; ++o1) {
-        const int o1x = o1 % 3 - 1, o1y = (o1 / 3) % 3 - 1, o1z = DIM == 3 ? o1 / 9 - 1 : 0;
-        const int fx = 2 * cx + o1x, fy = 2 * cy + o1y, fz = 2 * cz + o1z;
-        if (fx < 0 || fx >= mf.nnx || fy < 0 || fy >= mf.nny || fz < 0 || fz >= mf.nnz) continue;
-        const T w1 = (o1x ? T(0.5) : T(1)) * (o1y ? T(0.5) : T(1)) * (o1z ? T(0.5) : T(1));
-        const i64 fi = fx + (i64)mf.nnx * (fy + (i64)mf.nny * fz);
+  for (int o2 = 0; o2 < NS; ++o2) {
+    const int o2x = o2 % 3 - 1, o2y = (o2 / 3) % 3 - 1, o2z = DIM == 3 ? o2 / 9 - 1 : 0;
+    const int rx = o1x + o2x, ry = o1y + o2y, rz = o1z + o2z;
+    const T v = T(w1f) * __ldg(sp + (i64)o2 * mf.nn);
+    // per axis: even r -> coarse offset r/2 (weight 1); odd r -> (r-1)/2 and (r+1)/2 (1/2 each)
 #pragma unroll
-        for (int o2 = 0; o2 < NS; ++o2) {
-          const T av = stf[(blk * NS + o2) * mf.nn + fi];
-          if (av == T(0)) continue;
-          const int o2x = o2 % 3 - 1, o2y = (o2 / 3) % 3 - 1, o2z = DIM == 3 ? o2 / 9 - 1 : 0;
-          const int r[3] = {o1x + o2x, o1y + o2y, o1z + o2z};
-          int lo[3], hi[3];
-          T wl[3], wh[3];
-#pragma unroll
-          for (int d = 0; d < 3; ++d) {
-            if ((r[d] & 1) == 0) {
-              lo[d] = hi[d] = r[d] / 2;
-              wl[d] = T(1);
-              wh[d] = T(0);
-            } else {
-              lo[d] = (r[d] - 1) / 2;
-              hi[d] = (r[d] + 1) / 2;
-              wl[d] = wh[d] = T(0.5);
-            }
-          }
-          const T v = w1 * av;
-#pragma unroll
-          for (int c = 0; c < (1 << DIM); ++c) {
-            const T wx = (c & 1) ? wh[0] : wl[0];
-            const T wy = (c & 2) ? wh[1] : wl[1];
-            const T wz = DIM == 3 ? ((c & 4) ? wh[2] : wl[2]) : T(1);
-            const T ww = wx * wy * wz;
-            if (ww == T(0)) continue;
-            const int jx = (c & 1) ? hi[0] : lo[0], jy = (c & 2) ? hi[1] : lo[1];
-            const int jz = DIM == 3 ? ((c & 4) ? hi[2] : lo[2]) : 0;
-            const int oc = (jx + 1) + 3 * (jy + 1) + (DIM == 3 ? 9 * (jz + 1) : 0);
-            acc[oc] += v * ww;
-          }
-        }
-      }
-#pragma unroll
-      for (int o = 0; o < NS; ++o) stc[(blk * NS + o) * mc.nn + I] = acc[o];
+    for (int c = 0; c < (1 << DIM); ++c) {
+      const int bx = c & 1, by = (c >> 1) & 1, bz = (c >> 2) & 1;
+      if (((rx & 1) == 0 && bx) || ((ry & 1) == 0 && by) || (DIM == 3 && (rz & 1) == 0 && bz)) continue;
+      const int jx = (rx & 1) ? (rx - 1) / 2 + bx : rx / 2;
+      const int jy = (ry & 1) ? (ry - 1) / 2 + by : ry / 2;
+      const int jz = DIM == 3 ? ((rz & 1) ? (rz - 1) / 2 + bz : rz / 2) : 0;
+      const T ww = ((rx & 1) ? T(0.5) : T(1)) * ((ry & 1) ? T(0.5) : T(1)) * (DIM == 3 && (rz & 1) ? T(0.5) : T(1));
+      acc[(jx + 1) + 3 * (jy + 1) + (DIM == 3 ? 9 * (jz + 1) : 0)] += v * ww;
     }
+  }
+}
+
+template <int DIM, typename T, int... O1>
+__device__ __forceinline__ void rap_rows(const DevMesh& mf, const T* __restrict__ stf, int cx, int cy, int cz, T* acc,
+                                         std::integer_sequence<int, O1...>) {
+  (rap_row<DIM, T, O1>(mf, stf, cx, cy, cz, acc), ...);
+}
+
+template <int DIM, typename T>
+__global__ void __launch_bounds__(256, 2) k_rap(DevMesh mf, DevMesh mc, const T* __restrict__ stf, T* __restrict__ stc) {
+  constexpr int NS = Pow3<DIM>::V;
+  int cx, cy, cz;
+  i64 I;
+  if (!node3(mc, cx, cy, cz, I)) return;
+  for (int blk = 0; blk < 2; ++blk) {
+    T acc[NS];
+#pragma unroll
+    for (int o = 0; o < NS; ++o) acc[o] = T(0);
+    rap_rows<DIM, T>(mf, stf + (i64)blk * NS * mf.nn, cx, cy, cz, acc, std::make_integer_sequence<int, NS>{});
+#pragma unroll
+    for (int o = 0; o < NS; ++o) stc[((i64)blk * NS + o) * mc.nn + I] = acc[o];
   }
 }
 
@@ -361,17 +357,18 @@ template <int DIM, typename T>
 __global__ void k_gersh(DevMesh m, const T* __restrict__ st, T* __restrict__ dinv, double* __restrict__ partials) {
   constexpr int NS = Pow3<DIM>::V;
   constexpr int C = NS / 2;
-  __shared__ double red[2][256];
-  double mx[2] = {0.0, 0.0};
+  __shared__ T red[2][256];
+  T mx[2] = {T(0), T(0)};
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < m.nn; i += (i64)gridDim.x * blockDim.x) {
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
-      double s = 0.0;
+      T s = T(0);
 #pragma unroll
-      for (int o = 0; o < NS; ++o) s += fabs((double)st[(blk * NS + o) * m.nn + i]);
-      const double c = (double)st[(blk * NS + C) * m.nn + i];
-      dinv[blk * m.nn + i] = (T)(1.0 / c);
-      mx[blk] = fmax(mx[blk], s / c);
+      for (int o = 0; o < NS; ++o) s += fabs(st[(blk * NS + o) * m.nn + i]);
+      const T c = st[(blk * NS + C) * m.nn + i];
+      const T ci = T(1) / c;
+      dinv[blk * m.nn + i] = ci;
+      mx[blk] = fmax(mx[blk], s * ci);
     }
   }
   red[0][threadIdx.x] = mx[0];
@@ -385,17 +382,30 @@ __global__ void k_gersh(DevMesh m, const T* __restrict__ st, T* __restrict__ din
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    partials[2 * blockIdx.x] = red[0][0];
-    partials[2 * blockIdx.x + 1] = red[1][0];
+    partials[2 * blockIdx.x] = (double)red[0][0];
+    partials[2 * blockIdx.x + 1] = (double)red[1][0];
   }
 }
 
+// out[b] = max over the nb per-block partial maxima (one block of 256 threads)
 __global__ void k_max_partials(int nb, const double* __restrict__ partials, double* __restrict__ out) {
-  if (threadIdx.x < 2) {
-    double v = 0.0;
-    for (int b = 0; b < nb; ++b) v = fmax(v, partials[2 * b + threadIdx.x]);
-    out[threadIdx.x] = v;
+  __shared__ double red[2][256];
+  double v0 = 0.0, v1 = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    v0 = fmax(v0, partials[2 * b]);
+    v1 = fmax(v1, partials[2 * b + 1]);
   }
+  red[0][threadIdx.x] = v0;
+  red[1][threadIdx.x] = v1;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) {
+      red[0][threadIdx.x] = fmax(red[0][threadIdx.x], red[0][threadIdx.x + w]);
+      red[1][threadIdx.x] = fmax(red[1][threadIdx.x], red[1][threadIdx.x + w]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x < 2) out[threadIdx.x] = red[threadIdx.x][0];
 }
 
 // ---------------------------------------------------------------------------
@@ -640,8 +650,6 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
     count_launches(1);
     return cudaGetLastError();
   }
-  cudaError_t e = cudaMemsetAsync(L0.st, 0, sizeof(T) * 2 * NS * m.nn, st);
-  if (e != cudaSuccess) return e;
   FillArgs<T> A;
   A.m = m;
   A.P = c.P;
@@ -659,38 +667,30 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
   A.U = U;
   A.Un = Un;
   A.st = (T*)L0.st;
-  const int ntx = c.ntx, nty = c.nty, ntz = c.ntz;
-  for (int col = 0; col < (1 << m.dim); ++col) {
-    const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
-    A.color = col;
-    A.ctx = (ntx - cx + 1) / 2;
-    A.cty = (nty - cy + 1) / 2;
-    A.ctz = m.dim == 3 ? (ntz - cz + 1) / 2 : 1;
-    const long long blocks = (long long)A.ctx * A.cty * A.ctz;
-    if (blocks <= 0) continue;
-    if (m.dim == 3) {
-      if (c.P.model == 0)
-        {
-          k_stencil_fill<3, 0, T><<<(unsigned)blocks, 128, 0, st>>>(A);
-          count_launches(1);
-        }
-      else
-        {
-          k_stencil_fill<3, 1, T><<<(unsigned)blocks, 128, 0, st>>>(A);
-          count_launches(1);
-        }
+  cudaError_t e = cudaSuccess;
+  if (m.dim == 3) {
+    using FT = FillTile<3, T>;
+    const size_t smem = sizeof(T) * 2 * 27 * FT::NEL;
+    const dim3 grid(ceil_div(m.nnx, FT::X), ceil_div(m.nny, FT::Y), ceil_div(m.nnz, FT::Z));
+    if (c.P.model == 0) {
+      e = cudaFuncSetAttribute(k_stencil_fill<3, 0, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_stencil_fill<3, 0, T><<<grid, FT::THREADS, smem, st>>>(A);
     } else {
-      if (c.P.model == 0)
-        {
-          k_stencil_fill<2, 0, T><<<(unsigned)blocks, 128, 0, st>>>(A);
-          count_launches(1);
-        }
-      else
-        {
-          k_stencil_fill<2, 1, T><<<(unsigned)blocks, 128, 0, st>>>(A);
-          count_launches(1);
-        }
+      e = cudaFuncSetAttribute(k_stencil_fill<3, 1, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      k_stencil_fill<3, 1, T><<<grid, FT::THREADS, smem, st>>>(A);
     }
+    count_launches(1);
+  } else {
+    using FT = FillTile<2, T>;
+    const size_t smem = sizeof(T) * 2 * 9 * FT::NEL;
+    const dim3 grid(ceil_div(m.nnx, FT::X), ceil_div(m.nny, FT::Y), 1);
+    if (c.P.model == 0)
+      k_stencil_fill<2, 0, T><<<grid, FT::THREADS, smem, st>>>(A);
+    else
+      k_stencil_fill<2, 1, T><<<grid, FT::THREADS, smem, st>>>(A);
+    count_launches(1);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -719,7 +719,7 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
         count_launches(1);
       }
     {
-      k_max_partials<<<1, 32, 0, st>>>(nb, gersh_partials, lmax_dev + 2 * l);
+      k_max_partials<<<1, 256, 0, st>>>(nb, gersh_partials, lmax_dev + 2 * l);
       count_launches(1);
     }
   }
