@@ -418,7 +418,7 @@ struct Coef2 {
 
 // r = D^-1 (b - A x) (or D^-1 b if x == nullptr, and then x = 0); d = r * it
 template <int DIM, typename T>
-__global__ void k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
+__global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
   constexpr int NS = Pow3<DIM>::V;
   {
@@ -441,7 +441,7 @@ __global__ void k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __rest
 
 // x += d; if !last: r -= D^-1 A d; dout = c1 d + c2 r
 template <int DIM, typename T>
-__global__ void k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
+__global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
   constexpr int NS = Pow3<DIM>::V;
   {
@@ -464,7 +464,7 @@ __global__ void k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __rest
 }
 
 template <int DIM, typename T>
-__global__ void k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, 6) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
   constexpr int NS = Pow3<DIM>::V;
   {

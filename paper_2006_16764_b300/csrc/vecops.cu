@@ -1,7 +1,12 @@
 // FP64 vector kernels of the Krylov / Newton path (GMRES inner products run on
 // the GPU, Sec. 4.3). Reductions are deterministic: a fixed partition of the
 // index range into reduce_blocks() chunks, a fixed in-block tree, and a
-// second pass that sums the per-block partials in index order.
+// second pass in which one warp per output sums the per-block partials (lane l
+// takes partials l, l + 32, ... in order, then a fixed shuffle tree).
+// The multi-dot splits the k vectors into groups of 4 over a second grid axis
+// (one block per chunk and group), which keeps few registers per thread and
+// many blocks per SM; each partial is still the chunk's sum in thread-stride
+// order and fixed in-block tree, whatever the grouping.
 #include "ops.h"
 
 namespace tusas {
@@ -94,26 +99,30 @@ cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st) {
 static const int RB = 296;  // reduction blocks: 2 per SM
 int reduce_blocks() { return RB; }
 
-template <int KM>
+template <int JG>
 __global__ void __launch_bounds__(VT) k_multidot(i64 n, int k, const double* __restrict__ X, i64 ld,
-                                                 const double* __restrict__ y, double* __restrict__ partials) {
-  __shared__ double red[VT / 32][KM];
-  double acc[KM];
+                                                 const double* __restrict__ y, double* __restrict__ partials,
+                                                 int km) {
+  __shared__ double red[VT / 32][JG];
+  const int j0 = blockIdx.y * JG;
+  const int kg = k - j0 < JG ? k - j0 : JG;  // vectors of this group
+  double acc[JG];
 #pragma unroll
-  for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+  for (int j = 0; j < JG; ++j) acc[j] = 0.0;
   const i64 chunk = (n + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < n ? lo + chunk : n;
+  const double* Xg = X + j0 * ld;
   for (i64 i = lo + threadIdx.x; i < hi; i += VT) {
     const double yi = y[i];
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) acc[j] = fma(X[j * ld + i], yi, acc[j]);
+    for (int j = 0; j < JG; ++j)
+      if (j < kg) acc[j] = fma(Xg[j * ld + i], yi, acc[j]);
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int j = 0; j < KM; ++j) {
-    if (j < k) {
+  for (int j = 0; j < JG; ++j) {
+    if (j < kg) {
       double v = acc[j];
 #pragma unroll
       for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
@@ -121,59 +130,38 @@ __global__ void __launch_bounds__(VT) k_multidot(i64 n, int k, const double* __r
     }
   }
   __syncthreads();
-  if (threadIdx.x < k) {
+  if (threadIdx.x < kg) {
     double s = 0.0;
 #pragma unroll
     for (int w = 0; w < VT / 32; ++w) s += red[w][threadIdx.x];
-    partials[blockIdx.x * (i64)KM + threadIdx.x] = s;
+    partials[blockIdx.x * (i64)km + j0 + threadIdx.x] = s;
   }
 }
 
+// out[j] = sum_b partials[b km + j]: warp j, fixed per-lane order and shuffle tree (blockDim = 32 k)
 __global__ void k_reduce_partials(int nb, int k, int km, const double* __restrict__ partials, double* __restrict__ out) {
-  const int j = threadIdx.x;
+  const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (j >= k) return;
   double s = 0.0;
-  for (int b = 0; b < nb; ++b) s += partials[b * (i64)km + j];
-  out[j] = s;
+  for (int b = lane; b < nb; b += 32) s += partials[b * (i64)km + j];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+  if (lane == 0) out[j] = s;
 }
 
 cudaError_t multidot(i64 n, int k, const double* X, i64 ld, const double* y, double* partials, double* out,
                      cudaStream_t st) {
   if (k <= 0 || k > 32) return cudaErrorInvalidValue;
-  int km;
+  // partials[b km + j]: km = 1 for a single dot, else 32 (fixed stride for every k)
+  const int km = k == 1 ? 1 : 32;
   if (k == 1) {
-    km = 1;
-    {
-      k_multidot<1><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
-      count_launches(1);
-    }
-  } else if (k <= 4) {
-    km = 4;
-    {
-      k_multidot<4><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
-      count_launches(1);
-    }
-  } else if (k <= 8) {
-    km = 8;
-    {
-      k_multidot<8><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
-      count_launches(1);
-    }
-  } else if (k <= 16) {
-    km = 16;
-    {
-      k_multidot<16><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
-      count_launches(1);
-    }
+    k_multidot<1><<<dim3(RB, 1), VT, 0, st>>>(n, k, X, ld, y, partials, km);
   } else {
-    km = 32;
-    {
-      k_multidot<32><<<RB, VT, 0, st>>>(n, k, X, ld, y, partials);
-      count_launches(1);
-    }
+    k_multidot<4><<<dim3(RB, (k + 3) / 4), VT, 0, st>>>(n, k, X, ld, y, partials, km);
   }
+  count_launches(1);
   {
-    k_reduce_partials<<<1, 32, 0, st>>>(RB, k, km, partials, out);
+    k_reduce_partials<<<1, 32 * k, 0, st>>>(RB, k, km, partials, out);
     count_launches(1);
   }
   return cudaGetLastError();
