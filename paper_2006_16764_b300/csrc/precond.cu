@@ -640,7 +640,6 @@ void Precond::destroy() {
 template <typename T>
 cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st) {
   const DevMesh& m = c.m;
-  const int NS = m.dim == 3 ? 27 : 9;
   PrecondLevel& L0 = lv[0];
   if (m.order == 2) {
     // point Jacobi: element pass for diag(M11), diag(M22), then the reciprocals
