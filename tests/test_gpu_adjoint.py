@@ -38,12 +38,13 @@ def test_adjoint_matches_oracle_adjoint(kind):
     st = h.forward(dev(U0), 0.0, dt, n, 2)
     assert st["converged"]
     UN = host(h.get_state(dev(np.zeros_like(U0))))
-    assert np.abs(UN - states[-1]).max() <= 1e-9 * np.abs(states[-1]).max()
+    assert np.abs(UN - states[-1]).max() <= 1e-11 * np.abs(states[-1]).max()
     tg0 = dev(np.zeros_like(U0))
     ge, gd, ast = h.adjoint(dev(w), dev(d0), tg0, rtol=1e-12)
-    assert abs(ge - g_eps) <= 1e-7 * abs(g_eps)
-    assert abs(gd - g0 @ d0) <= 1e-7 * abs(g0 @ d0)
-    assert np.abs(host(tg0) - g0).max() <= 1e-7 * np.abs(g0).max()
+    # measured: dS/d eps4 within 3e-13 / 4e-13, dS/dU_0 within 9e-10 / 3e-13 (pure / alloy)
+    assert abs(ge - g_eps) <= 1e-10 * abs(g_eps)
+    assert abs(gd - g0 @ d0) <= 1e-8 * abs(g0 @ d0)
+    assert np.abs(host(tg0) - g0).max() <= 1e-8 * np.abs(g0).max()
     # the state is restored to U_N
     assert np.array_equal(host(h.get_state(dev(np.zeros_like(U0)))), UN)
 
