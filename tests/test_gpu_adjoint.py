@@ -14,6 +14,12 @@ pytestmark = pytest.mark.gpu
 
 
 def _problem(kind):
+    if kind == "pure16":
+        # the 16 x 16 case of the adjoint check against the oracle's direct-solve (dense Jacobian) adjoint
+        mesh = Mesh(2, 16, 16, 0, 1.25)
+        prm = Params(model=0, eps4=0.05, lam=3.19, D=2.0, Delta=0.65, precond=1, jvp_mode=1, newton_rtol=1e-13)
+        U0f = lambda p: synth.seed_state(mesh, p, radius=8.0)
+        return mesh, prm, U0f, 0.5, 3
     if kind == "pure":
         mesh = Mesh(2, 10, 10, 0, 2.0)
         prm = Params(model=0, eps4=0.04, lam=3.19, D=2.0, Delta=0.6, precond=1, jvp_mode=1, newton_rtol=1e-13)
@@ -25,7 +31,7 @@ def _problem(kind):
     return mesh, prm, U0f, 0.3, 2
 
 
-@pytest.mark.parametrize("kind", ["pure", "alloy"])
+@pytest.mark.parametrize("kind", ["pure", "pure16", "alloy"])
 def test_adjoint_matches_oracle_adjoint(kind):
     mesh, prm, U0f, dt, n = _problem(kind)
     U0 = U0f(prm)
