@@ -5,15 +5,17 @@
  *
  * The library evaluates, on one GPU, the discrete residual F(U) of the coupled
  * phase-field / solute (or dimensionless temperature) system on a structured
- * box of Q1 quadrilaterals or hexahedra (Sec. 2.1.1, Eqs. pf2, conc2, gs, jat,
- * with the theta-method of Eqs. dpf / theta at theta = 1), its Jacobian action
- * (finite difference, Eq. JFmatvec, or an exact tangent), the transposed
- * action, the block-diagonal preconditioner of Eq. (pre) and a Newton-Krylov
- * time step (Sec. 2.2, 2.3).
+ * box of Q1 quadrilaterals or hexahedra, or Q2 quadrilaterals (Sec. 2.1.1,
+ * Eqs. pf2, conc2, gs, jat, with the theta-method of Eqs. dpf, dc, theta), its
+ * Jacobian action (finite difference, Eq. JFmatvec, or an exact tangent), the
+ * transposed action, the block-diagonal preconditioner of Eq. (pre), a
+ * Newton-Krylov time step (Sec. 2.2, 2.3) and a discrete adjoint through a
+ * sequence of steps.
  *
  * Conventions for every entry point:
  *   - vectors are FP64 arrays of length 2*N_nodes, field-major
- *     [phi(0..N_nodes-1) ; u(0..N_nodes-1)], node index i + (nx+1)(j + (ny+1)k);
+ *     [phi(0..N_nodes-1) ; u(0..N_nodes-1)], node index i + nnx (j + nny k) with
+ *     nnx = order nx + 1, nny = order ny + 1 (tusas_mesh);
  *   - vector pointers are caller-owned DEVICE memory of the handle's device
  *     unless an entry point says otherwise; the library never frees them;
  *   - work is enqueued on the handle's stream (tusas_set_stream) and is
@@ -69,7 +71,9 @@ typedef struct tusas_params {
   int jvp_mode;          /* Newton-Krylov Jacobian action: 0 finite difference, 1 exact tangent */
   int precond;           /* 0 none, 1 point Jacobi, 2 block Jacobi with geometric multigrid */
   int smoother_fp32;     /* multigrid operators, smoother and coarse levels in FP32 (1) or FP64 (0) */
-  int gmres_restart, gmres_maxit, newton_maxit;
+  int gmres_restart;     /* Krylov vectors per cycle, 1..30 */
+  int gmres_maxit;       /* GMRES iterations per Newton iteration (a truncated solve is still a Newton direction) */
+  int newton_maxit;
   double newton_rtol, newton_atol;
   double eta0, eta_min, eta_max, gamma, omega;   /* forcing terms, Eqs. force1..forcing */
   int mg_levels, cheb_degree, coarse_degree, linesearch_max;

@@ -865,10 +865,7 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
 }
 
 cudaError_t Precond::apply(const double* r, double* z, cudaStream_t st) {
-  if (kind == 0) {
-    if (lv.empty()) return cudaErrorInvalidValue;
-    return cudaErrorInvalidValue;
-  }
+  if (kind == 0 || lv.empty()) return cudaErrorInvalidValue;  // identity is applied by the caller
   return fp32 ? apply_t<float>(r, z, st) : apply_t<double>(r, z, st);
 }
 

@@ -44,7 +44,7 @@ __device__ __forceinline__ double gp_last_coord(const DevMesh& m, int e_last, in
 
 template <int MODE>
 struct MinBlocks {
-  static const int V = MODE == 2 ? 4 : (MODE == 3 ? 3 : 2);  // tangent: 4 CTAs / SM, adjoint: 3
+  static const int V = MODE == 2 || MODE == 3 ? 3 : 2;  // tangent and adjoint: 3 CTAs / SM (no spills)
 };
 
 template <int DIM, int MODEL, int MODE>
