@@ -366,6 +366,28 @@ def run_report(name):
                             "forward_s": t1 - t0, "adjoint_s": t2 - t1,
                             "forward_gmres": pb.last_forward["gmres_its"], "adjoint_gmres": pb.last_adjoint["gmres_its"]})
         out["samples"] = samples
+        # the same 8 samples at once: 8 handles on 8 streams, one host thread each
+        from paper_2006_16764_b300.adjoint import solid_fraction_batch
+
+        probs = []
+        for _ in samples:
+            s_ = torch.cuda.Stream(dev)
+            probs.append(SolidFractionProblem(
+                pkg.Tusas(w.mesh, prm, stream=s_), prm, pb.initial_state, pb.dU0_ddelta, pb.w, c, 0.0, w.dt,
+                w.steps, 10, 1e-12, stream=s_))
+        sam = [(x["eps4"], x["Delta"]) for x in samples]
+        solid_fraction_batch(probs[:1], sam[:1])  # allocate the first handle's checkpoints outside the timing
+        t0 = time.perf_counter()
+        res = solid_fraction_batch(probs, sam)
+        t1 = time.perf_counter()
+        out["batch_of_8"] = {
+            "seconds": t1 - t0,
+            "sequential_seconds": sum(x["forward_s"] + x["adjoint_s"] for x in samples),
+            "max_abs_diff_vs_sequential": max(
+                max(abs(r_["S"] - x["S"]), abs(r_["dS_deps4"] - x["dS_deps4"]), abs(r_["dS_dDelta"] - x["dS_dDelta"]))
+                for r_, x in zip(res, samples))}
+        for p_ in probs:
+            p_.handle.close()
         # central differences (h = 1e-6) for the first sample, Newton tolerance 1e-13
         hh = 1e-6
         s0 = samples[0]

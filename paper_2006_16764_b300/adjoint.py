@@ -81,3 +81,35 @@ class SolidFractionProblem:
     adj_rtol: float = 1e-10
     last_forward: dict = None
     last_adjoint: dict = None
+    stream: object = None  # the handle's torch.cuda.Stream (solid_fraction_batch)
+
+
+def solid_fraction_batch(problems, samples):
+    """S and its discrete-adjoint gradients for several (eps4, Delta) samples at once.
+
+    Problem i (its own handle, created on its own stream ``problems[i].stream``)
+    takes ``samples[i]``; one host thread drives each handle, so the kernels of
+    all samples share the GPU (the library releases the interpreter lock in
+    every call and keeps no global state between handles). Returns a list of
+    dicts with S, dS/d eps4, dS/d Delta and the forward / adjoint statistics;
+    each sample gives bitwise the same numbers as a sequential run.
+    """
+    from concurrent.futures import ThreadPoolExecutor
+
+    torch.cuda.synchronize()
+
+    def one(pb, sample):
+        e4, dl = float(sample[0]), float(sample[1])
+        with torch.cuda.stream(pb.stream):
+            prm = dataclasses.replace(pb.params, eps4=e4, Delta=dl)
+            pb.handle.set_params(prm)
+            U0 = pb.initial_state(dl)
+            fw = pb.handle.forward(U0, pb.t0, pb.dt, pb.nsteps, pb.ckpt_every)
+            UN = torch.empty_like(U0)
+            pb.handle.get_state(UN)
+            S = pb.handle.dot(pb.w, UN) + pb.c
+            ge, gd, st = pb.handle.adjoint(pb.w, pb.dU0_ddelta, rtol=pb.adj_rtol)
+        return {"eps4": e4, "Delta": dl, "S": S, "dS_deps4": ge, "dS_dDelta": gd, "forward": fw, "adjoint": st}
+
+    with ThreadPoolExecutor(max_workers=len(problems)) as ex:
+        return list(ex.map(one, problems, samples))

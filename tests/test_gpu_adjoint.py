@@ -94,3 +94,34 @@ def test_autograd_function_matches_central_differences():
     fd_d = (S_at(prm.eps4, prm.Delta + hh) - S_at(prm.eps4, prm.Delta - hh)) / (2 * hh)
     assert abs(float(ge) - fd_e) <= 1e-5 * abs(fd_e)
     assert abs(float(gd) - fd_d) <= 1e-5 * abs(fd_d)
+
+
+def test_concurrent_samples_match_sequential_bitwise():
+    """solid_fraction_batch: several samples on their own handles and streams at once give
+    bitwise the numbers of one-at-a-time runs (deterministic kernels, no shared state)."""
+    import torch
+
+    import paper_2006_16764_b300 as pkg
+    from paper_2006_16764_b300.adjoint import SolidFractionProblem, solid_fraction_batch, solid_fraction_weights
+
+    mesh, prm, U0f, dt, n = _problem("alloy")
+    w, c = solid_fraction_weights(mesh)
+    nn = mesh.n_nodes
+    d0 = dev(np.concatenate([np.zeros(nn), -np.ones(nn)]))
+    tw = dev(w)
+    init = lambda d: dev(U0f(dataclasses.replace(prm, Delta=d)))
+    samples = [(0.03, 0.5), (0.045, 0.42), (0.02, 0.61)]
+    probs = []
+    for _ in samples:
+        s = torch.cuda.Stream()
+        probs.append(SolidFractionProblem(pkg.Tusas(mesh, prm, stream=s), prm, init, d0, tw, c, 0.0, dt, n, 1, 1e-12,
+                                          stream=s))
+    seq = [solid_fraction_batch([pb], [sm])[0] for pb, sm in zip(probs, samples)]
+    conc = solid_fraction_batch(probs, samples)
+    for a, b in zip(seq, conc):
+        assert (a["S"], a["dS_deps4"], a["dS_dDelta"]) == (b["S"], b["dS_deps4"], b["dS_dDelta"])
+    # and the gradients are the oracle's
+    st = OA.forward(mesh, dataclasses.replace(prm, eps4=0.045, Delta=0.42), U0f(dataclasses.replace(prm, Delta=0.42)),
+                    0.0, dt, n)
+    g_eps, g0 = OA.gradient(mesh, dataclasses.replace(prm, eps4=0.045, Delta=0.42), st, 0.0, dt, w)
+    assert abs(conc[1]["dS_deps4"] - g_eps) <= 1e-10 * abs(g_eps)
