@@ -147,10 +147,14 @@ int tusas_jvp_fd(tusas_handle* h, const double* U, const double* v, double* Jv);
 int tusas_jtvp(tusas_handle* h, const double* U, const double* w, double* JTw);
 
 /* (dF/dU^n)^T w at U, with the stored U^n: the coupling of consecutive time
- * steps in a discrete adjoint. theta = 1 only (TUSAS_EINVAL otherwise). */
+ * steps in a discrete adjoint (time terms, and for theta < 1 the level-n
+ * spatial terms weighted 1 - theta). TUSAS_EINVAL for theta < 1 with
+ * phihat_form 0, where F also depends on U^{n-1}. */
 int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* out);
 
-/* dF/dp at U for parameter `which` (0 = eps4, the anisotropy of Eq. gs); theta = 1 only. */
+/* dF/dp at U for parameter `which` (0 = eps4, the anisotropy of Eq. gs), through the time
+ * term and the flux at both time levels of the theta-method. TUSAS_EINVAL for theta < 1 with
+ * phihat_form 0. */
 int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF);
 
 /* Build the preconditioner of Eq. (pre) (blocks of Eqs. pref2 / preconc2)
@@ -162,7 +166,8 @@ int tusas_precond_setup(tusas_handle* h, const double* U);
  * r and z are FP64 device vectors and may not alias. */
 int tusas_precond_apply(tusas_handle* h, const double* r, double* z);
 
-/* One backward-Euler step of size dt: solve F(U; U^n) = 0 by Newton-Krylov
+/* One time step of size dt (backward Euler at theta = 1, the theta-method of Eqs. dpf / dc
+ * otherwise): solve F(U; U^n) = 0 by Newton-Krylov
  * (Sec. 2.2/2.3: right-preconditioned restarted GMRES, forcing terms,
  * backtracking line search) from U = U^n, then U^n <- U, t^n <- t^n + dt.
  * Synchronises; fills *stats if non-NULL. On TUSAS_ENOCONV the state is
@@ -171,7 +176,7 @@ int tusas_step(tusas_handle* h, tusas_stats* stats);
 
 /* Forward sweep for a discrete adjoint (no counterpart in the paper, whose
  * solver needs only F and J v): set the state to U0 (host or device) at t0,
- * take nsteps backward-Euler steps of size dt with tusas_step, and record
+ * take nsteps steps of size dt with tusas_step (any theta; phihat_form 1 when theta < 1), and record
  * U_0, U_c, U_2c, ... (c = ckpt_every) in handle-owned device memory. The
  * state becomes U_N. *total (if non-NULL) sums the step statistics.
  * Synchronises. Returns the first failing step's code. */

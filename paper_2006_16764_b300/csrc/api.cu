@@ -459,7 +459,7 @@ int tusas_jtvp_prev(tusas_handle* h, const double* U, const double* w, double* o
   int rc = ready(h);
   if (rc) return rc;
   if (!U || !w || !out || out == U || out == w) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
-  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "(dF/dU^n)^T w is implemented for theta = 1 only");
+  if (h->ec.P.phihat_old) return fail(h, TUSAS_EINVAL, "(dF/dU^n)^T w needs phihat_form 1 when theta < 1");
   const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_PREV_T, h->ec, U, h->Un, w, out, nullptr, h->st));
   tend(h, TUSAS_T_ADJOINT, t0);
@@ -471,7 +471,7 @@ int tusas_dFdp(tusas_handle* h, const double* U, int which, double* dF) {
   if (rc) return rc;
   if (!U || !dF || U == dF) return fail(h, TUSAS_EINVAL, "null or aliased vectors");
   if (which != 0) return fail(h, TUSAS_EINVAL, "only which = 0 (eps4) is available");
-  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "dF/dp is implemented for theta = 1 only");
+  if (h->ec.P.phihat_old) return fail(h, TUSAS_EINVAL, "dF/dp needs phihat_form 1 when theta < 1");
   const size_t t0 = tbeg(h);
   TCK(tusas::elem_run(tusas::M_DEPS, h->ec, U, h->Un, nullptr, dF, nullptr, h->st));
   tend(h, TUSAS_T_ADJOINT, t0);
@@ -794,7 +794,8 @@ int set_state_dev(tusas_handle* h, const double* U, double t) {
 extern "C" int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int nsteps, int ckpt_every,
                              tusas_stats* total) {
   if (!h || !U0 || nsteps < 1 || ckpt_every < 1) return fail(h, TUSAS_EINVAL, "bad forward arguments");
-  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "the discrete adjoint is implemented for theta = 1 only");
+  if (h->prm.theta != 1.0 && h->prm.phihat_form == 0)
+    return fail(h, TUSAS_EINVAL, "the discrete adjoint needs phihat_form 1 when theta < 1");
   int rc = tusas_set_state(h, U0, t0, dt);
   if (rc) return rc;
   const size_t nck = (size_t)(nsteps + ckpt_every - 1) / ckpt_every + 1;
@@ -837,7 +838,8 @@ extern "C" int tusas_adjoint(tusas_handle* h, const double* w, const double* d0,
                              double* g0, double adj_rtol, tusas_stats* stats) {
   if (!h || !w || !grad_eps4) return fail(h, TUSAS_EINVAL, "null argument");
   if (h->fw_steps < 1) return fail(h, TUSAS_EINVAL, "call tusas_forward first");
-  if (h->prm.theta != 1.0) return fail(h, TUSAS_EINVAL, "the discrete adjoint is implemented for theta = 1 only");
+  if (h->prm.theta != 1.0 && h->prm.phihat_form == 0)
+    return fail(h, TUSAS_EINVAL, "the discrete adjoint needs phihat_form 1 when theta < 1");
   if (!(adj_rtol > 0.0)) return fail(h, TUSAS_EINVAL, "adj_rtol must be positive");
   const int N = h->fw_steps, c = h->fw_every;
   const double t0 = h->fw_t0, dt = h->fw_dt;

@@ -296,21 +296,33 @@ __device__ __forceinline__ void spatial_old(const DevPhys& P, double phi, double
   for (int d = 0; d < DIM; ++d) o.fu[d] = Dq * g[d];
 }
 
+// d/d eps4 of the anisotropic flux W^2 a(p) (a + 16 eps (n_i^2 - sn)) p_i, scaled by w.
+template <int DIM>
+__device__ __forceinline__ void flux_deps(const DevPhys& P, const double* p, double w, double* f) {
+  Aniso<DIM> An;
+  An.eval(p, P.eps4);
+  const double ae = An.r == 0.0 ? 0.0 : fma(4.0, An.sn, -3.0);
+  const double W2 = w * P.W0 * P.W0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    const double md = An.n2[d] - An.sn;
+    f[d] += W2 * p[d] * (ae * fma(16.0 * P.eps4, md, An.a) + An.a * fma(16.0, md, ae));
+  }
+}
+
 // d(integrands)/d eps4 at one Gauss point (Eq. gs differentiated in eps4, through
-// the flux and the tau(n) time term). tf1: difference-of-products time term.
+// the flux and the tau(n) time term). tf1: difference-of-products time term; pn is
+// grad(phi^n), used by tf1 and, for theta < 1, by the level-n flux weighted (1 - theta).
 template <int DIM>
 __device__ __forceinline__ void gp_deps(const DevPhys& P, bool tf1, double phi, double u, double dphi, double du,
                                         const double* p, const double* pn, GPOut<DIM>& o) {
   Aniso<DIM> An;
   An.eval(p, P.eps4);
   const double ae = An.r == 0.0 ? 0.0 : fma(4.0, An.sn, -3.0);
-  const double W2 = P.W0 * P.W0;
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    const double md = An.n2[d] - An.sn;
-    o.fphi[d] = W2 * p[d] * (ae * fma(16.0 * P.eps4, md, An.a) + An.a * fma(16.0, md, ae));
-    o.fu[d] = 0.0;
-  }
+  for (int d = 0; d < DIM; ++d) o.fphi[d] = o.fu[d] = 0.0;
+  flux_deps<DIM>(P, p, P.theta, o.fphi);
+  if (P.theta != 1.0) flux_deps<DIM>(P, pn, 1.0 - P.theta, o.fphi);
   const double B = fma(1.0 - P.k, u, 1.0);
   if (!tf1) {
     o.sphi = P.tau0 * B * dphi * P.idt * 2.0 * An.a * ae;
@@ -322,6 +334,46 @@ __device__ __forceinline__ void gp_deps(const DevPhys& P, bool tf1, double phi, 
     o.sphi = P.tau0 * P.idt * 2.0 * (B * An.a * ae * phi - Bn * Ao.a * aoe * (phi - dphi));
   }
   o.su = 0.0;
+}
+
+// Transposed linearisation of the level-n spatial integrands weighted (1 - theta)
+// (spatial_old) at (phi^n, u^n, grad phi^n = pn, grad u^n = gn, G4 at t^n), applied to
+// the adjoint fields (w0, grad w0 = gw0, w1, grad w1 = gw1) and added to o.
+template <int DIM, int MODEL>
+__device__ __forceinline__ void old_spatial_t(const DevPhys& P, double phin, double un, const double* pn,
+                                              const double* gn, double G4, double w0, const double* gw0,
+                                              const double* gw1, GPOut<DIM>& o) {
+  const double wt = 1.0 - P.theta;
+  Aniso<DIM> A;
+  A.eval(pn, P.eps4);
+  const double eps = P.eps4, a2 = A.a * A.a;
+  const double om = 1.0 - phin * phin;
+  // -d(bulk)/d phi and -d(bulk)/d u, bulk = phi - phi^3 - lam (1 - phi^2)^2 (u + G4)
+  const double sphi = -((1.0 - 3.0 * phin * phin) + 4.0 * P.lam * phin * om * (un + G4));
+  const double su = P.lam * om * om;
+  const double qp = MODEL == 0 ? 0.0 : -0.5 * P.D;  // D dq/dphi
+  const double q = MODEL == 0 ? P.D : 0.5 * P.D * (1.0 - phin);
+  double gdot = 0.0;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) gdot = fma(gn[d], gw1[d], gdot);
+  o.sphi = fma(wt, fma(sphi, w0, qp * gdot), o.sphi);
+  o.su = fma(wt * su, w0, o.su);
+  // flux Hessian, as in pointwise()
+  const double e32a = 32.0 * eps * A.a, e256 = 256.0 * eps * eps, e16a = 16.0 * eps * A.a;
+  const double W2 = wt * P.W0 * P.W0;
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    double hx = 0.0;
+#pragma unroll
+    for (int j = 0; j < DIM; ++j) {
+      const double mi = A.n2[i] - A.sn, mj = A.n2[j] - A.sn;
+      double v = A.n[i] * A.n[j] * (e32a * (A.sn - A.n2[i] - A.n2[j]) + e256 * mi * mj);
+      if (i == j) v += a2 + e16a * (3.0 * A.n2[i] - A.sn);
+      hx = fma(v, gw0[j], hx);
+    }
+    o.fphi[i] = fma(W2, hx, o.fphi[i]);
+    o.fu[i] = fma(wt * q, gw1[i], o.fu[i]);
+  }
 }
 
 // Integrands of (dF/dU^n)^T w at one Gauss point: (w0, w1) the values of the

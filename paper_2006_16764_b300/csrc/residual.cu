@@ -165,11 +165,21 @@ elem_kernel(const ElemArgs A) {
       interp<DIM, true>(nu, u, gu, A.S);
       interp<DIM, false, double>(ndp, dphi, nullptr, A.S);
       interp<DIM, false, double>(ndu, du, nullptr, A.S);
-      if (tf1) {
+      // grad(phi^n): literal time term, or the level-n flux of the theta-method in dF/d eps4 and
+      // (dF/dU^n)^T w; grad(u^n) for the latter
+      const bool oldn = (MODE == M_DEPS || MODE == M_PREV_T) && A.P.theta != 1.0;
+      double gun[DIM][NH];
+      if (tf1 || oldn) {
         double npn[NN], vpn[NN];
 #pragma unroll
         for (int a = 0; a < NN; ++a) npn[a] = sU[4][sidx[a]];
         interp<DIM, true>(npn, vpn, gpn, A.S);
+      }
+      if (MODE == M_PREV_T && oldn) {
+        double nun[NN], vun[NN];
+#pragma unroll
+        for (int a = 0; a < NN; ++a) nun[a] = sU[1][sidx[a]] - sU[3][sidx[a]];
+        interp<DIM, true>(nun, vun, gun, A.S);
       }
       double pho[NN];
       if ((MODE == M_RES || MODE == M_RES_LIN) && A.P.phihat_old) {
@@ -200,7 +210,7 @@ elem_kernel(const ElemArgs A) {
         for (int d = 0; d < DIM; ++d) {
           p[d] = gp[d][remove_bit(g, d)];
           gg[d] = gu[d][remove_bit(g, d)];
-          pn[d] = tf1 ? gpn[d][remove_bit(g, d)] : 0.0;
+          pn[d] = (tf1 || oldn) ? gpn[d][remove_bit(g, d)] : 0.0;
         }
         double G4 = 0.0;
         if (MODEL == 1 && A.P.has_g4) {
@@ -223,6 +233,18 @@ elem_kernel(const ElemArgs A) {
 #pragma unroll
           for (int d = 0; d < DIM; ++d) gw[d] = gw1[d][remove_bit(g, d)];
           gp_prev_t<DIM, MODEL>(A.P, tf1, phi[g], u[g], dphi[g], du[g], p, pn, w0[g], w1[g], gw, o);
+          if (oldn) {
+            double gn[DIM], gv0[DIM];
+#pragma unroll
+            for (int d = 0; d < DIM; ++d) {
+              gn[d] = gun[d][remove_bit(g, d)];
+              gv0[d] = gw0[d][remove_bit(g, d)];
+            }
+            const double G4n = (MODEL == 1 && A.P.has_g4)
+                                   ? (gp_last_coord<DIM>(m, e_last, g) - A.P.zT - A.P.Vp * (A.P.t_new - A.P.dt)) / A.P.lT
+                                   : 0.0;
+            old_spatial_t<DIM, MODEL>(A.P, phi[g] - dphi[g], u[g] - du[g], pn, gn, G4n, w0[g], gv0, gw, o);
+          }
         }
         s0[g] = o.sphi;
         s1[g] = o.su;

@@ -236,8 +236,10 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
 #pragma unroll
       for (int a = 0; a < NL; ++a) nd[a] = sU[3 * NT + sidx[a]];
       q2_interp<false>(T, nd, du, nullptr, nullptr);
+      // grad(phi^n) (literal time term; level-n flux of the theta-method in the adjoint modes)
+      const bool oldn = (MODE == M_DEPS || MODE == M_PREV_T) && A.P.theta != 1.0;
       double pnx[NL], pny[NL], pnv[NL];
-      if (tf1 && MODE != M_OLD && MODE != M_DIAG) {
+      if ((tf1 || oldn) && MODE != M_OLD && MODE != M_DIAG) {
 #pragma unroll
         for (int a = 0; a < NL; ++a) nd[a] = sU[4 * NT + sidx[a]];
         q2_interp<true>(T, nd, pnv, pnx, pny);
@@ -254,11 +256,16 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
 #pragma unroll
         for (int g = 0; g < NL; ++g) pho[g] = 0.0;
       }
-      double w0[NL], w1[NL], w1x[NL], w1y[NL];
+      double w0[NL], w0x[NL], w0y[NL], w1[NL], w1x[NL], w1y[NL], unv[NL], unx[NL], uny[NL];
+      if (MODE == M_PREV_T && oldn) {
+#pragma unroll
+        for (int a = 0; a < NL; ++a) nd[a] = sU[NT + sidx[a]] - sU[3 * NT + sidx[a]];
+        q2_interp<true>(T, nd, unv, unx, uny);
+      }
       if (MODE == M_PREV_T) {
 #pragma unroll
         for (int a = 0; a < NL; ++a) nd[a] = sV[sidx[a]];
-        q2_interp<false>(T, nd, w0, nullptr, nullptr);
+        q2_interp<true>(T, nd, w0, w0x, w0y);
 #pragma unroll
         for (int a = 0; a < NL; ++a) nd[a] = sV[NT + sidx[a]];
         q2_interp<true>(T, nd, w1, w1x, w1y);
@@ -301,6 +308,13 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
         } else {  // M_PREV_T
           const double gw[2] = {w1x[g], w1y[g]};
           gp_prev_t<2, MODEL>(P, tf1, phi[g], u[g], dphi[g], du[g], p, pn, w0[g], w1[g], gw, o);
+          if (oldn) {
+            const double gn[2] = {unx[g], uny[g]}, gv0[2] = {w0x[g], w0y[g]};
+            const double G4n = (MODEL == 1 && P.has_g4)
+                                   ? (fma(m.h, ey + T.xg[g / 3], m.y0) - P.zT - P.Vp * (P.t_new - P.dt)) / P.lT
+                                   : 0.0;
+            old_spatial_t<2, MODEL>(P, phi[g] - dphi[g], u[g] - du[g], pn, gn, G4n, w0[g], gv0, gw, o);
+          }
         }
         s0[g] = o.sphi;
         s1[g] = o.su;

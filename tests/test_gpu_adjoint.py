@@ -20,6 +20,12 @@ def _problem(kind):
         prm = Params(model=0, eps4=0.05, lam=3.19, D=2.0, Delta=0.65, precond=1, jvp_mode=1, newton_rtol=1e-13)
         U0f = lambda p: synth.seed_state(mesh, p, radius=8.0)
         return mesh, prm, U0f, 0.5, 3
+    if kind == "alloy_cn":
+        mesh = Mesh(2, 10, 10, 0, 1.2, -6.0, -6.0)
+        prm = Params(model=1, k=0.15, eps4=0.03, lam=3.19, D=2.0, Delta=0.5, precond=1, jvp_mode=1,
+                     newton_rtol=1e-13, theta=0.5, phihat_form=1)
+        U0f = lambda p: synth.seed_state(mesh, p, radius=3.0, centred=True)
+        return mesh, prm, U0f, 0.3, 3
     if kind == "pure":
         mesh = Mesh(2, 10, 10, 0, 2.0)
         prm = Params(model=0, eps4=0.04, lam=3.19, D=2.0, Delta=0.6, precond=1, jvp_mode=1, newton_rtol=1e-13)
@@ -31,7 +37,7 @@ def _problem(kind):
     return mesh, prm, U0f, 0.3, 2
 
 
-@pytest.mark.parametrize("kind", ["pure", "pure16", "alloy"])
+@pytest.mark.parametrize("kind", ["pure", "pure16", "alloy", "alloy_cn"])
 def test_adjoint_matches_oracle_adjoint(kind):
     mesh, prm, U0f, dt, n = _problem(kind)
     U0 = U0f(prm)

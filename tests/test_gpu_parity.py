@@ -248,8 +248,15 @@ def test_theta_method_residual_tangent_adjoint(name, mesh, prm):
     assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v, Unm1=Unm1)) <= 1e-12
     h.jtvp(tU, dev(w), out)
     assert rel(host(out), OJ.jtvp(mesh, prm, U, Un, tn, dt, w, Unm1=Unm1)) <= 1e-12
-    with pytest.raises(pkg.TusasError):
+    if prm.phihat_form == 1:
+        # level-n spatial terms weighted (1 - theta) in (dF/dU^n)^T w and dF/d eps4
+        h.jtvp_prev(tU, dev(w), out)
+        assert rel(host(out), OJ.dF_dUn_T(mesh, prm, U, Un, tn, dt, w)) <= 1e-12
         h.dFdp(tU, out, 0)
+        assert rel(host(out), OJ.dF_deps4(mesh, prm, U, Un, tn, dt)) <= 1e-12
+    else:
+        with pytest.raises(pkg.TusasError):
+            h.dFdp(tU, out, 0)
 
 
 @pytest.mark.parametrize("form", [1, 0])

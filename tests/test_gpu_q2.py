@@ -81,6 +81,11 @@ def test_q2_theta_method(form):
     assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v, Unm1=Unm1)) <= 1e-12
     h.jtvp(tU, dev(w), out)
     assert rel(host(out), OJ.jtvp(mesh, prm, U, Un, tn, dt, w, Unm1=Unm1)) <= 1e-12
+    if form == 1:
+        h.jtvp_prev(tU, dev(w), out)
+        assert rel(host(out), OJ.dF_dUn_T(mesh, prm, U, Un, tn, dt, w)) <= 1e-12
+        h.dFdp(tU, out, 0)
+        assert rel(host(out), OJ.dF_deps4(mesh, prm, U, Un, tn, dt)) <= 1e-12
 
 
 @pytest.mark.parametrize("prm", [PURE, ALLOY], ids=["pure", "alloy"])
