@@ -196,6 +196,18 @@ class Hierarchy:
         return chebyshev(A, dinv, b, x, lo, hi, self.cheb_degree)
 
 
+def q2_lattice(mesh):
+    """The Q2 node grid seen as a Q1 box of spacing h/2 (the multigrid hierarchy of a Q2 block).
+
+    Its first coarsening by 2 is the grid of the Q2 element vertices, and the
+    (bi)linear prolongation between the two is the exact embedding of the Q1
+    space of the elements in their Q2 space, so the Galerkin product P^T A P of
+    the assembled Q2 block is the Q1 operator with the Q2 quadrature
+    (9-point); the levels below are the Q1 hierarchy.
+    """
+    return dataclasses.replace(mesh, nx=2 * mesh.nx, ny=2 * mesh.ny, h=mesh.h / 2, order=1)
+
+
 class Preconditioner:
     """z = M^-1 r for kind 0 (identity), 1 (point Jacobi), 2 (block Jacobi + GMG)."""
 
@@ -208,8 +220,9 @@ class Preconditioner:
         if self.kind == 1:
             self.d = np.concatenate([self.M11.diagonal(), self.M22.diagonal()])
         else:
-            self.h11 = Hierarchy(mesh, self.M11, prm.mg_levels, prm.cheb_degree, prm.coarse_degree)
-            self.h22 = Hierarchy(mesh, self.M22, prm.mg_levels, prm.cheb_degree, prm.coarse_degree)
+            hm = q2_lattice(mesh) if fem.order(mesh) == 2 else mesh
+            self.h11 = Hierarchy(hm, self.M11, prm.mg_levels, prm.cheb_degree, prm.coarse_degree)
+            self.h22 = Hierarchy(hm, self.M22, prm.mg_levels, prm.cheb_degree, prm.coarse_degree)
 
     def apply(self, r):
         if self.kind == 0:

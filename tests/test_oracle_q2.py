@@ -95,3 +95,36 @@ def test_q2_sampled_node_residual_matches_full_residual():
     rp, ru = R.residual_at_nodes(mesh, prm, U, Un, 0.4, 0.3, nodes)
     assert np.abs(rp - F[nodes]).max() <= 1e-13 * np.abs(F).max()
     assert np.abs(ru - F[n + nodes]).max() <= 1e-13 * np.abs(F).max()
+
+
+def test_q2_multigrid_hierarchy():
+    """Q2 blocks on the h/2 node lattice: the first Galerkin product is the element-vertex Q1
+    operator (9-point stencil, exact embedding of Q1 in Q2: P^T M_Q2 P of the mass block equals
+    the Q1 mass matrix built from the same elements), and the V-cycle converges as a
+    stationary iteration."""
+    from oracle import precond as P
+
+    mesh = Mesh(2, 8, 6, 0, 0.7, order=2)
+    prm = Params(model=0, eps4=0.05, lam=3.19, D=2.0, precond=2)
+    U, Un = synth.random_fields(mesh, 5)
+    U, Un = 0.3 * U, 0.3 * Un
+    M11, M22 = P.blocks(mesh, prm, U, Un, 0.4)
+    lat = P.q2_lattice(mesh)
+    Pm = P.prolongation(lat)
+    # mass part of M22 for the pure metal is (1/dt) M: its Galerkin product is (1/dt) x Q1 mass
+    q1 = Mesh(2, 8, 6, 0, 0.7)
+    Mc = (Pm.T @ M22 @ Pm).tocsr()
+    Kq1 = tb.mass(q1) / 0.4 + prm.theta * prm.D * tb.stiffness(q1)
+    assert abs(Mc - Kq1).max() <= 1e-13 * abs(Kq1).max()
+    # V-cycle as a stationary iteration on M11: contraction about 0.58 per cycle with degree-2
+    # Chebyshev smoothing and 0.27 with degree 3 (the Q2 lattice mixes vertex, edge and centre
+    # nodes, whose diagonals differ)
+    rng = np.random.default_rng(0)
+    b = rng.standard_normal(mesh.n_nodes)
+    r0 = np.linalg.norm(b)
+    for deg, bound in ((2, 1e-2), (3, 1e-5)):
+        H = P.Hierarchy(lat, M11, 3, cheb_degree=deg)
+        x = np.zeros_like(b)
+        for _ in range(10):
+            x = x + H.vcycle(b - M11 @ x)
+        assert np.linalg.norm(b - M11 @ x) < bound * r0
