@@ -204,8 +204,8 @@ def run_q2_report(stream):
 
     Kernel rates at equal node counts (Q2 with n elements per axis vs Q1 with 2n), and
     backward-Euler JFNK steps of the dendrite seed with the same node spacing:
-    Q2 512^2 (point Jacobi, the preconditioner Q2 handles take) against Q1 1024^2 with
-    point Jacobi and with the GMG V-cycle.
+    Q2 512^2 (point Jacobi, and multigrid from the h/2 node lattice) against Q1 1024^2
+    with point Jacobi and with the GMG V-cycle.
     """
     import dataclasses
 
@@ -225,6 +225,7 @@ def run_q2_report(stream):
     m2 = synth.Mesh(2, 512, 512, 0, 400.0 / 512, order=2)
     variants = [("q2_512_exact_jacobi", m2, dict(precond=1, jvp_mode=1)),
                 ("q2_512_fd_jacobi", m2, dict(precond=1, jvp_mode=0)),
+                ("q2_512_exact_gmg_fp32", m2, dict(precond=2, jvp_mode=1, smoother_fp32=1, cheb_degree=3)),
                 ("q1_1024_exact_jacobi", w.mesh, dict(precond=1, jvp_mode=1)),
                 ("q1_1024_exact_gmg_fp32", w.mesh, dict(precond=2, jvp_mode=1, smoother_fp32=1))]
     for name, mesh, opts in variants:

@@ -44,9 +44,10 @@ enum {
  * rule, node (i,j,k) at (x0 + i h, y0 + j h, z0 + k h). order 2: biquadratic
  * Q2 elements with the 3 x 3 Gauss rule (2D only; the higher-order elements of
  * the tip-velocity study, Sec. 4.1), node (i,j) at (x0 + i h/2, y0 + j h/2),
- * (2 nx + 1)(2 ny + 1) nodes; Q2 handles take precond 0 or 1 (point Jacobi
- * on the diagonals of M11, M22), and tusas_create returns TUSAS_EINVAL for
- * precond 2 or order 2 in 3D. Nodes are numbered x fastest in every case. */
+ * (2 nx + 1)(2 ny + 1) nodes; their multigrid (precond 2) starts on the node
+ * lattice of spacing h/2 (25-point stencils) and coarsens to the element
+ * vertices; tusas_create returns TUSAS_EINVAL for order 2 in 3D. Nodes are
+ * numbered x fastest in every case. */
 typedef struct tusas_mesh {
   int dim;
   int nx, ny, nz;

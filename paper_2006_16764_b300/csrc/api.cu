@@ -124,10 +124,6 @@ int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
     why = "order must be 0 or 1 (Q1) or 2 (Q2, 2D only)";
     return TUSAS_EINVAL;
   }
-  if (m->order == 2 && p->precond == 2) {
-    why = "Q2 meshes take precond 0 or 1 (no multigrid hierarchy for Q2)";
-    return TUSAS_EINVAL;
-  }
   const int po = m->order == 2 ? 2 : 1;
   const double nodes = (double)(po * m->nx + 1) * (po * m->ny + 1) * (m->dim == 3 ? m->nz + 1 : 1);
   if (nodes > 2.0e9) {

@@ -44,6 +44,10 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
 cudaError_t q2_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
                    double* lin, cudaStream_t st, const double* phold);
 void q2_tables(Q2Tab& T, double h);
+// 25-point stencils [2][25][nodes] of the preconditioner blocks of a Q2 box on its node
+// lattice, at the iterate U with U^n (T = float or double).
+template <typename T>
+cudaError_t q2_stencil_fill(const ElemCtx& c, const double* U, const double* Un, T* st, cudaStream_t s);
 
 // ---- FP64 vector kernels (deterministic) ----------------------------------
 // y = a*x + y

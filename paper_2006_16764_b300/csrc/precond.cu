@@ -23,6 +23,12 @@ template <int DIM>
 struct Pow3 {
   static const int V = DIM == 2 ? 9 : 27;
 };
+// stencil of radius R: (2R + 1)^dim entries (R = 2 only for the 2D Q2 node lattice)
+template <int DIM, int R>
+struct Sten {
+  static const int W = 2 * R + 1;
+  static const int V = DIM == 2 ? W * W : W * W * W;
+};
 
 // ---------------------------------------------------------------------------
 // fine-level stencil fill
@@ -254,17 +260,18 @@ __device__ __forceinline__ bool node3(const DevMesh& m, int& ix, int& iy, int& i
 }
 
 // sum_o A[o] x[node + o] in offset order; interior nodes skip the bounds tests
-template <int DIM, typename T>
+template <int DIM, typename T, int R = 1>
 __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __restrict__ x, const DevMesh& m, i64 node,
                                            int ix, int iy, int iz) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Sten<DIM, R>::V, W = Sten<DIM, R>::W;
   const i64 sy = m.nnx, sz = (i64)m.nnx * m.nny;
   T s = T(0);
-  const bool interior = ix > 0 && ix < m.nnx - 1 && iy > 0 && iy < m.nny - 1 && (DIM == 2 || (iz > 0 && iz < m.nnz - 1));
+  const bool interior = ix >= R && ix < m.nnx - R && iy >= R && iy < m.nny - R &&
+                        (DIM == 2 || (iz >= R && iz < m.nnz - R));
   if (interior) {
 #pragma unroll
     for (int o = 0; o < NS; ++o) {
-      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
+      const int ox = o % W - R, oy = (o / W) % W - R, oz = DIM == 3 ? o / (W * W) - R : 0;
       const i64 off = ox + sy * oy + sz * oz;
       // symmetric operator: a backward entry A(i, i+o) is read as A(i+o, i), the neighbour's
       // forward entry, so only the 14 forward / centre coefficient arrays are streamed
@@ -274,7 +281,7 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __
   } else {
 #pragma unroll
     for (int o = 0; o < NS; ++o) {
-      const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
+      const int ox = o % W - R, oy = (o / W) % W - R, oz = DIM == 3 ? o / (W * W) - R : 0;
       const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
       if (jx < 0 || jx >= m.nnx || jy < 0 || jy >= m.nny || jz < 0 || jz >= m.nnz) continue;
       const i64 off = ox + sy * oy + sz * oz;
@@ -302,10 +309,10 @@ static int grid_nodes(i64 n) {
 // coarse nodes interpolating to 2I + o1 + o2. The offset o1 is a template parameter and the o2
 // loop is unrolled, so every accumulator index is a compile-time constant and the 3^dim
 // accumulators stay in registers.
-template <int DIM, typename T, int O1>
+template <int DIM, typename T, int RF, int O1>
 __device__ __forceinline__ void rap_row(const DevMesh& mf, const T* __restrict__ stf, int cx, int cy, int cz,
                                         T* acc) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Sten<DIM, RF>::V, WF = Sten<DIM, RF>::W;
   constexpr int o1x = O1 % 3 - 1, o1y = (O1 / 3) % 3 - 1, o1z = DIM == 3 ? O1 / 9 - 1 : 0;
   const int fx = 2 * cx + o1x, fy = 2 * cy + o1y, fz = 2 * cz + o1z;
   if (fx < 0 || fx >= mf.nnx || fy < 0 || fy >= mf.nny || fz < 0 || fz >= mf.nnz) return;
@@ -313,7 +320,7 @@ __device__ __forceinline__ void rap_row(const DevMesh& mf, const T* __restrict__
   const T* sp = stf + fx + (i64)mf.nnx * (fy + (i64)mf.nny * fz);
 #pragma unroll
   for (int o2 = 0; o2 < NS; ++o2) {
-    const int o2x = o2 % 3 - 1, o2y = (o2 / 3) % 3 - 1, o2z = DIM == 3 ? o2 / 9 - 1 : 0;
+    const int o2x = o2 % WF - RF, o2y = (o2 / WF) % WF - RF, o2z = DIM == 3 ? o2 / (WF * WF) - RF : 0;
     const int rx = o1x + o2x, ry = o1y + o2y, rz = o1z + o2z;
     const T v = T(w1f) * __ldg(sp + (i64)o2 * mf.nn);
     // per axis: even r -> coarse offset r/2 (weight 1); odd r -> (r-1)/2 and (r+1)/2 (1/2 each)
@@ -324,21 +331,25 @@ __device__ __forceinline__ void rap_row(const DevMesh& mf, const T* __restrict__
       const int jx = (rx & 1) ? (rx - 1) / 2 + bx : rx / 2;
       const int jy = (ry & 1) ? (ry - 1) / 2 + by : ry / 2;
       const int jz = DIM == 3 ? ((rz & 1) ? (rz - 1) / 2 + bz : rz / 2) : 0;
+      // a radius-2 fine stencil (Q2 lattice) reaches coarse offsets up to 2 only through
+      // entries that are structurally zero (nodes of different elements): skip them
+      if (jx < -1 || jx > 1 || jy < -1 || jy > 1 || jz < -1 || jz > 1) continue;
       const T ww = ((rx & 1) ? T(0.5) : T(1)) * ((ry & 1) ? T(0.5) : T(1)) * (DIM == 3 && (rz & 1) ? T(0.5) : T(1));
       acc[(jx + 1) + 3 * (jy + 1) + (DIM == 3 ? 9 * (jz + 1) : 0)] += v * ww;
     }
   }
 }
 
-template <int DIM, typename T, int... O1>
+template <int DIM, typename T, int RF, int... O1>
 __device__ __forceinline__ void rap_rows(const DevMesh& mf, const T* __restrict__ stf, int cx, int cy, int cz, T* acc,
                                          std::integer_sequence<int, O1...>) {
-  (rap_row<DIM, T, O1>(mf, stf, cx, cy, cz, acc), ...);
+  (rap_row<DIM, T, RF, O1>(mf, stf, cx, cy, cz, acc), ...);
 }
 
-template <int DIM, typename T>
+// fine stencils of radius RF (1, or 2 on the Q2 lattice), coarse stencils of radius 1
+template <int DIM, typename T, int RF = 1>
 __global__ void __launch_bounds__(256, 2) k_rap(DevMesh mf, DevMesh mc, const T* __restrict__ stf, T* __restrict__ stc) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Pow3<DIM>::V, NSF = Sten<DIM, RF>::V;
   int cx, cy, cz;
   i64 I;
   if (!node3(mc, cx, cy, cz, I)) return;
@@ -346,16 +357,16 @@ __global__ void __launch_bounds__(256, 2) k_rap(DevMesh mf, DevMesh mc, const T*
     T acc[NS];
 #pragma unroll
     for (int o = 0; o < NS; ++o) acc[o] = T(0);
-    rap_rows<DIM, T>(mf, stf + (i64)blk * NS * mf.nn, cx, cy, cz, acc, std::make_integer_sequence<int, NS>{});
+    rap_rows<DIM, T, RF>(mf, stf + (i64)blk * NSF * mf.nn, cx, cy, cz, acc, std::make_integer_sequence<int, NS>{});
 #pragma unroll
     for (int o = 0; o < NS; ++o) stc[((i64)blk * NS + o) * mc.nn + I] = acc[o];
   }
 }
 
 // D^-1 and the Gershgorin bound max_i sum_j |a_ij| / a_ii per block.
-template <int DIM, typename T>
+template <int DIM, typename T, int R = 1>
 __global__ void k_gersh(DevMesh m, const T* __restrict__ st, T* __restrict__ dinv, double* __restrict__ partials) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Sten<DIM, R>::V;
   constexpr int C = NS / 2;
   __shared__ T red[2][256];
   T mx[2] = {T(0), T(0)};
@@ -417,10 +428,10 @@ struct Coef2 {
 };
 
 // r = D^-1 (b - A x) (or D^-1 b if x == nullptr, and then x = 0); d = r * it
-template <int DIM, typename T>
+template <int DIM, typename T, int R = 1>
 __global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Sten<DIM, R>::V;
   {
     int ix, iy, iz;
     i64 i;
@@ -431,7 +442,7 @@ __global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __rest
       if (zero_x)
         x[blk * m.nn + i] = T(0);
       else
-        v -= stencil_apply<DIM, T>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
+        v -= stencil_apply<DIM, T, R>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
       const T rr = dinv[blk * m.nn + i] * v;
       r[blk * m.nn + i] = rr;
       d[blk * m.nn + i] = rr * it.a[blk];
@@ -440,10 +451,10 @@ __global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __rest
 }
 
 // x += d; if !last: r -= D^-1 A d; dout = c1 d + c2 r
-template <int DIM, typename T>
+template <int DIM, typename T, int R = 1>
 __global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Sten<DIM, R>::V;
   {
     int ix, iy, iz;
     i64 i;
@@ -454,7 +465,7 @@ __global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __rest
       const T dk = d[k];
       x[k] += dk;
       if (!last) {
-        const T ad = stencil_apply<DIM, T>(st + blk * NS * m.nn, d + blk * m.nn, m, i, ix, iy, iz);
+        const T ad = stencil_apply<DIM, T, R>(st + blk * NS * m.nn, d + blk * m.nn, m, i, ix, iy, iz);
         const T rr = r[k] - dinv[k] * ad;
         r[k] = rr;
         dout[k] = c.a[blk] * dk + c.b[blk] * rr;
@@ -463,10 +474,10 @@ __global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __rest
   }
 }
 
-template <int DIM, typename T>
+template <int DIM, typename T, int R = 1>
 __global__ void __launch_bounds__(256, 6) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
-  constexpr int NS = Pow3<DIM>::V;
+  constexpr int NS = Sten<DIM, R>::V;
   {
     int ix, iy, iz;
     i64 i;
@@ -474,7 +485,7 @@ __global__ void __launch_bounds__(256, 6) k_resid(DevMesh m, const T* __restrict
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk)
       res[blk * m.nn + i] =
-          bvec[blk * m.nn + i] - stencil_apply<DIM, T>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
+          bvec[blk * m.nn + i] - stencil_apply<DIM, T, R>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
   }
 }
 
@@ -587,8 +598,7 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
   bytes = 0;
   if (kind == 0) return cudaSuccess;
   const size_t esz = fp32 ? sizeof(float) : sizeof(double);
-  if (m.order == 2) {
-    if (kind != 1) return cudaErrorInvalidValue;
+  if (m.order == 2 && kind == 1) {
     PrecondLevel L = {};
     L.m = m;
     L.nn = m.nn;
@@ -598,14 +608,23 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
     bytes += (esz + sizeof(double)) * 2 * m.nn;
     return cudaMalloc(&diag, sizeof(double) * 2 * m.nn);
   }
-  const int NS = m.dim == 3 ? 27 : 9;
   const int nlev = kind == 1 ? 1 : (levels < 1 ? 1 : levels);
+  // Q2 (2D): the finest level is the node lattice of spacing h/2 with 25-point stencils; its
+  // coarsening by 2 is the element-vertex grid (the Q1 space embedded in the Q2 space)
   DevMesh cur = m;
+  if (m.order == 2) {
+    cur.order = 1;
+    cur.nx = 2 * m.nx;
+    cur.ny = 2 * m.ny;
+    cur.h = 0.5 * m.h;
+  }
   for (int l = 0; l < nlev; ++l) {
     PrecondLevel L = {};
     L.m = cur;
     L.nn = cur.nn;
-    void** bufs[] = {&L.dinv, &L.b, &L.x, &L.r, &L.d, &L.d2, &L.res};
+    L.r = (l == 0 && m.order == 2) ? 2 : 1;
+    const int NS = L.r == 2 ? 25 : (m.dim == 3 ? 27 : 9);
+    void** bufs[] = {&L.dinv, &L.b, &L.x, &L.r_, &L.d, &L.d2, &L.res};
     cudaError_t e = cudaMalloc(&L.st, esz * 2 * NS * cur.nn);
     if (e != cudaSuccess) return e;
     bytes += esz * 2 * NS * cur.nn;
@@ -626,7 +645,7 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
 
 void Precond::destroy() {
   for (auto& L : lv) {
-    void* bufs[] = {L.st, L.dinv, L.b, L.x, L.r, L.d, L.d2, L.res};
+    void* bufs[] = {L.st, L.dinv, L.b, L.x, L.r_, L.d, L.d2, L.res};
     for (void* p : bufs)
       if (p) cudaFree(p);
   }
@@ -641,13 +660,19 @@ template <typename T>
 cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st) {
   const DevMesh& m = c.m;
   PrecondLevel& L0 = lv[0];
-  if (m.order == 2) {
+  if (m.order == 2 && kind == 1) {
     // point Jacobi: element pass for diag(M11), diag(M22), then the reciprocals
     cudaError_t e = elem_run(M_DIAG, c, U, Un, nullptr, diag, nullptr, st);
     if (e != cudaSuccess) return e;
     k_recip<T><<<grid_nodes(2 * m.nn), 256, 0, st>>>(2 * m.nn, diag, (T*)L0.dinv);
     count_launches(1);
     return cudaGetLastError();
+  }
+  if (m.order == 2) {
+    // multigrid: 25-point stencils on the Q2 node lattice, then the Galerkin levels below
+    cudaError_t e = q2_stencil_fill<T>(c, U, Un, (T*)L0.st, st);
+    if (e != cudaSuccess) return e;
+    return galerkin_and_bounds<T>(st);
   }
   FillArgs<T> A;
   A.m = m;
@@ -693,36 +718,38 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  return galerkin_and_bounds<T>(st);
+}
+
+// Galerkin coarse stencils of levels 1.., D^-1 and the Gershgorin bounds of every level.
+// Synchronises once (the bounds are host scalars of the Chebyshev smoother).
+template <typename T>
+cudaError_t Precond::galerkin_and_bounds(cudaStream_t st) {
+  const int dim = lv[0].m.dim;
   for (size_t l = 1; l < lv.size(); ++l) {
-    if (m.dim == 3)
-      {
-        k_rap<3, T><<<grid3(lv[l].m), block3(lv[l].m), 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
-        count_launches(1);
-      }
+    const PrecondLevel& F = lv[l - 1];
+    const PrecondLevel& C = lv[l];
+    if (dim == 3)
+      k_rap<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.st, (T*)C.st);
+    else if (F.r == 2)
+      k_rap<2, T, 2><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.st, (T*)C.st);
     else
-      {
-        k_rap<2, T><<<grid3(lv[l].m), block3(lv[l].m), 0, st>>>(lv[l - 1].m, lv[l].m, (const T*)lv[l - 1].st, (T*)lv[l].st);
-        count_launches(1);
-      }
+      k_rap<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.st, (T*)C.st);
+    count_launches(1);
   }
   for (size_t l = 0; l < lv.size(); ++l) {
     const int nb = grid_nodes(lv[l].nn);
-    if (m.dim == 3)
-      {
-        k_gersh<3, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
-        count_launches(1);
-      }
+    if (dim == 3)
+      k_gersh<3, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
+    else if (lv[l].r == 2)
+      k_gersh<2, T, 2><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
     else
-      {
-        k_gersh<2, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
-        count_launches(1);
-      }
-    {
-      k_max_partials<<<1, 256, 0, st>>>(nb, gersh_partials, lmax_dev + 2 * l);
-      count_launches(1);
-    }
+      k_gersh<2, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
+    count_launches(1);
+    k_max_partials<<<1, 256, 0, st>>>(nb, gersh_partials, lmax_dev + 2 * l);
+    count_launches(1);
   }
-  e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   std::vector<double> lm(2 * lv.size());
   e = cudaMemcpyAsync(lm.data(), lmax_dev, sizeof(double) * lm.size(), cudaMemcpyDeviceToHost, st);
@@ -757,17 +784,15 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   }
   const bool d3 = L.m.dim == 3;
   if (d3)
-    {
-      k_cheb_init<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
-                                           (T*)L.r, (T*)L.d, it);
-      count_launches(1);
-    }
+    k_cheb_init<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
+                                                         zero_x, (T*)L.r_, (T*)L.d, it);
+  else if (L.r == 2)
+    k_cheb_init<2, T, 2><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b,
+                                                            (T*)L.x, zero_x, (T*)L.r_, (T*)L.d, it);
   else
-    {
-      k_cheb_init<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x, zero_x,
-                                           (T*)L.r, (T*)L.d, it);
-      count_launches(1);
-    }
+    k_cheb_init<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
+                                                         zero_x, (T*)L.r_, (T*)L.d, it);
+  count_launches(1);
   T* dcur = (T*)L.d;
   T* dnext = (T*)L.d2;
   for (int kk = 0; kk < degree; ++kk) {
@@ -779,17 +804,15 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
       rho[b] = rn;
     }
     if (d3)
-      {
-        k_cheb_step<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
-                                             last);
-        count_launches(1);
-      }
+      k_cheb_step<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
+                                                           dcur, dnext, cc, last);
+    else if (L.r == 2)
+      k_cheb_step<2, T, 2><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x,
+                                                              (T*)L.r_, dcur, dnext, cc, last);
     else
-      {
-        k_cheb_step<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r, dcur, dnext, cc,
-                                             last);
-        count_launches(1);
-      }
+      k_cheb_step<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
+                                                           dcur, dnext, cc, last);
+    count_launches(1);
     T* tmp = dcur;
     dcur = dnext;
     dnext = tmp;
@@ -816,10 +839,11 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
       count_launches(1);
     }
   } else {
-    {
+    if (F.r == 2)
+      k_resid<2, T, 2><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+    else
       k_resid<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
-      count_launches(1);
-    }
+    count_launches(1);
     {
       k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
       count_launches(1);

@@ -13,11 +13,12 @@ struct PrecondLevel {
   void* dinv;  // [2][nn]
   void* b;     // right-hand side [2][nn]
   void* x;     // iterate
-  void* r;     // Jacobi-scaled Chebyshev residual
+  void* r_;    // Jacobi-scaled Chebyshev residual
   void* d;     // Chebyshev direction (double buffered with d2)
   void* d2;
   void* res;   // unscaled residual for the restriction
   double lmax[2];
+  int r;       // stencil radius: 1 (3^dim points), 2 on the Q2 node lattice (5 x 5)
 };
 
 class Precond {
@@ -48,6 +49,8 @@ class Precond {
   cudaError_t setup_t(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st);
   template <typename T>
   cudaError_t apply_t(const double* r, double* z, cudaStream_t st);
+  template <typename T>
+  cudaError_t galerkin_and_bounds(cudaStream_t st);
   template <typename T>
   cudaError_t vcycle(int l, cudaStream_t st);
   template <typename T>

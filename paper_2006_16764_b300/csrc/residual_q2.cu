@@ -385,6 +385,129 @@ void q2_tables(Q2Tab& T, double h) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Preconditioner blocks M11, M22 (Eqs. pref2, preconc2) of a Q2 box as 25-point
+// stencils on its node lattice (spacing h/2): one thread per node gathers the
+// rows of the element matrices of its 1, 2 or 4 elements in a fixed order and
+// writes its two rows once (no colouring, deterministic). Arithmetic in the
+// stencil precision T (the preconditioner's).
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Q2FillArgs {
+  DevMesh m;  // the Q2 mesh
+  DevPhys P;
+  Q2Tab Tb;
+  const double* U;
+  const double* Un;
+  T* st;  // [2][25][nn]
+};
+
+template <int MODEL, typename T>
+__global__ void __launch_bounds__(256) k_q2_stencil_fill(const Q2FillArgs<T> A) {
+  const DevMesh& m = A.m;
+  const Q2Tab& Tb = A.Tb;
+  const DevPhys& P = A.P;
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+  if (ix >= m.nnx || iy >= m.nny) return;
+  const i64 node = ix + (i64)m.nnx * iy;
+  T acc[2][25];
+#pragma unroll
+  for (int b = 0; b < 2; ++b)
+#pragma unroll
+    for (int o = 0; o < 25; ++o) acc[b][o] = T(0);
+  const T wg[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
+  const T h2 = T(m.h * m.h);
+  // candidate elements per axis: even index 2e = right end of e - 1 (local 2) and left end of e
+  // (local 0); odd index 2e + 1 = middle of e (local 1)
+#pragma unroll
+  for (int cy = 0; cy < 2; ++cy) {
+    const int ey = (iy & 1) ? (cy == 0 ? (iy - 1) / 2 : -1) : iy / 2 - 1 + cy;
+    const int ay = (iy & 1) ? 1 : 2 - 2 * cy;
+    if (ey < 0 || ey >= m.ny) continue;
+#pragma unroll
+    for (int cx = 0; cx < 2; ++cx) {
+      const int ex = (ix & 1) ? (cx == 0 ? (ix - 1) / 2 : -1) : ix / 2 - 1 + cx;
+      const int ax = (ix & 1) ? 1 : 2 - 2 * cx;
+      if (ex < 0 || ex >= m.nx) continue;
+      T nphi[9], nu[9], npn[9];
+#pragma unroll
+      for (int b = 0; b < 9; ++b) {
+        const i64 nb = (2 * ex + b % 3) + (i64)m.nnx * (2 * ey + b / 3);
+        nphi[b] = (T)__ldg(A.U + nb);
+        nu[b] = (T)__ldg(A.U + m.nn + nb);
+        npn[b] = (T)__ldg(A.Un + nb);
+      }
+#pragma unroll
+      for (int g = 0; g < 9; ++g) {
+        const int gx = g % 3, gy = g / 3;
+        T phi = 0, px = 0, py = 0, u = 0, phin = 0;
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+          const T Nb = T(Tb.B[gx][b % 3] * Tb.B[gy][b / 3]);
+          phi += Nb * nphi[b];
+          u += Nb * nu[b];
+          phin += Nb * npn[b];
+          px += T(Tb.G[gx][b % 3] * Tb.B[gy][b / 3]) * nphi[b];
+          py += T(Tb.B[gx][b % 3] * Tb.G[gy][b / 3]) * nphi[b];
+        }
+        // Gauss-point coefficients of the two blocks (as the Q1 fill)
+        const T q = px * px + py * py;
+        T a = T(1);
+        if ((double)q >= TUSAS_GUARD_Q) {
+          const T iq = T(1) / q;
+          a = T(1.0 - 3.0 * P.eps4) + T(4.0 * P.eps4) * (px * px * px * px + py * py * py * py) * iq * iq;
+        }
+        const T a2 = a * a, k = T(P.k);
+        const T Bu = T(1) + (T(1) - k) * u;
+        const T Ac = MODEL == 0 ? T(1) : T(0.5) * ((T(1) + k) - (T(1) - k) * phin);
+        const T mob = MODEL == 0 ? T(1) : T(0.5) * (T(1) - phi);
+        const T W = h2 * wg[gx] * wg[gy];
+        const T cm[2] = {W * T(P.tau0) * Bu * a2 * T(P.idt), W * Ac * T(P.idt)};
+        const T ck[2] = {W * T(P.thW2) * a2, W * T(P.thD) * mob};
+        // row of local node a = (ax, ay) against the 9 local nodes b
+        const T Na = T(Tb.B[gx][ax] * Tb.B[gy][ay]);
+        const T Nax = T(Tb.G[gx][ax] * Tb.B[gy][ay]), Nay = T(Tb.B[gx][ax] * Tb.G[gy][ay]);
+#pragma unroll
+        for (int b = 0; b < 9; ++b) {
+          const int bx = b % 3, by = b / 3;
+          const T Nb = T(Tb.B[gx][bx] * Tb.B[gy][by]);
+          const T gdot = Nax * T(Tb.G[gx][bx] * Tb.B[gy][by]) + Nay * T(Tb.B[gx][bx] * Tb.G[gy][by]);
+          const int o = (bx - ax + 2) + 5 * (by - ay + 2);
+#pragma unroll
+          for (int blk = 0; blk < 2; ++blk) acc[blk][o] += cm[blk] * Na * Nb + ck[blk] * gdot;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int blk = 0; blk < 2; ++blk)
+#pragma unroll
+    for (int o = 0; o < 25; ++o) A.st[((i64)blk * 25 + o) * m.nn + node] = acc[blk][o];
+}
+
+template <typename T>
+cudaError_t q2_stencil_fill(const ElemCtx& c, const double* U, const double* Un, T* st, cudaStream_t s) {
+  if (c.m.dim != 2 || c.m.order != 2) return cudaErrorInvalidValue;
+  Q2FillArgs<T> a;
+  a.m = c.m;
+  a.P = c.P;
+  a.Tb = c.q2;
+  a.U = U;
+  a.Un = Un;
+  a.st = st;
+  const dim3 blk(32, 8);
+  const dim3 grid(ceil_div(c.m.nnx, 32), ceil_div(c.m.nny, 8));
+  if (c.P.model == 0)
+    k_q2_stencil_fill<0, T><<<grid, blk, 0, s>>>(a);
+  else
+    k_q2_stencil_fill<1, T><<<grid, blk, 0, s>>>(a);
+  count_launches(1);
+  return cudaGetLastError();
+}
+template cudaError_t q2_stencil_fill<float>(const ElemCtx&, const double*, const double*, float*, cudaStream_t);
+template cudaError_t q2_stencil_fill<double>(const ElemCtx&, const double*, const double*, double*, cudaStream_t);
+
 template <int MODEL, int MODE>
 static cudaError_t q2_colours(const ElemCtx& c, Q2Args a, cudaStream_t st) {
   constexpr int NE = Tile<2>::X * Tile<2>::Y;

@@ -65,7 +65,7 @@ def test_invalid_arguments_fail_without_gpu_work():
 
 
 def test_mesh_validation_rejects_bad_orders_before_gpu_work():
-    """order must be 0/1 (Q1) or 2 (Q2, 2D only); Q2 has no multigrid hierarchy (precond 2)."""
+    """order must be 0/1 (Q1) or 2 (Q2, 2D only); precond in 0..2."""
     import ctypes
 
     import paper_2006_16764_b300 as pkg
@@ -75,7 +75,7 @@ def test_mesh_validation_rejects_bad_orders_before_gpu_work():
     h = ctypes.c_void_p()
     for mesh, prm in [(Mesh(3, 4, 4, 4, 1.0, order=2), Params(precond=1)),
                       (Mesh(2, 4, 4, 0, 1.0, order=3), Params(precond=1)),
-                      (Mesh(2, 4, 4, 0, 1.0, order=2), Params(precond=2))]:
+                      (Mesh(2, 4, 4, 0, 1.0, order=2), Params(precond=3))]:
         cm, cp = pkg.make_mesh(mesh), pkg.make_params(prm)
         assert lib.tusas_create(ctypes.byref(cm), ctypes.byref(cp), ctypes.byref(h)) == pkg.EINVAL
         assert not h.value

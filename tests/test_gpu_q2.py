@@ -106,6 +106,26 @@ def test_q2_jacobi_matches_oracle(prm, fp32, tol):
     assert rel(host(z), want) <= tol
 
 
+@pytest.mark.parametrize("prm", [PURE, ALLOY], ids=["pure", "alloy"])
+@pytest.mark.parametrize("fp32,tol", [(0, 1e-10), (1, 2e-4)])
+def test_q2_multigrid_matches_oracle(prm, fp32, tol):
+    """Block Jacobi + multigrid for Q2: 25-point stencils on the h/2 node lattice, Galerkin
+    coarsening to the element vertices and the Q1 levels below (ragged lattice levels)."""
+    mesh = Mesh(2, 24, 20, 0, 0.8, order=2)
+    prm = dataclasses.replace(prm, precond=2, smoother_fp32=fp32, mg_levels=4, cheb_degree=3)
+    U, Un = synth.random_fields(mesh, 21)
+    Un = 0.5 * Un
+    U = 0.5 * U
+    h = handle(mesh, prm)
+    h.set_state(dev(Un), 0.0, 0.3)
+    h.precond_setup(dev(U))
+    r = synth.random_vector(mesh, 11)
+    z = dev(np.zeros_like(r))
+    h.precond_apply(dev(r), z)
+    want = OP.Preconditioner(mesh, prm, U, Un, 0.3).apply(r)
+    assert rel(host(z), want) <= tol
+
+
 def test_q2_residual_is_bitwise_deterministic():
     mesh = Mesh(2, 45, 27, 0, 0.8, order=2)
     U, Un = synth.random_fields(mesh, 3)
@@ -122,6 +142,7 @@ def test_q2_residual_is_bitwise_deterministic():
 Q2_STEPS = [
     ("pure-exact", dict(jvp_mode=1)),
     ("pure-fd", dict(jvp_mode=0)),
+    ("pure-exact-gmg", dict(jvp_mode=1, precond=2, cheb_degree=3, gmres_maxit=30)),
 ]
 
 
@@ -129,7 +150,7 @@ Q2_STEPS = [
 def test_q2_converged_steps_match_oracle(name, opts):
     w = synth.scaled(synth.workload("dendrite2d_128"), 16, 16)
     mesh = dataclasses.replace(w.mesh, order=2)
-    prm = dataclasses.replace(w.params, precond=1, smoother_fp32=0, **opts)
+    prm = dataclasses.replace(w.params, **dict(dict(precond=1, smoother_fp32=0), **opts))
     U0 = synth.seed_state(mesh, prm, radius=8.0)
     h = handle(mesh, prm)
     h.set_state(dev(U0), 0.0, w.dt)
