@@ -405,31 +405,41 @@ struct Q2FillArgs {
 template <int MODEL, typename T>
 __global__ void __launch_bounds__(256) k_q2_stencil_fill(const Q2FillArgs<T> A) {
   const DevMesh& m = A.m;
-  const Q2Tab& Tb = A.Tb;
   const DevPhys& P = A.P;
+  // basis tables in the stencil precision: value, x- and y-derivative of local node b at Gauss point g
+  __shared__ T sN[9][9], sNx[9][9], sNy[9][9], sW[9];
+  for (int t = threadIdx.x + blockDim.x * threadIdx.y; t < 81; t += blockDim.x * blockDim.y) {
+    const int g = t / 9, b = t % 9;
+    const int gx = g % 3, gy = g / 3, bx = b % 3, by = b / 3;
+    sN[g][b] = T(A.Tb.B[gx][bx] * A.Tb.B[gy][by]);
+    sNx[g][b] = T(A.Tb.G[gx][bx] * A.Tb.B[gy][by]);
+    sNy[g][b] = T(A.Tb.B[gx][bx] * A.Tb.G[gy][by]);
+    if (b == 0) {
+      const double wg[3] = {5.0 / 18.0, 8.0 / 18.0, 5.0 / 18.0};
+      sW[g] = T(m.h * m.h * wg[gx] * wg[gy]);
+    }
+  }
+  __syncthreads();
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   const int iy = blockIdx.y * blockDim.y + threadIdx.y;
   if (ix >= m.nnx || iy >= m.nny) return;
   const i64 node = ix + (i64)m.nnx * iy;
-  T acc[2][25];
+  T acc0[25], acc1[25];
 #pragma unroll
-  for (int b = 0; b < 2; ++b)
-#pragma unroll
-    for (int o = 0; o < 25; ++o) acc[b][o] = T(0);
-  const T wg[3] = {T(5.0 / 18.0), T(8.0 / 18.0), T(5.0 / 18.0)};
-  const T h2 = T(m.h * m.h);
+  for (int o = 0; o < 25; ++o) acc0[o] = acc1[o] = T(0);
+  const T k = T(P.k), eps = T(P.eps4), a0 = T(1.0 - 3.0 * P.eps4);
+  const T tau_dt = T(P.tau0 * P.idt), idt = T(P.idt), thW2 = T(P.thW2), thD = T(P.thD);
   // candidate elements per axis: even index 2e = right end of e - 1 (local 2) and left end of e
   // (local 0); odd index 2e + 1 = middle of e (local 1)
-#pragma unroll
   for (int cy = 0; cy < 2; ++cy) {
     const int ey = (iy & 1) ? (cy == 0 ? (iy - 1) / 2 : -1) : iy / 2 - 1 + cy;
     const int ay = (iy & 1) ? 1 : 2 - 2 * cy;
     if (ey < 0 || ey >= m.ny) continue;
-#pragma unroll
     for (int cx = 0; cx < 2; ++cx) {
       const int ex = (ix & 1) ? (cx == 0 ? (ix - 1) / 2 : -1) : ix / 2 - 1 + cx;
       const int ax = (ix & 1) ? 1 : 2 - 2 * cx;
       if (ex < 0 || ex >= m.nx) continue;
+      const int a = ax + 3 * ay;
       T nphi[9], nu[9], npn[9];
 #pragma unroll
       for (int b = 0; b < 9; ++b) {
@@ -438,52 +448,51 @@ __global__ void __launch_bounds__(256) k_q2_stencil_fill(const Q2FillArgs<T> A) 
         nu[b] = (T)__ldg(A.U + m.nn + nb);
         npn[b] = (T)__ldg(A.Un + nb);
       }
-#pragma unroll
+#pragma unroll 1
       for (int g = 0; g < 9; ++g) {
-        const int gx = g % 3, gy = g / 3;
         T phi = 0, px = 0, py = 0, u = 0, phin = 0;
 #pragma unroll
         for (int b = 0; b < 9; ++b) {
-          const T Nb = T(Tb.B[gx][b % 3] * Tb.B[gy][b / 3]);
+          const T Nb = sN[g][b];
           phi += Nb * nphi[b];
           u += Nb * nu[b];
           phin += Nb * npn[b];
-          px += T(Tb.G[gx][b % 3] * Tb.B[gy][b / 3]) * nphi[b];
-          py += T(Tb.B[gx][b % 3] * Tb.G[gy][b / 3]) * nphi[b];
+          px += sNx[g][b] * nphi[b];
+          py += sNy[g][b] * nphi[b];
         }
         // Gauss-point coefficients of the two blocks (as the Q1 fill)
         const T q = px * px + py * py;
-        T a = T(1);
+        T an = T(1);
         if ((double)q >= TUSAS_GUARD_Q) {
           const T iq = T(1) / q;
-          a = T(1.0 - 3.0 * P.eps4) + T(4.0 * P.eps4) * (px * px * px * px + py * py * py * py) * iq * iq;
+          an = a0 + T(4) * eps * (px * px * px * px + py * py * py * py) * iq * iq;
         }
-        const T a2 = a * a, k = T(P.k);
+        const T a2 = an * an;
         const T Bu = T(1) + (T(1) - k) * u;
         const T Ac = MODEL == 0 ? T(1) : T(0.5) * ((T(1) + k) - (T(1) - k) * phin);
         const T mob = MODEL == 0 ? T(1) : T(0.5) * (T(1) - phi);
-        const T W = h2 * wg[gx] * wg[gy];
-        const T cm[2] = {W * T(P.tau0) * Bu * a2 * T(P.idt), W * Ac * T(P.idt)};
-        const T ck[2] = {W * T(P.thW2) * a2, W * T(P.thD) * mob};
-        // row of local node a = (ax, ay) against the 9 local nodes b
-        const T Na = T(Tb.B[gx][ax] * Tb.B[gy][ay]);
-        const T Nax = T(Tb.G[gx][ax] * Tb.B[gy][ay]), Nay = T(Tb.B[gx][ax] * Tb.G[gy][ay]);
+        const T W = sW[g];
+        const T Na = sN[g][a], Nax = sNx[g][a], Nay = sNy[g][a];
+        const T m0 = W * tau_dt * Bu * a2 * Na, m1 = W * Ac * idt * Na;
+        const T k0 = W * thW2 * a2, k1 = W * thD * mob;
+        // row of local node a against b = a + (dx, dy): compile-time stencil slots
 #pragma unroll
-        for (int b = 0; b < 9; ++b) {
-          const int bx = b % 3, by = b / 3;
-          const T Nb = T(Tb.B[gx][bx] * Tb.B[gy][by]);
-          const T gdot = Nax * T(Tb.G[gx][bx] * Tb.B[gy][by]) + Nay * T(Tb.B[gx][bx] * Tb.G[gy][by]);
-          const int o = (bx - ax + 2) + 5 * (by - ay + 2);
-#pragma unroll
-          for (int blk = 0; blk < 2; ++blk) acc[blk][o] += cm[blk] * Na * Nb + ck[blk] * gdot;
+        for (int o = 0; o < 25; ++o) {
+          const int bx = ax + o % 5 - 2, by = ay + o / 5 - 2;
+          if (bx < 0 || bx > 2 || by < 0 || by > 2) continue;
+          const int b = bx + 3 * by;
+          const T gd = Nax * sNx[g][b] + Nay * sNy[g][b];
+          acc0[o] += m0 * sN[g][b] + k0 * gd;
+          acc1[o] += m1 * sN[g][b] + k1 * gd;
         }
       }
     }
   }
 #pragma unroll
-  for (int blk = 0; blk < 2; ++blk)
-#pragma unroll
-    for (int o = 0; o < 25; ++o) A.st[((i64)blk * 25 + o) * m.nn + node] = acc[blk][o];
+  for (int o = 0; o < 25; ++o) {
+    A.st[(i64)o * m.nn + node] = acc0[o];
+    A.st[((i64)25 + o) * m.nn + node] = acc1[o];
+  }
 }
 
 template <typename T>
