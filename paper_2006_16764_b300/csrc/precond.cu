@@ -11,6 +11,8 @@
 // inverts the blocks with algebraic multigrid and Chebyshev smoothing
 // (Sec. 4.4); on the structured box the geometric hierarchy is the natural
 // equivalent. Operators, smoother and coarse levels run in FP32 or FP64 (T).
+// On a Q2 box the finest level is its node grid seen as a box of spacing h/2
+// (25-point stencils); its Galerkin coarsening is the grid of element vertices.
 #include <math.h>
 
 #include <utility>

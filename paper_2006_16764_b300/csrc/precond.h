@@ -29,12 +29,13 @@ class Precond {
   std::vector<PrecondLevel> lv;
   double* gersh_partials = nullptr;  // [blocks][2]
   double* lmax_dev = nullptr;        // [levels][2]
-  double* diag = nullptr;            // Q2 meshes: FP64 diagonals of M11, M22 [2][nn]
+  double* diag = nullptr;            // Q2 point Jacobi: FP64 diagonals of M11, M22 [2][nn]
   size_t bytes = 0;
 
   // Allocate the hierarchy for the mesh (levels: coarsen by 2 while every
-  // element count is even and >= 2, at most `levels`). Q2 meshes take point
-  // Jacobi only (kind 1): their diagonals come from an element pass.
+  // element count is even and >= 2, at most `levels`). On a Q2 mesh point
+  // Jacobi takes the diagonals from an element pass, and the multigrid starts on
+  // the node lattice of spacing h/2 (25-point stencils) above the vertex grid.
   cudaError_t create(const DevMesh& m, int kind, int fp32, int levels, int cheb_degree, int coarse_degree);
   void destroy();
   // Fill the fine stencils of M11 / M22 at the iterate U (Gauss-point
