@@ -38,17 +38,18 @@ WORKLOAD = "alloy3d_256x256x128"
 CPU_SAMPLE = (48, 48, 32)
 
 # FP64 floating-point operations per element of one element-tile pass, counted
-# from the compiled kernels (DADD + DMUL + 2 DFMA per element, ncu
-# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum / elements of
-# the 3D alloy kernels). Algorithmic bytes per element: nodal reads/writes
-# (8 B per field value, one node per element) plus the stored linearisation
-# (23 coefficients x 8 Gauss points x 8 B).
-FP64_FLOPS_PER_ELEM = {"residual": 1456.0, "residual_lin": 2372.0, "jv": 920.5}
+# from the compiled kernels (DADD + DMUL + 2 DFMA per element: ncu
+# smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over the 8
+# colour launches of one pass on the 256x192x64 alloy box / its elements).
+# Algorithmic bytes per element: nodal reads/writes (8 B per field value, one
+# node per element) plus the stored linearisation (23 coefficients x 8 Gauss
+# points x 8 B).
+FP64_FLOPS_PER_ELEM = {"residual": 1417.0, "residual_lin": 2456.0, "jv": 920.5}
 BYTES_PER_ELEM = {"residual": 48.0, "residual_lin": 48.0 + 1472.0, "jv": 32.0 + 1472.0}
-# DRAM bytes per element measured by ncu on the 256x192x64 sub-box (one colour
-# launch, dram__bytes_read.sum + dram__bytes_write.sum / elements); the traffic
-# scales with the elements processed (same tiles, same per-element streams).
-NCU_BYTES_PER_ELEM = {"residual": 154.0, "residual_lin": 1513.0, "jv": 1610.3}
+# DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
+# dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
+# with the elements processed (same tiles, same per-element streams).
+NCU_BYTES_PER_ELEM = {"residual": 153.1, "residual_lin": 1511.4, "jv": 1610.0}
 
 
 def parse():
