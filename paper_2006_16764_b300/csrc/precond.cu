@@ -261,6 +261,19 @@ __device__ __forceinline__ bool node3(const DevMesh& m, int& ix, int& iy, int& i
   return true;
 }
 
+// Node and block (M11 / M22) of the calling thread in a smoother launch: the grid's z
+// extent is twice the node grid's, blocks one after the other (grid3b).
+__device__ __forceinline__ bool node3b(const DevMesh& m, int& ix, int& iy, int& iz, i64& node, int& blk) {
+  const int zb = gridDim.z >> 1;
+  blk = blockIdx.z >= zb;
+  ix = blockIdx.x * blockDim.x + threadIdx.x;
+  iy = blockIdx.y * blockDim.y + threadIdx.y;
+  iz = (blockIdx.z - blk * zb) * blockDim.z + threadIdx.z;
+  if (ix >= m.nnx || iy >= m.nny || iz >= m.nnz) return false;
+  node = ix + (i64)m.nnx * (iy + (i64)m.nny * iz);
+  return true;
+}
+
 // sum_o A[o] x[node + o] in offset order; interior nodes skip the bounds tests
 template <int DIM, typename T, int R = 1>
 __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __restrict__ x, const DevMesh& m, i64 node,
@@ -298,6 +311,11 @@ static dim3 block3(const DevMesh& m) { return m.dim == 3 ? dim3(32, 4, 2) : dim3
 static dim3 grid3(const DevMesh& m) {
   const dim3 b = block3(m);
   return dim3((m.nnx + b.x - 1) / b.x, (m.nny + b.y - 1) / b.y, (m.nnz + b.z - 1) / b.z);
+}
+// smoother launches: one thread per node and block (node3b)
+static dim3 grid3b(const DevMesh& m) {
+  const dim3 g = grid3(m);
+  return dim3(g.x, g.y, 2 * g.z);
 }
 
 static int grid_nodes(i64 n) {
@@ -435,20 +453,17 @@ __global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __rest
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
   constexpr int NS = Sten<DIM, R>::V;
   {
-    int ix, iy, iz;
+    int ix, iy, iz, blk;
     i64 i;
-    if (!node3(m, ix, iy, iz, i)) return;
-#pragma unroll
-    for (int blk = 0; blk < 2; ++blk) {
-      T v = bvec[blk * m.nn + i];
-      if (zero_x)
-        x[blk * m.nn + i] = T(0);
-      else
-        v -= stencil_apply<DIM, T, R>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
-      const T rr = dinv[blk * m.nn + i] * v;
-      r[blk * m.nn + i] = rr;
-      d[blk * m.nn + i] = rr * it.a[blk];
-    }
+    if (!node3b(m, ix, iy, iz, i, blk)) return;
+    T v = bvec[blk * m.nn + i];
+    if (zero_x)
+      x[blk * m.nn + i] = T(0);
+    else
+      v -= stencil_apply<DIM, T, R>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
+    const T rr = dinv[blk * m.nn + i] * v;
+    r[blk * m.nn + i] = rr;
+    d[blk * m.nn + i] = rr * (blk ? it.a[1] : it.a[0]);
   }
 }
 
@@ -458,20 +473,17 @@ __global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __rest
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
   constexpr int NS = Sten<DIM, R>::V;
   {
-    int ix, iy, iz;
+    int ix, iy, iz, blk;
     i64 i;
-    if (!node3(m, ix, iy, iz, i)) return;
-#pragma unroll
-    for (int blk = 0; blk < 2; ++blk) {
-      const i64 k = blk * m.nn + i;
-      const T dk = d[k];
-      x[k] += dk;
-      if (!last) {
-        const T ad = stencil_apply<DIM, T, R>(st + blk * NS * m.nn, d + blk * m.nn, m, i, ix, iy, iz);
-        const T rr = r[k] - dinv[k] * ad;
-        r[k] = rr;
-        dout[k] = c.a[blk] * dk + c.b[blk] * rr;
-      }
+    if (!node3b(m, ix, iy, iz, i, blk)) return;
+    const i64 k = blk * m.nn + i;
+    const T dk = d[k];
+    x[k] += dk;
+    if (!last) {
+      const T ad = stencil_apply<DIM, T, R>(st + blk * NS * m.nn, d + blk * m.nn, m, i, ix, iy, iz);
+      const T rr = r[k] - dinv[k] * ad;
+      r[k] = rr;
+      dout[k] = (blk ? c.a[1] : c.a[0]) * dk + (blk ? c.b[1] : c.b[0]) * rr;
     }
   }
 }
@@ -481,13 +493,11 @@ __global__ void __launch_bounds__(256, 6) k_resid(DevMesh m, const T* __restrict
                         T* __restrict__ res) {
   constexpr int NS = Sten<DIM, R>::V;
   {
-    int ix, iy, iz;
+    int ix, iy, iz, blk;
     i64 i;
-    if (!node3(m, ix, iy, iz, i)) return;
-#pragma unroll
-    for (int blk = 0; blk < 2; ++blk)
-      res[blk * m.nn + i] =
-          bvec[blk * m.nn + i] - stencil_apply<DIM, T, R>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
+    if (!node3b(m, ix, iy, iz, i, blk)) return;
+    res[blk * m.nn + i] =
+        bvec[blk * m.nn + i] - stencil_apply<DIM, T, R>(st + blk * NS * m.nn, x + blk * m.nn, m, i, ix, iy, iz);
   }
 }
 
@@ -786,13 +796,13 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   }
   const bool d3 = L.m.dim == 3;
   if (d3)
-    k_cheb_init<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
+    k_cheb_init<3, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
                                                          zero_x, (T*)L.r_, (T*)L.d, it);
   else if (L.r == 2)
-    k_cheb_init<2, T, 2><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b,
+    k_cheb_init<2, T, 2><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b,
                                                             (T*)L.x, zero_x, (T*)L.r_, (T*)L.d, it);
   else
-    k_cheb_init<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
+    k_cheb_init<2, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
                                                          zero_x, (T*)L.r_, (T*)L.d, it);
   count_launches(1);
   T* dcur = (T*)L.d;
@@ -806,13 +816,13 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
       rho[b] = rn;
     }
     if (d3)
-      k_cheb_step<3, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
+      k_cheb_step<3, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
                                                            dcur, dnext, cc, last);
     else if (L.r == 2)
-      k_cheb_step<2, T, 2><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x,
+      k_cheb_step<2, T, 2><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x,
                                                               (T*)L.r_, dcur, dnext, cc, last);
     else
-      k_cheb_step<2, T><<<grid3(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
+      k_cheb_step<2, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
                                                            dcur, dnext, cc, last);
     count_launches(1);
     T* tmp = dcur;
@@ -833,7 +843,7 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   const bool d3 = F.m.dim == 3;
   if (d3) {
     {
-      k_resid<3, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      k_resid<3, T><<<grid3b(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
       count_launches(1);
     }
     {
@@ -842,9 +852,9 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
     }
   } else {
     if (F.r == 2)
-      k_resid<2, T, 2><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      k_resid<2, T, 2><<<grid3b(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
     else
-      k_resid<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+      k_resid<2, T><<<grid3b(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
     count_launches(1);
     {
       k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
