@@ -198,14 +198,18 @@ def test_q2_full_size_residual_on_sampled_nodes():
     assert np.abs(F[n + nodes] - ru).max() <= 1e-12 * scale
 
 
-def test_q2_adjoint_gradient_matches_oracle():
-    """Discrete adjoint through 3 backward-Euler steps on a Q2 box (Simpson solid-fraction
-    weights): dS/d eps4 and dS/dU_0 against the oracle's direct-solve adjoint."""
+@pytest.mark.parametrize("variant", ["be-jacobi", "cn-multigrid"])
+def test_q2_adjoint_gradient_matches_oracle(variant):
+    """Discrete adjoint through 3 steps on a Q2 box (Simpson solid-fraction weights): dS/d eps4
+    and dS/dU_0 against the oracle's direct-solve adjoint; backward Euler with point Jacobi, and
+    Crank-Nicolson with the lattice multigrid in the transposed solves."""
     from oracle import adjoint as OA
 
     mesh = Mesh(2, 8, 8, 0, 2.0, order=2)
     prm = Params(model=0, eps4=0.04, lam=3.19, D=2.0, Delta=0.6, precond=1, jvp_mode=1, newton_rtol=1e-13,
                  smoother_fp32=0)
+    if variant == "cn-multigrid":
+        prm = dataclasses.replace(prm, theta=0.5, phihat_form=1, precond=2, mg_levels=3)
     U0 = synth.seed_state(mesh, prm, radius=6.0)
     dt, n = 0.5, 3
     states = OA.forward(mesh, prm, U0, 0.0, dt, n)
