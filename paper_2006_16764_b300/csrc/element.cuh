@@ -123,12 +123,109 @@ __device__ __forceinline__ void accumulate(const double* s, double (*f)[1 << DIM
   for (int a = 0; a < NN; ++a) out[a] = acc[a];
 }
 
+// ---- scaled forms (tangent and adjoint passes) ----------------------------
+// The scale factors of interp / accumulate have product form over the axes
+// (s per set bit of a Walsh coefficient, times a constant), so they can sit in
+// the evaluation butterflies, (c0, c1) -> (c0 - s c1, c0 + s c1), as FMAs, with
+// the constants folded into the stored linearisation (LinScale): values come
+// out as 2^dim v, gradients as (h 2^dim / 2) grad v, and the accumulation takes
+// integrands scaled by w / 2^dim (values) and w / 2^dim * 2 / (h s) (fluxes).
+template <int DIM>
+__device__ __forceinline__ void walsh_eval_s(double* v, double s) {
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int a = 0; a < (1 << DIM); ++a) {
+      if (!(a & (1 << d))) {
+        const double c0 = v[a], c1 = v[a | (1 << d)];
+        v[a] = fma(-s, c1, c0);
+        v[a | (1 << d)] = fma(s, c1, c0);
+      }
+    }
+  }
+}
+template <>
+__device__ __forceinline__ void walsh_eval_s<0>(double*, double) {}
+
+template <int DIM>
+__device__ __forceinline__ void interp_s(const double* nodal, double* val, double (*grad)[1 << (DIM - 1)], double s) {
+  constexpr int NN = 1 << DIM;
+  double c[NN];
+#pragma unroll
+  for (int a = 0; a < NN; ++a) c[a] = nodal[a];
+  walsh_fwd<DIM>(c);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+    for (int j = 0; j < NN / 2; ++j) grad[d][j] = c[insert_bit(j, d, 1)];
+    walsh_eval_s<DIM - 1>(grad[d], s);
+  }
+#pragma unroll
+  for (int b = 0; b < NN; ++b) val[b] = c[b];
+  walsh_eval_s<DIM>(val, s);
+}
+
+template <int DIM>
+__device__ __forceinline__ void accumulate_s(const double* sv, double (*f)[1 << DIM], double* out, double s) {
+  constexpr int NN = 1 << DIM;
+  double acc[NN];
+#pragma unroll
+  for (int g = 0; g < NN; ++g) acc[g] = sv[g];
+  walsh_fwd<DIM>(acc);
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) {
+    double t[NN / 2];
+#pragma unroll
+    for (int j = 0; j < NN / 2; ++j) t[j] = f[d][insert_bit(j, d, 0)] + f[d][insert_bit(j, d, 1)];
+    walsh_fwd<DIM - 1>(t);
+#pragma unroll
+    for (int j = 0; j < NN / 2; ++j) acc[insert_bit(j, d, 1)] += t[j];
+  }
+  walsh_eval_s<DIM>(acc, s);
+#pragma unroll
+  for (int a = 0; a < NN; ++a) out[a] = acc[a];
+}
+
+// Factors of the stored linearisation for the scaled forms, by the type of a
+// coefficient: (input value | gradient) -> (output value | flux); s and 1/s
+// correct the mixed value-gradient coefficients in the transposed product;
+// the model-0 constants of the u equation, scaled.
+#define TUSAS_INV_2SQRT2 0.35355339059327373
+
+struct LinScale {
+  double vv, gv, vf, gf;
+  double s, inv_s;
+  double mdphat, idt, thD;
+  // physics constants times their factors, for the linearisation pass (lin_consts)
+  double m_th_vv, tau_idt_vv, thlam_vv, tau_vv, tau2_gv, thW2_gf, half_omk_vv, m_half_thD_vf, cw_dphat_vf, cw_omk_vf,
+      half_thD_gf, cw_gf;
+};
+
+// Fill the linearisation constants of K from the physics P (host).
+inline void lin_consts(LinScale& K, const DevPhys& P) {
+  const double cw = TUSAS_INV_2SQRT2 * P.W0, omk = 1.0 - P.k;
+  K.mdphat = -0.5 * P.dphat * K.vv;
+  K.idt = P.idt * K.vv;
+  K.thD = P.thD * K.gf;
+  K.m_th_vv = -P.theta * K.vv;
+  K.tau_idt_vv = P.tau0 * P.idt * K.vv;
+  K.thlam_vv = P.theta * P.lam * K.vv;
+  K.tau_vv = P.tau0 * K.vv;
+  K.tau2_gv = 2.0 * P.tau0 * K.gv;
+  K.thW2_gf = P.thW2 * K.gf;
+  K.half_omk_vv = 0.5 * omk * K.vv;
+  K.m_half_thD_vf = -0.5 * P.thD * K.vf;
+  K.cw_dphat_vf = cw * P.dphat * K.vf;
+  K.cw_omk_vf = cw * omk * K.vf;
+  K.half_thD_gf = 0.5 * P.thD * K.gf;
+  K.cw_gf = cw * K.gf;
+}
+
 // ---------------------------------------------------------------------------
 // Pointwise physics (Sec. 4.2, Eqs. pf2, lambda, directional, conc2, jat, gs)
 // ---------------------------------------------------------------------------
 
 #define TUSAS_GUARD_Q 1e-20
-#define TUSAS_INV_2SQRT2 0.35355339059327373
 
 // Anisotropy a(p) = 1 - 3 eps + 4 eps sum n_i^4 (Eq. gs) from p = grad phi.
 // On return n[] is the unit normal, n2[] its squares, sn = sum n_i^4, r = 1/|p|
@@ -176,6 +273,15 @@ struct NLin {
   static const int VALUE = MODEL == 0 ? PHI : PHI + 2 + DIM + 4 + DIM;
 };
 
+// unit factors: stored coefficients in true units (host)
+inline LinScale lin_unit(const DevPhys& P) {
+  LinScale K{};
+  K.vv = K.gv = K.vf = K.gf = 1.0;
+  K.s = K.inv_s = 1.0;
+  lin_consts(K, P);
+  return K;
+}
+
 // symmetric index (i <= j) -> 0..SYM-1: diagonal first, then (0,1),(0,2),(1,2)
 template <int DIM>
 __host__ __device__ constexpr int sym_index(int i, int j) {
@@ -184,10 +290,13 @@ __host__ __device__ constexpr int sym_index(int i, int j) {
 
 // Residual integrands and, if LIN, the pointwise Jacobian written to L[c]
 // (c-th coefficient of this Gauss point; stride given by the caller's writer).
+// The stored coefficients L carry the LinScale factors of their type (K; unit
+// factors give the coefficients in true units): the factors ride on constants
+// that are uniform across threads, so they cost no work per Gauss point.
 template <int DIM, int MODEL, bool LIN>
 __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u, double dphi, double du,
                                           double phold, const double* p, const double* g, const double* pn,
-                                          double G4, GPOut<DIM>& o, double* L) {
+                                          double G4, GPOut<DIM>& o, double* L, const LinScale& K) {
   Aniso<DIM> A;
   A.eval(p, P.eps4);
   const double eps = P.eps4;
@@ -236,9 +345,9 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
   for (int d = 0; d < DIM; ++d) ap[d] = c16 * A.n[d] * (A.n2[d] - A.sn) * A.r;
   const double dbulk = (1.0 - 3.0 * phi2) + 4.0 * P.lam * phi * om * ug;
   const double tfac = P.time_form == 0 ? dphidt : phi * P.idt;  // multiplies d(B a^2)
-  L[0] = fma(-P.theta, dbulk, P.tau0 * B * a2 * P.idt);           // alpha_phi
-  L[1] = fma(P.theta * P.lam, om * om, P.tau0 * omk * a2 * tfac);  // alpha_u
-  const double c2a = 2.0 * P.tau0 * B * tfac * A.a;
+  L[0] = fma(K.m_th_vv, dbulk, K.tau_idt_vv * B * a2);           // alpha_phi
+  L[1] = fma(K.thlam_vv, om * om, K.tau_vv * omk * a2 * tfac);  // alpha_u
+  const double c2a = K.tau2_gv * B * tfac * A.a;
 #pragma unroll
   for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * ap[d];         // alpha_p
   // H = theta W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn))
@@ -251,23 +360,24 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
       const double mi = A.n2[i] - A.sn, mj = A.n2[j] - A.sn;
       double v = A.n[i] * A.n[j] * (e32a * (A.sn - A.n2[i] - A.n2[j]) + e256 * mi * mj);
       if (i == j) v += a2 + e16a * (3.0 * A.n2[i] - A.sn);
-      L[2 + DIM + sym_index<DIM>(i, j)] = P.thW2 * v;
+      L[2 + DIM + sym_index<DIM>(i, j)] = K.thW2_gf * v;
     }
   }
   if (MODEL == 1) {
     constexpr int o0 = NLin<DIM, 1>::PHI;
-    L[o0 + 0] = -0.5 * B * P.dphat;                  // beta_phi
-    L[o0 + 1] = Acoef * P.idt - 0.5 * phihat * omk;  // beta_u
+    L[o0 + 0] = K.mdphat * B;                                // beta_phi
+    L[o0 + 1] = fma(Acoef, K.idt, -K.half_omk_vv * phihat);  // beta_u
     // direction of the antitrapping current and its derivative factors
     const double cw = TUSAS_INV_2SQRT2 * P.W0;
     double nv[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) nv[d] = P.jat_norm ? A.n[d] : p[d];
-    const double kap = P.jat_norm ? cw * B * phihat * A.r : cw * B * phihat;
+    const double kap = P.jat_norm ? K.cw_gf * B * phihat * A.r : K.cw_gf * B * phihat;
+    const double cgp = K.cw_dphat_vf * B;
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(-0.5 * P.thD, g[d], cw * B * P.dphat * nv[d]);  // gamma_phi
-    L[o0 + 2 + DIM] = cw * omk * phihat;                                                              // c_u
-    L[o0 + 3 + DIM] = Dq;                                                                             // gamma_g
+    for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(K.m_half_thD_vf, g[d], cgp * nv[d]);  // gamma_phi
+    L[o0 + 2 + DIM] = K.cw_omk_vf * phihat;                                                 // c_u
+    L[o0 + 3 + DIM] = K.half_thD_gf * (1.0 - phi);                                          // gamma_g
     L[o0 + 4 + DIM] = kap;                                                                            // kappa1
     L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                                         // kappa2
 #pragma unroll
@@ -425,9 +535,14 @@ __device__ __forceinline__ void gp_prev_t(const DevPhys& P, bool tf1, double phi
 // Apply the stored pointwise Jacobian (TRANS = false) or its transpose.
 // Inputs (x0, x1, xp, xg): forward = (dphi, du, dp, dg);
 // transpose = (s_phi, s_u, f_phi, f_u) test-side quantities.
-template <int DIM, int MODEL, bool TRANS>
+// SCALED: L, the inputs and the outputs are in the scaled forms (interp_s /
+// accumulate_s, LinScale K); otherwise in true units (K unused).
+template <int DIM, int MODEL, bool TRANS, bool SCALED = false>
 __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, double x0, double x1, const double* xp,
-                                          const double* xg, GPOut<DIM>& o) {
+                                          const double* xg, GPOut<DIM>& o, const LinScale& K = LinScale{}) {
+  const double mdphat = SCALED ? K.mdphat : -0.5 * P.dphat;
+  const double idt = SCALED ? K.idt : P.idt;
+  const double thD = SCALED ? K.thD : P.thD;
   constexpr int S0 = 2 + DIM;
   double Hx[DIM];
 #pragma unroll
@@ -445,9 +560,9 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
 #pragma unroll
     for (int d = 0; d < DIM; ++d) o.fphi[d] = Hx[d];
     if (MODEL == 0) {
-      o.su = fma(-0.5 * P.dphat, x0, x1 * P.idt);
+      o.su = fma(mdphat, x0, x1 * idt);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) o.fu[d] = P.thD * xg[d];
+      for (int d = 0; d < DIM; ++d) o.fu[d] = thD * xg[d];
     } else {
       constexpr int o0 = NLin<DIM, 1>::PHI;
       o.su = fma(L[o0], x0, L[o0 + 1] * x1);
@@ -463,25 +578,28 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
   } else {
     // x0 = s_phi-hat, x1 = s_u-hat, xp = f_phi-hat, xg = f_u-hat
     double s0 = L[0] * x0, s1 = L[1] * x0;
+    const double x0p = SCALED ? x0 * K.inv_s : x0;  // gradient -> value coefficients, transposed
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o.fphi[d] = fma(L[2 + d], x0, Hx[d]);
+    for (int d = 0; d < DIM; ++d) o.fphi[d] = fma(L[2 + d], x0p, Hx[d]);
     if (MODEL == 0) {
-      s0 = fma(-0.5 * P.dphat, x1, s0);
-      s1 = fma(P.idt, x1, s1);
+      s0 = fma(mdphat, x1, s0);
+      s1 = fma(idt, x1, s1);
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) o.fu[d] = P.thD * xg[d];
+      for (int d = 0; d < DIM; ++d) o.fu[d] = thD * xg[d];
     } else {
       constexpr int o0 = NLin<DIM, 1>::PHI;
       const double* nv = L + o0 + 6 + DIM;
       s0 = fma(L[o0], x1, s0);
       s1 = fma(L[o0 + 1], x1, s1);
-      double nfu = 0.0;
+      double nfu = 0.0, gs = 0.0;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
-        s0 = fma(L[o0 + 2 + d], xg[d], s0);
+        gs = fma(L[o0 + 2 + d], xg[d], gs);
         nfu = fma(nv[d], xg[d], nfu);
       }
-      s1 = fma(L[o0 + 2 + DIM] * nfu, 1.0, s1);
+      // value -> flux coefficients, transposed: times s in the scaled forms
+      s0 = SCALED ? fma(gs, K.s, s0) : s0 + gs;
+      s1 = fma(L[o0 + 2 + DIM] * nfu, SCALED ? K.s : 1.0, s1);
       const double k2 = L[o0 + 5 + DIM] * nfu;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {

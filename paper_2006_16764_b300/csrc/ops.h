@@ -27,6 +27,8 @@ struct ElemCtx {
   DevMesh m;
   DevPhys P;
   Scales S;
+  LinScale K;   // scaled linearisation of the Q1 tangent / adjoint passes
+  LinScale Ku;  // unit factors (Q2 passes)
   Q2Tab q2;
   int ntx, nty, ntz;  // tiles per axis
   int nlin;           // linearisation coefficients per Gauss point

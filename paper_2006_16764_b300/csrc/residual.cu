@@ -23,6 +23,7 @@ struct ElemArgs {
   DevMesh m;
   DevPhys P;
   Scales S;
+  LinScale K;  // scaled linearisation (tangent / adjoint passes)
   const double* U;
   const double* Un;
   const double* V;
@@ -129,8 +130,8 @@ elem_kernel(const ElemArgs A) {
         n0[a] = sV[0][sidx[a]];
         n1[a] = sV[NVF - 1][sidx[a]];
       }
-      interp<DIM, true>(n0, v0, gv0, A.S);
-      interp<DIM, true>(n1, v1, gv1, A.S);
+      interp_s<DIM>(n0, v0, gv0, A.K.s);
+      interp_s<DIM>(n1, v1, gv1, A.K.s);
 #pragma unroll
       for (int g = 0; g < NN; ++g) {
         double L[NC];
@@ -142,7 +143,7 @@ elem_kernel(const ElemArgs A) {
           xp[d] = gv0[d][remove_bit(g, d)];
           xg[d] = gv1[d][remove_bit(g, d)];
         }
-        lin_apply<DIM, MODEL, MODE == M_JTV>(A.P, L, v0[g], v1[g], xp, xg, o);
+        lin_apply<DIM, MODEL, MODE == M_JTV, true>(A.P, L, v0[g], v1[g], xp, xg, o, A.K);
         s0[g] = o.sphi;
         s1[g] = o.su;
 #pragma unroll
@@ -221,7 +222,8 @@ elem_kernel(const ElemArgs A) {
           spatial_old<DIM, MODEL>(A.P, phi[g], u[g], p, gg, G4, o);
         } else if (MODE == M_RES || MODE == M_RES_LIN) {
           double L[MODE == M_RES_LIN ? NC : 1];
-          pointwise<DIM, MODEL, MODE == M_RES_LIN>(A.P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L);
+          pointwise<DIM, MODEL, MODE == M_RES_LIN>(A.P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L,
+                                                   A.K);
           if (MODE == M_RES_LIN) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) linp[(c * NN + g) * NE] = L[c];
@@ -255,8 +257,13 @@ elem_kernel(const ElemArgs A) {
         }
       }
     }
-    accumulate<DIM>(s0, f0, r0, A.S);
-    accumulate<DIM>(s1, f1, r1, A.S);
+    if (MODE == M_JV || MODE == M_JTV) {
+      accumulate_s<DIM>(s0, f0, r0, A.K.s);
+      accumulate_s<DIM>(s1, f1, r1, A.K.s);
+    } else {
+      accumulate<DIM>(s0, f0, r0, A.S);
+      accumulate<DIM>(s1, f1, r1, A.S);
+    }
   }
 #pragma unroll
   for (int a = 0; a < NN; ++a) {
@@ -301,6 +308,20 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
     c.S.gs[k] = pow(s, k) * 2.0 / (m.h * nnodes);
     c.S.gsw[k] = c.S.gs[k] * w;
   }
+  // scaled forms: input values / gradients come out of interp_s times 2^dim and h 2^dim / 2;
+  // accumulate_s takes values times w / 2^dim and fluxes times w / 2^dim * 2 / (h s)
+  {
+    const double al = w / nnodes, be = al * 2.0 / (m.h * s);
+    const double ga = 1.0 / nnodes, de = 2.0 / (m.h * nnodes);
+    c.K.vv = al * ga;
+    c.K.gv = al * de;
+    c.K.vf = be * ga;
+    c.K.gf = be * de;
+    c.K.s = s;
+    c.K.inv_s = 1.0 / s;
+    lin_consts(c.K, P);
+  }
+  c.Ku = lin_unit(P);
   if (dim == 3) {
     c.ntx = ceil_div(m.nx, Tile<3>::X);
     c.nty = ceil_div(m.ny, Tile<3>::Y);
@@ -363,6 +384,7 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
   a.m = c.m;
   a.P = c.P;
   a.S = c.S;
+  a.K = c.K;
   a.U = U;
   a.Un = Un;
   a.V = V;
