@@ -187,7 +187,8 @@ int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int n
 /* Discrete adjoint of the last tusas_forward for S = w^T U_N (w a device
  * vector): J_N^T lam_N = w, J_n^T lam_n = -(dF_{n+1}/dU_n)^T lam_{n+1},
  * each solved by right-preconditioned FGMRES on J^T (same preconditioner,
- * which is symmetric) to ||r|| <= adj_rtol ||rhs||; the states are
+ * which is symmetric) to ||r|| <= adj_rtol ||rhs|| within max(gmres_maxit,
+ * 1000) iterations (the forward steps keep gmres_maxit); the states are
  * recomputed segment by segment from the checkpoints (deterministic, so they
  * equal the forward's). Returns dS/d eps4 = -sum_n lam_n^T dF_n/d eps4 in
  * *grad_eps4 (host); if grad_dir != NULL, (dS/dU_0) . d0 for the device

@@ -574,7 +574,7 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
 // Flexible right-preconditioned restarted GMRES with classical Gram-Schmidt
 // applied twice, x0 = 0; solves J x = b (b = -F) to ||b - J x|| <= tol_abs.
 static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol_abs, int* its_out,
-                 tusas_stats* stats, bool* converged = nullptr) {
+                 tusas_stats* stats, bool* converged = nullptr, int maxit = -1) {
   const int m = h->prm.gmres_restart;
   const i64 N = h->N;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), col(64);
@@ -587,7 +587,8 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
   int rc = host_norm(h, r, &beta);
   if (rc) return rc;
   double resid = beta;
-  while (beta > tol_abs && its < h->prm.gmres_maxit) {
+  if (maxit < 0) maxit = h->prm.gmres_maxit;
+  while (beta > tol_abs && its < maxit) {
     if (!isfinite(beta)) return fail(h, TUSAS_ENONFINITE, "non-finite GMRES residual");
     TCK(tusas::vscal(N, 1.0 / beta, r, h->st));  // V_0 = r / beta
     std::fill(g.begin(), g.end(), 0.0);
@@ -636,7 +637,7 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       g[j] = cs[j] * g[j];
       resid = fabs(g[j + 1]);
       mu = j + 1;
-      if (resid <= tol_abs || its >= h->prm.gmres_maxit || den == 0.0) break;
+      if (resid <= tol_abs || its >= maxit || den == 0.0) break;
     }
     for (int i = mu - 1; i >= 0; --i) {
       double s = g[i];
@@ -645,7 +646,7 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
     }
     TCK(cudaMemcpyAsync(h->sc + 128, y.data(), sizeof(double) * mu, cudaMemcpyHostToDevice, h->st));
     TCK(tusas::multi_comb(N, mu, h->Z, N, h->sc + 128, x, h->st));
-    if (resid <= tol_abs || its >= h->prm.gmres_maxit) break;
+    if (resid <= tol_abs || its >= maxit) break;
     // restart: r = b - J x
     rc = jv_apply(h, op, x, h->tmp);
     if (rc) return rc;
@@ -787,6 +788,8 @@ int set_state_dev(tusas_handle* h, const double* U, double t) {
 }
 }  // namespace
 
+static const int kAdjointMaxit = 1000;
+
 extern "C" int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int nsteps, int ckpt_every,
                              tusas_stats* total) {
   if (!h || !U0 || nsteps < 1 || ckpt_every < 1) return fail(h, TUSAS_EINVAL, "bad forward arguments");
@@ -894,7 +897,10 @@ extern "C" int tusas_adjoint(tusas_handle* h, const double* w, const double* d0,
       if (rc) return rc;
       int its = 0;
       bool ok = true;
-      rc = gmres(h, OP_TRANS, h->lam_rhs, h->lam, adj_rtol * bn, &its, &S, &ok);
+      // the adjoint solves must reach their tolerance: at least 1000 iterations whatever the
+      // (possibly truncating) Newton-Krylov cap of the forward steps
+      rc = gmres(h, OP_TRANS, h->lam_rhs, h->lam, adj_rtol * bn, &its, &S, &ok,
+                 std::max(h->prm.gmres_maxit, kAdjointMaxit));
       if (rc) return rc;
       S.gmres_its += its;
       if (S.newton_its < 32) S.gmres_per_newton[S.newton_its] = its;

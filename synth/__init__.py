@@ -186,6 +186,8 @@ def workload(name: str) -> Workload:
     gains little after about 10 iterations elsewhere, while the truncated
     solves leave the converged states unchanged to 1e-10 and the Newton
     iteration counts within 2 %; the alloy takes degree-3 Chebyshev smoothing.
+    The adjoint workload's forward steps take the same cap (its transposed
+    solves run to their tolerance regardless).
 
     dendrite2d_128      : 2D pure metal, 128^2 on [0,400]^2, FD-JFNK + Jacobi, dt 0.5
     dendrite2d_1024     : 2D pure metal, 1024^2 on [0,400]^2, GMG, dt 0.5
@@ -209,7 +211,7 @@ def workload(name: str) -> Workload:
                    precond=2, jvp_mode=1, cheb_degree=3, gmres_maxit=10)
         return Workload(name, Mesh(3, 256, 256, 128, 0.8), p, 0.2, 20)
     if name == "adjoint2d_512":
-        return Workload(name, Mesh(2, 512, 512, 0, 400.0 / 512), _pure(precond=2), 0.5, 50)
+        return Workload(name, Mesh(2, 512, 512, 0, 400.0 / 512), _pure(precond=2, gmres_maxit=10), 0.5, 50)
     raise KeyError(name)
 
 
