@@ -108,10 +108,12 @@ def test_q2_jacobi_matches_oracle(prm, fp32, tol):
 
 @pytest.mark.parametrize("prm", [PURE, ALLOY], ids=["pure", "alloy"])
 @pytest.mark.parametrize("fp32,tol", [(0, 1e-10), (1, 2e-4)])
-def test_q2_multigrid_matches_oracle(prm, fp32, tol):
+@pytest.mark.parametrize("dims", [(24, 20), (3, 5), (1, 1)], ids=["24x20", "3x5", "1x1"])
+def test_q2_multigrid_matches_oracle(prm, fp32, tol, dims):
     """Block Jacobi + multigrid for Q2: 25-point stencils on the h/2 node lattice, Galerkin
-    coarsening to the element vertices and the Q1 levels below (ragged lattice levels)."""
-    mesh = Mesh(2, 24, 20, 0, 0.8, order=2)
+    coarsening to the element vertices and the Q1 levels below (odd element counts stop the
+    hierarchy at the vertex grid; a single element has a 3 x 3 lattice and a 2 x 2 vertex grid)."""
+    mesh = Mesh(2, dims[0], dims[1], 0, 0.8, order=2)
     prm = dataclasses.replace(prm, precond=2, smoother_fp32=fp32, mg_levels=4, cheb_degree=3)
     U, Un = synth.random_fields(mesh, 21)
     Un = 0.5 * Un
