@@ -692,7 +692,7 @@ def run_ours(args, ws, rank, local):
     del F
 
     # FD-FP64 comparison path from the same starting state
-    jfnk = {"exact_fp32": {"s_per_step": ms / args.steps / 1e3,
+    jfnk = {"exact_fp32": {"s_per_step": ms / args.steps / 1e3, "steps_per_s": args.steps * 1e3 / ms,
                            "newton_its": [s["newton_its"] for s in stats],
                            "gmres_its": [s["gmres_its"] for s in stats],
                            "kappa": 2 * w.dt * (prm.D / (1 + prm.k)) / mesh.h ** 2}}
