@@ -44,12 +44,12 @@ CPU_SAMPLE = (48, 48, 32)
 # Algorithmic bytes per element: nodal reads/writes (8 B per field value, one
 # node per element) plus the stored linearisation (23 coefficients x 8 Gauss
 # points x 8 B).
-FP64_FLOPS_PER_ELEM = {"residual": 1417.0, "residual_lin": 2417.0, "jv": 931.5}
+FP64_FLOPS_PER_ELEM = {"residual": 1431.5, "residual_lin": 2415.5, "jv": 883.5}
 BYTES_PER_ELEM = {"residual": 48.0, "residual_lin": 48.0 + 1472.0, "jv": 32.0 + 1472.0}
 # DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
 # with the elements processed (same tiles, same per-element streams).
-NCU_BYTES_PER_ELEM = {"residual": 153.1, "residual_lin": 1511.5, "jv": 1609.9}
+NCU_BYTES_PER_ELEM = {"residual": 153.0, "residual_lin": 1511.4, "jv": 1609.9}
 
 
 def parse():

@@ -3,18 +3,20 @@
 // solute system, their linearisation, and the transposed (test-function)
 // accumulation back to the element nodes.
 //
-// Sum factorisation. With eta = 2 xi - 1 per axis, the Q1 interpolant of the
-// element's nodal values v_a (a = ax + 2 ay + 4 az) is
+// Sum factorisation. The element kernels (FP64) interpolate axis by axis
+// (interp_l below): per axis a pair of values gives the two Gauss-point
+// values and their difference in three operations, and the test-function
+// accumulation is the exact transpose. In 3D this costs 54 FP64 operations
+// for the values and gradient of one field at all 8 Gauss points (256 for the
+// direct basis sums), which matters because the kernels are bound by the FP64
+// pipe, not by memory. The preconditioner fill (FP32 or FP64) interpolates
+// with Walsh-Hadamard butterflies (interp): with eta = 2 xi - 1 per axis the
+// Q1 interpolant of the element's nodal values v_a (a = ax + 2 ay + 4 az) is
 //     v(eta) = 2^-dim sum_b C_b prod_{d in b} eta_d,
-// C = H v the Walsh-Hadamard transform (butterfly (x, y) -> (x + y, y - x) on
-// every axis). The 2-point Gauss points sit at eta_d = +-1/sqrt(3), so values
-// at all Gauss points are H^T applied to C_b s^|b| 2^-dim (s = 1/sqrt 3), and
-// the derivative along axis d is the (dim-1)-dimensional H^T of the
-// coefficients with bit d set, scaled by 2/(h 2^dim) s^(|b|-1). The test-
-// function accumulation is the exact transpose. In 3D this costs 92 FP64
-// operations for the values and gradient of one field at all 8 Gauss points
-// (256 for the direct basis sums), which matters because the kernels are
-// bound by the FP64 pipe, not by memory.
+// C = H v (butterfly (x, y) -> (x + y, y - x) on every axis); the Gauss points
+// sit at eta_d = +-1/sqrt(3), so the values are H^T applied to C_b s^|b| 2^-dim
+// (s = 1/sqrt 3), and the derivative along axis d is the (dim-1)-dimensional
+// H^T of the coefficients with bit d set, scaled by 2/(h 2^dim) s^(|b|-1).
 #pragma once
 #include "common.cuh"
 
@@ -99,102 +101,124 @@ __device__ __forceinline__ void interp(const T* nodal, T* val, T (*grad)[1 << (D
   walsh_eval<DIM, T>(val);
 }
 
-// Transposed accumulation: out_a = w sum_g ( s_g N_a(g) + sum_d f_dg dN_a/dx_d(g) ).
-template <int DIM>
-__device__ __forceinline__ void accumulate(const double* s, double (*f)[1 << DIM], double* out, const Scales& S) {
-  constexpr int NN = 1 << DIM;
-  double acc[NN];
-#pragma unroll
-  for (int g = 0; g < NN; ++g) acc[g] = s[g];
-  walsh_fwd<DIM>(acc);
-#pragma unroll
-  for (int b = 0; b < NN; ++b) acc[b] *= S.vsw[popc(b)];
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    double t[NN / 2];
-#pragma unroll
-    for (int j = 0; j < NN / 2; ++j) t[j] = f[d][insert_bit(j, d, 0)] + f[d][insert_bit(j, d, 1)];
-    walsh_fwd<DIM - 1>(t);
-#pragma unroll
-    for (int j = 0; j < NN / 2; ++j) acc[insert_bit(j, d, 1)] += t[j] * S.gsw[popc(j)];
-  }
-  walsh_eval<DIM>(acc);
-#pragma unroll
-  for (int a = 0; a < NN; ++a) out[a] = acc[a];
-}
+// ---- staged 1D forms ----------------------------------------------------------
+// Axis by axis, a pair of values (x0 at xi = 0, x1 at xi = 1) gives the values
+// at the two Gauss points xi = t and 1 - t, t = (1 - 1/sqrt 3) / 2, and the
+// difference b = x1 - x0 (h times the derivative along the axis, constant
+// along it): b = x1 - x0, x0 + t b, x1 - t b, three FP64 operations. The
+// difference of an earlier axis is carried through the later axes by the same
+// two-point interpolation. In 3D this costs 54 operations for the values and
+// the 12 distinct gradient entries of a field at the 8 Gauss points (72 with
+// the Walsh butterflies of interp), 36 for values alone (56). The
+// accumulation is the exact transpose (78 operations against 104): pairs
+// (yL, yR) and a derivative term yb go back to the nodes as
+// yL - q, yR + q with q = t (yL - yR) + yb.
+#define TUSAS_GP_T 0.21132486540518713  // (1 - 1/sqrt(3)) / 2
 
-// ---- scaled forms (tangent and adjoint passes) ----------------------------
-// The scale factors of interp / accumulate have product form over the axes
-// (s per set bit of a Walsh coefficient, times a constant), so they can sit in
-// the evaluation butterflies, (c0, c1) -> (c0 - s c1, c0 + s c1), as FMAs, with
-// the constants folded into the stored linearisation (LinScale): values come
-// out as 2^dim v, gradients as (h 2^dim / 2) grad v, and the accumulation takes
-// integrands scaled by w / 2^dim (values) and w / 2^dim * 2 / (h s) (fluxes).
-template <int DIM>
-__device__ __forceinline__ void walsh_eval_s(double* v, double s) {
+// Values at the Gauss points and, if GRAD, the differences grad[d][j] = h dv/dx_d at
+// the Gauss points whose other-axis bits are j.
+template <int DIM, bool GRAD = true>
+__device__ __forceinline__ void interp_l(const double* nodal, double* val, double (*grad)[1 << (DIM - 1)]) {
+  constexpr int NN = 1 << DIM;
+  constexpr int NH = NN / 2;
+  const double t = TUSAS_GP_T;
+#pragma unroll
+  for (int a = 0; a < NN; ++a) val[a] = nodal[a];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
+    if (GRAD) {
 #pragma unroll
-    for (int a = 0; a < (1 << DIM); ++a) {
+      for (int e = 0; e < d; ++e) {  // earlier differences: axis d is bit d - 1 of j
+#pragma unroll
+        for (int j = 0; j < NH; ++j) {
+          if (!(j & (1 << (d - 1)))) {
+            const double x0 = grad[e][j], x1 = grad[e][j | (1 << (d - 1))];
+            const double b = x1 - x0;
+            grad[e][j] = fma(t, b, x0);
+            grad[e][j | (1 << (d - 1))] = fma(-t, b, x1);
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < NN; ++a) {
       if (!(a & (1 << d))) {
-        const double c0 = v[a], c1 = v[a | (1 << d)];
-        v[a] = fma(-s, c1, c0);
-        v[a | (1 << d)] = fma(s, c1, c0);
+        const double x0 = val[a], x1 = val[a | (1 << d)];
+        const double b = x1 - x0;
+        if (GRAD) grad[d][remove_bit(a, d)] = b;
+        val[a] = fma(t, b, x0);
+        val[a | (1 << d)] = fma(-t, b, x1);
       }
     }
   }
 }
-template <>
-__device__ __forceinline__ void walsh_eval_s<0>(double*, double) {}
 
-template <int DIM>
-__device__ __forceinline__ void interp_s(const double* nodal, double* val, double (*grad)[1 << (DIM - 1)], double s) {
-  constexpr int NN = 1 << DIM;
-  double c[NN];
+// Values and gradients in true units (the differences of interp_l times 1/h).
+template <int DIM, bool GRAD>
+__device__ __forceinline__ void interp_true(const double* nodal, double* val, double (*grad)[1 << (DIM - 1)],
+                                            double inv_h) {
+  interp_l<DIM, GRAD>(nodal, val, grad);
+  if (GRAD) {
 #pragma unroll
-  for (int a = 0; a < NN; ++a) c[a] = nodal[a];
-  walsh_fwd<DIM>(c);
+    for (int d = 0; d < DIM; ++d) {
+#pragma unroll
+      for (int j = 0; j < (1 << (DIM - 1)); ++j) grad[d][j] *= inv_h;
+    }
+  }
+}
+
+// Transpose of interp_l: out_a = sum_g ( sv_g N_a(g) + sum_d f_dg h dN_a/dx_d(g) ).
+// The fluxes f[d][g] are summed over the two Gauss points along d first (the
+// difference along d is the same at both).
+template <int DIM>
+__device__ __forceinline__ void accumulate_l(const double* sv, double (*f)[1 << DIM], double* out) {
+  constexpr int NN = 1 << DIM;
+  constexpr int NH = NN / 2;
+  const double t = TUSAS_GP_T;
+  double F[DIM][NH];
+#pragma unroll
+  for (int a = 0; a < NN; ++a) out[a] = sv[a];
 #pragma unroll
   for (int d = 0; d < DIM; ++d) {
 #pragma unroll
-    for (int j = 0; j < NN / 2; ++j) grad[d][j] = c[insert_bit(j, d, 1)];
-    walsh_eval_s<DIM - 1>(grad[d], s);
+    for (int j = 0; j < NH; ++j) F[d][j] = f[d][insert_bit(j, d, 0)] + f[d][insert_bit(j, d, 1)];
   }
 #pragma unroll
-  for (int b = 0; b < NN; ++b) val[b] = c[b];
-  walsh_eval_s<DIM>(val, s);
-}
-
-template <int DIM>
-__device__ __forceinline__ void accumulate_s(const double* sv, double (*f)[1 << DIM], double* out, double s) {
-  constexpr int NN = 1 << DIM;
-  double acc[NN];
+  for (int d = DIM - 1; d >= 0; --d) {
 #pragma unroll
-  for (int g = 0; g < NN; ++g) acc[g] = sv[g];
-  walsh_fwd<DIM>(acc);
+    for (int a = 0; a < NN; ++a) {
+      if (!(a & (1 << d))) {
+        const double yL = out[a], yR = out[a | (1 << d)];
+        const double q = fma(t, yL - yR, F[d][remove_bit(a, d)]);
+        out[a] = yL - q;
+        out[a | (1 << d)] = yR + q;
+      }
+    }
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) {
-    double t[NN / 2];
+    for (int e = 0; e < d; ++e) {
 #pragma unroll
-    for (int j = 0; j < NN / 2; ++j) t[j] = f[d][insert_bit(j, d, 0)] + f[d][insert_bit(j, d, 1)];
-    walsh_fwd<DIM - 1>(t);
-#pragma unroll
-    for (int j = 0; j < NN / 2; ++j) acc[insert_bit(j, d, 1)] += t[j];
+      for (int j = 0; j < NH; ++j) {
+        if (!(j & (1 << (d - 1)))) {
+          const double yL = F[e][j], yR = F[e][j | (1 << (d - 1))];
+          const double dd = yL - yR;
+          F[e][j] = fma(-t, dd, yL);
+          F[e][j | (1 << (d - 1))] = fma(t, dd, yR);
+        }
+      }
+    }
   }
-  walsh_eval_s<DIM>(acc, s);
-#pragma unroll
-  for (int a = 0; a < NN; ++a) out[a] = acc[a];
 }
 
-// Factors of the stored linearisation for the scaled forms, by the type of a
-// coefficient: (input value | gradient) -> (output value | flux); s and 1/s
-// correct the mixed value-gradient coefficients in the transposed product;
-// the model-0 constants of the u equation, scaled.
+// Factors of the stored linearisation for the staged forms, by the type of a
+// coefficient: (input value | gradient) -> (output value | flux). interp_l gives
+// values and h times the gradients; accumulate_l takes values times the Gauss
+// weight w and fluxes times w / h, so vv = w, gv = vf = w / h, gf = w / h^2.
+// The same stored coefficients then serve the transposed product unchanged.
+// Also the model-0 constants of the u equation, scaled.
 #define TUSAS_INV_2SQRT2 0.35355339059327373
 
 struct LinScale {
   double vv, gv, vf, gf;
-  double s, inv_s;
   double mdphat, idt, thD;
   // physics constants times their factors, for the linearisation pass (lin_consts)
   double m_th_vv, tau_idt_vv, thlam_vv, tau_vv, tau2_gv, thW2_gf, half_omk_vv, m_half_thD_vf, cw_dphat_vf, cw_omk_vf,
@@ -277,7 +301,6 @@ struct NLin {
 inline LinScale lin_unit(const DevPhys& P) {
   LinScale K{};
   K.vv = K.gv = K.vf = K.gf = 1.0;
-  K.s = K.inv_s = 1.0;
   lin_consts(K, P);
   return K;
 }
@@ -535,8 +558,8 @@ __device__ __forceinline__ void gp_prev_t(const DevPhys& P, bool tf1, double phi
 // Apply the stored pointwise Jacobian (TRANS = false) or its transpose.
 // Inputs (x0, x1, xp, xg): forward = (dphi, du, dp, dg);
 // transpose = (s_phi, s_u, f_phi, f_u) test-side quantities.
-// SCALED: L, the inputs and the outputs are in the scaled forms (interp_s /
-// accumulate_s, LinScale K); otherwise in true units (K unused).
+// SCALED: L, the inputs and the outputs are in the staged forms (interp_l /
+// accumulate_l, LinScale K); otherwise in true units (K unused).
 template <int DIM, int MODEL, bool TRANS, bool SCALED = false>
 __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, double x0, double x1, const double* xp,
                                           const double* xg, GPOut<DIM>& o, const LinScale& K = LinScale{}) {
@@ -578,9 +601,8 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
   } else {
     // x0 = s_phi-hat, x1 = s_u-hat, xp = f_phi-hat, xg = f_u-hat
     double s0 = L[0] * x0, s1 = L[1] * x0;
-    const double x0p = SCALED ? x0 * K.inv_s : x0;  // gradient -> value coefficients, transposed
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o.fphi[d] = fma(L[2 + d], x0p, Hx[d]);
+    for (int d = 0; d < DIM; ++d) o.fphi[d] = fma(L[2 + d], x0, Hx[d]);
     if (MODEL == 0) {
       s0 = fma(mdphat, x1, s0);
       s1 = fma(idt, x1, s1);
@@ -597,9 +619,8 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
         gs = fma(L[o0 + 2 + d], xg[d], gs);
         nfu = fma(nv[d], xg[d], nfu);
       }
-      // value -> flux coefficients, transposed: times s in the scaled forms
-      s0 = SCALED ? fma(gs, K.s, s0) : s0 + gs;
-      s1 = fma(L[o0 + 2 + DIM] * nfu, SCALED ? K.s : 1.0, s1);
+      s0 += gs;
+      s1 = fma(L[o0 + 2 + DIM], nfu, s1);
       const double k2 = L[o0 + 5 + DIM] * nfu;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {

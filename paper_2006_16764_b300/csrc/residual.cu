@@ -22,8 +22,9 @@ namespace tusas {
 struct ElemArgs {
   DevMesh m;
   DevPhys P;
-  Scales S;
-  LinScale K;  // scaled linearisation (tangent / adjoint passes)
+  double h, inv_h;  // element size and its inverse
+  double wh;        // Gauss weight over h, w / h: the node-sum factor of the residual-type passes
+  LinScale K;       // staged-form linearisation factors (tangent / adjoint passes)
   const double* U;
   const double* Un;
   const double* V;
@@ -130,8 +131,8 @@ elem_kernel(const ElemArgs A) {
         n0[a] = sV[0][sidx[a]];
         n1[a] = sV[NVF - 1][sidx[a]];
       }
-      interp_s<DIM>(n0, v0, gv0, A.K.s);
-      interp_s<DIM>(n1, v1, gv1, A.K.s);
+      interp_l<DIM>(n0, v0, gv0);
+      interp_l<DIM>(n1, v1, gv1);
 #pragma unroll
       for (int g = 0; g < NN; ++g) {
         double L[NC];
@@ -162,10 +163,10 @@ elem_kernel(const ElemArgs A) {
         ndu[a] = sU[3][sidx[a]];
       }
       double phi[NN], u[NN], dphi[NN], du[NN], gp[DIM][NH], gu[DIM][NH], gpn[DIM][NH];
-      interp<DIM, true>(nphi, phi, gp, A.S);
-      interp<DIM, true>(nu, u, gu, A.S);
-      interp<DIM, false, double>(ndp, dphi, nullptr, A.S);
-      interp<DIM, false, double>(ndu, du, nullptr, A.S);
+      interp_true<DIM, true>(nphi, phi, gp, A.inv_h);
+      interp_true<DIM, true>(nu, u, gu, A.inv_h);
+      interp_true<DIM, false>(ndp, dphi, nullptr, A.inv_h);
+      interp_true<DIM, false>(ndu, du, nullptr, A.inv_h);
       // grad(phi^n): literal time term, or the level-n flux of the theta-method in dF/d eps4 and
       // (dF/dU^n)^T w; grad(u^n) for the latter
       const bool oldn = (MODE == M_DEPS || MODE == M_PREV_T) && A.P.theta != 1.0;
@@ -174,20 +175,20 @@ elem_kernel(const ElemArgs A) {
         double npn[NN], vpn[NN];
 #pragma unroll
         for (int a = 0; a < NN; ++a) npn[a] = sU[4][sidx[a]];
-        interp<DIM, true>(npn, vpn, gpn, A.S);
+        interp_true<DIM, true>(npn, vpn, gpn, A.inv_h);
       }
       if (MODE == M_PREV_T && oldn) {
         double nun[NN], vun[NN];
 #pragma unroll
         for (int a = 0; a < NN; ++a) nun[a] = sU[1][sidx[a]] - sU[3][sidx[a]];
-        interp<DIM, true>(nun, vun, gun, A.S);
+        interp_true<DIM, true>(nun, vun, gun, A.inv_h);
       }
       double pho[NN];
       if ((MODE == M_RES || MODE == M_RES_LIN) && A.P.phihat_old) {
         double npo[NN];
 #pragma unroll
         for (int a = 0; a < NN; ++a) npo[a] = sU[NUF - 1][sidx[a]];
-        interp<DIM, false, double>(npo, pho, nullptr, A.S);
+        interp_true<DIM, false>(npo, pho, nullptr, A.inv_h);
       } else {
 #pragma unroll
         for (int a = 0; a < NN; ++a) pho[a] = 0.0;
@@ -200,8 +201,8 @@ elem_kernel(const ElemArgs A) {
           n0[a] = sV[0][sidx[a]];
           n1[a] = sV[NVF - 1][sidx[a]];
         }
-        interp<DIM, true>(n0, w0, gw0, A.S);
-        interp<DIM, true>(n1, w1, gw1, A.S);
+        interp_true<DIM, true>(n0, w0, gw0, A.inv_h);
+        interp_true<DIM, true>(n1, w1, gw1, A.inv_h);
       }
       const int e_last = DIM == 3 ? ez : ey;
 #pragma unroll
@@ -248,8 +249,9 @@ elem_kernel(const ElemArgs A) {
             old_spatial_t<DIM, MODEL>(A.P, phi[g] - dphi[g], u[g] - du[g], pn, gn, G4n, w0[g], gv0, gw, o);
           }
         }
-        s0[g] = o.sphi;
-        s1[g] = o.su;
+        // true-unit integrands: values times h here, the node sums times w / h
+        s0[g] = o.sphi * A.h;
+        s1[g] = o.su * A.h;
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           f0[d][g] = o.fphi[d];
@@ -257,13 +259,8 @@ elem_kernel(const ElemArgs A) {
         }
       }
     }
-    if (MODE == M_JV || MODE == M_JTV) {
-      accumulate_s<DIM>(s0, f0, r0, A.K.s);
-      accumulate_s<DIM>(s1, f1, r1, A.K.s);
-    } else {
-      accumulate<DIM>(s0, f0, r0, A.S);
-      accumulate<DIM>(s1, f1, r1, A.S);
-    }
+    accumulate_l<DIM>(s0, f0, r0);
+    accumulate_l<DIM>(s1, f1, r1);
   }
 #pragma unroll
   for (int a = 0; a < NN; ++a) {
@@ -287,6 +284,10 @@ elem_kernel(const ElemArgs A) {
         acc1 += sC[NN + a][e];
       }
     }
+    if (MODE != M_JV && MODE != M_JTV) {
+      acc0 *= A.wh;
+      acc1 *= A.wh;
+    }
     const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
     A.out[node] += acc0;
     A.out[m.nn + node] += acc1;
@@ -308,19 +309,13 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
     c.S.gs[k] = pow(s, k) * 2.0 / (m.h * nnodes);
     c.S.gsw[k] = c.S.gs[k] * w;
   }
-  // scaled forms: input values / gradients come out of interp_s times 2^dim and h 2^dim / 2;
-  // accumulate_s takes values times w / 2^dim and fluxes times w / 2^dim * 2 / (h s)
-  {
-    const double al = w / nnodes, be = al * 2.0 / (m.h * s);
-    const double ga = 1.0 / nnodes, de = 2.0 / (m.h * nnodes);
-    c.K.vv = al * ga;
-    c.K.gv = al * de;
-    c.K.vf = be * ga;
-    c.K.gf = be * de;
-    c.K.s = s;
-    c.K.inv_s = 1.0 / s;
-    lin_consts(c.K, P);
-  }
+  // staged forms: interp_l gives values and h times the gradients; accumulate_l takes
+  // values times w and fluxes times w / h
+  c.K.vv = w;
+  c.K.gv = w / m.h;
+  c.K.vf = w / m.h;
+  c.K.gf = w / (m.h * m.h);
+  lin_consts(c.K, P);
   c.Ku = lin_unit(P);
   if (dim == 3) {
     c.ntx = ceil_div(m.nx, Tile<3>::X);
@@ -383,7 +378,9 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
   ElemArgs a;
   a.m = c.m;
   a.P = c.P;
-  a.S = c.S;
+  a.h = c.m.h;
+  a.inv_h = 1.0 / c.m.h;
+  a.wh = (c.m.dim == 3 ? 0.125 * c.m.h * c.m.h : 0.25 * c.m.h);
   a.K = c.K;
   a.U = U;
   a.Un = Un;
