@@ -294,6 +294,8 @@ elem_kernel(const ElemArgs A) {
   }
 }
 
+#include "tangent3.cuh"
+
 void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
   c.m = m;
   c.P = P;
@@ -341,6 +343,7 @@ size_t elem_lin_doubles(const ElemCtx& c) {
 template <int DIM, int MODEL, int MODE>
 static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
   constexpr int NE = Tile<DIM>::X * Tile<DIM>::Y * Tile<DIM>::Z;
+  constexpr bool tile3 = DIM == 3 && (MODE == M_JV || MODE == M_JTV);
   for (int col = 0; col < (1 << DIM); ++col) {
     const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
     a.color = col;
@@ -349,7 +352,10 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
     a.ctz = DIM == 3 ? (c.ntz - cz + 1) / 2 : 1;
     const long long blocks = (long long)a.ctx * a.cty * a.ctz;
     if (blocks <= 0) continue;
-    elem_kernel<DIM, MODEL, MODE><<<(unsigned)blocks, NE, 0, st>>>(a);
+    if constexpr (tile3)
+      tan3_kernel<MODEL, MODE == M_JTV><<<(unsigned)blocks, Tan3::NE, Tan3::BYTES, st>>>(a);
+    else
+      elem_kernel<DIM, MODEL, MODE><<<(unsigned)blocks, NE, 0, st>>>(a);
     count_launches(1);
   }
   return cudaGetLastError();

@@ -94,6 +94,13 @@ def test_residual_is_bitwise_deterministic():
         assert np.array_equal(host(F), ref)
     assert h.dot(tU, tU) == h.dot(tU, tU)
     assert abs(h.dot(tU, tU) - float(U @ U)) <= 1e-12 * float(U @ U)
+    # the tangent and its transpose (tile-level sums in shared memory) repeat bitwise too
+    tv = dev(synth.random_vector(mesh, 4))
+    for op in (h.jvp, h.jtvp):
+        ref = host(op(tU, tv, dev(np.zeros_like(U)))).copy()
+        for _ in range(5):
+            op(tU, tv, F)
+            assert np.array_equal(host(F), ref)
 
 
 def _precond_case(dim, fp32, kind=2):
