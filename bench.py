@@ -44,12 +44,12 @@ CPU_SAMPLE = (48, 48, 32)
 # Algorithmic bytes per element: nodal reads/writes (8 B per field value, one
 # node per element) plus the stored linearisation (23 coefficients x 8 Gauss
 # points x 8 B).
-FP64_FLOPS_PER_ELEM = {"residual": 1431.5, "residual_lin": 2415.5, "jv": 802.7}
+FP64_FLOPS_PER_ELEM = {"residual": 1323.3, "residual_lin": 2163.3, "jv": 802.7}
 BYTES_PER_ELEM = {"residual": 48.0, "residual_lin": 48.0 + 1472.0, "jv": 32.0 + 1472.0}
 # DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
 # with the elements processed (same tiles, same per-element streams).
-NCU_BYTES_PER_ELEM = {"residual": 153.0, "residual_lin": 1511.4, "jv": 1609.7}
+NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1511.3, "jv": 1609.6}
 
 
 def parse():
@@ -664,7 +664,7 @@ def run_ours(args, ws, rank, local):
     achieved = flops / (per_launch * 1e-3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
             "frac": achieved * 1e12 / fp64_peak, "traffic": NCU_BYTES_PER_ELEM[dom] * ne,
-            "kernel": ("tan3_kernel (3D alloy tangent J v)" if dom == "jv" else f"elem_kernel {dom} (3D alloy)")
+            "kernel": ("tan3_kernel (3D alloy tangent J v)" if dom == "jv" else f"res3_kernel {dom} (3D alloy)")
             + ", one operator application = 8 colour launches",
             "launch_ms": per_launch, "launches": d_cnt,
             "peak_kind": "fp64 FMA-chain throughput measured in this run (tusas_fma_peak)",

@@ -363,27 +363,38 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
   }
   if constexpr (LIN) {
   // ---- pointwise Jacobian -------------------------------------------------
-  double ap[DIM];  // da/dp_i = 16 eps n_i (n_i^2 - sn) / |p|
+  // m_i = n_i^2 - sn, R_i = n_i m_i: da/dp_i = 16 eps R_i / |p|
+  double R[DIM];
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) ap[d] = c16 * A.n[d] * (A.n2[d] - A.sn) * A.r;
+  for (int d = 0; d < DIM; ++d) R[d] = A.n[d] * (A.n2[d] - A.sn);
   const double dbulk = (1.0 - 3.0 * phi2) + 4.0 * P.lam * phi * om * ug;
   const double tfac = P.time_form == 0 ? dphidt : phi * P.idt;  // multiplies d(B a^2)
   L[0] = fma(K.m_th_vv, dbulk, K.tau_idt_vv * B * a2);           // alpha_phi
   L[1] = fma(K.thlam_vv, om * om, K.tau_vv * omk * a2 * tfac);  // alpha_u
-  const double c2a = K.tau2_gv * B * tfac * A.a;
+  const double c2a = K.tau2_gv * B * tfac * A.a * (c16 * A.r);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * ap[d];         // alpha_p
-  // H = theta W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn))
-  //            + n_i n_j (32 eps a (sn - n_i^2 - n_j^2) + 256 eps^2 (n_i^2 - sn)(n_j^2 - sn)) ]
-  const double e32a = 32.0 * eps * A.a, e256 = 256.0 * eps * eps, e16a = 16.0 * eps * A.a;
+  for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * R[d];  // alpha_p = 2 tau0 B a da/dp
+  // H = theta W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn)) + n_i n_j B_ij ],
+  //   B_ij = 256 eps^2 m_i m_j + 32 eps a (sn - n_i^2 - n_j^2) = 256 eps^2 m_i m_j - 32 eps a (m_i + m_j + sn).
+  // With n_i^2 = m_i + sn: n_i n_j B_ij = P_i R_j - T_i n_j, P_i = n_i (256 eps^2 m_i - 32 eps a),
+  // T_i = 32 eps a n_i^3, and the diagonal term is a^2 + 32 eps a sn + 48 eps a m_i;
+  // theta W0^2 and the coefficient factor ride on P_i, T_i and the diagonal constants.
+  const double e32a = 32.0 * eps * A.a, e256 = 256.0 * eps * eps;
+  const double kt = K.thW2_gf * e32a;
+  const double kd0 = K.thW2_gf * fma(e32a, A.sn, a2), kd1 = 1.5 * kt;
+  double Pk[DIM], Tk[DIM];
+#pragma unroll
+  for (int i = 0; i < DIM; ++i) {
+    Pk[i] = K.thW2_gf * A.n[i] * fma(e256, A.n2[i] - A.sn, -e32a);
+    Tk[i] = kt * A.n[i] * A.n2[i];
+  }
 #pragma unroll
   for (int i = 0; i < DIM; ++i) {
 #pragma unroll
     for (int j = i; j < DIM; ++j) {
-      const double mi = A.n2[i] - A.sn, mj = A.n2[j] - A.sn;
-      double v = A.n[i] * A.n[j] * (e32a * (A.sn - A.n2[i] - A.n2[j]) + e256 * mi * mj);
-      if (i == j) v += a2 + e16a * (3.0 * A.n2[i] - A.sn);
-      L[2 + DIM + sym_index<DIM>(i, j)] = K.thW2_gf * v;
+      double v = fma(Pk[i], R[j], -Tk[i] * A.n[j]);
+      if (i == j) v += fma(kd1, A.n2[i] - A.sn, kd0);
+      L[2 + DIM + sym_index<DIM>(i, j)] = v;
     }
   }
   if (MODEL == 1) {
@@ -391,7 +402,6 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u
     L[o0 + 0] = K.mdphat * B;                                // beta_phi
     L[o0 + 1] = fma(Acoef, K.idt, -K.half_omk_vv * phihat);  // beta_u
     // direction of the antitrapping current and its derivative factors
-    const double cw = TUSAS_INV_2SQRT2 * P.W0;
     double nv[DIM];
 #pragma unroll
     for (int d = 0; d < DIM; ++d) nv[d] = P.jat_norm ? A.n[d] : p[d];

@@ -442,6 +442,11 @@ __global__ void k_max_partials(int nb, const double* __restrict__ partials, doub
 // ---------------------------------------------------------------------------
 // Chebyshev smoother, residual, transfers
 // ---------------------------------------------------------------------------
+// resident 256-thread blocks per SM the smoother kernels are compiled for
+#ifndef TUSAS_SMOOTH_MINB
+#define TUSAS_SMOOTH_MINB 8
+#endif
+
 template <typename T>
 struct Coef2 {
   T a[2], b[2];
@@ -449,7 +454,7 @@ struct Coef2 {
 
 // r = D^-1 (b - A x) (or D^-1 b if x == nullptr, and then x = 0); d = r * it
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
+__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(256, 6) k_cheb_init(DevMesh m, const T* __rest
 
 // x += d; if !last: r -= D^-1 A d; dout = c1 d + c2 r
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
+__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -489,7 +494,7 @@ __global__ void __launch_bounds__(256, 6) k_cheb_step(DevMesh m, const T* __rest
 }
 
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, 6) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
   constexpr int NS = Sten<DIM, R>::V;
   {

@@ -294,7 +294,7 @@ elem_kernel(const ElemArgs A) {
   }
 }
 
-#include "tangent3.cuh"
+#include "tile3.cuh"
 
 void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
   c.m = m;
@@ -343,7 +343,14 @@ size_t elem_lin_doubles(const ElemCtx& c) {
 template <int DIM, int MODEL, int MODE>
 static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
   constexpr int NE = Tile<DIM>::X * Tile<DIM>::Y * Tile<DIM>::Z;
-  constexpr bool tile3 = DIM == 3 && (MODE == M_JV || MODE == M_JTV);
+  // 3D: tile-level sum factorisation for the tangent and residual passes
+  constexpr bool tan3 = DIM == 3 && (MODE == M_JV || MODE == M_JTV);
+  constexpr bool res3 = DIM == 3 && (MODE == M_RES || MODE == M_RES_LIN);
+  if constexpr (res3) {
+    const cudaError_t e = cudaFuncSetAttribute(res3_kernel<MODEL, MODE == M_RES_LIN>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Res3::BYTES);
+    if (e != cudaSuccess) return e;
+  }
   for (int col = 0; col < (1 << DIM); ++col) {
     const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
     a.color = col;
@@ -352,8 +359,10 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
     a.ctz = DIM == 3 ? (c.ntz - cz + 1) / 2 : 1;
     const long long blocks = (long long)a.ctx * a.cty * a.ctz;
     if (blocks <= 0) continue;
-    if constexpr (tile3)
-      tan3_kernel<MODEL, MODE == M_JTV><<<(unsigned)blocks, Tan3::NE, Tan3::BYTES, st>>>(a);
+    if constexpr (tan3)
+      tan3_kernel<MODEL, MODE == M_JTV><<<(unsigned)blocks, T3::NE, Tan3::BYTES, st>>>(a);
+    else if constexpr (res3)
+      res3_kernel<MODEL, MODE == M_RES_LIN><<<(unsigned)blocks, T3::NE, Res3::BYTES, st>>>(a);
     else
       elem_kernel<DIM, MODEL, MODE><<<(unsigned)blocks, NE, 0, st>>>(a);
     count_launches(1);

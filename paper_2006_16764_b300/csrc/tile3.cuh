@@ -1,0 +1,462 @@
+// 3D element passes with tile-level sum factorisation (tangent, transposed
+// tangent, residual, residual + linearisation).
+//
+// The staged 1D forms of interp_l / accumulate_l work axis by axis, and the
+// x- and y-stages of an element only see the nodes of one x-edge or one face:
+// neighbouring elements of a tile share them. These kernels run those stages
+// once per edge / face of the 8 x 4 x 4 tile through shared memory instead of
+// once per element: forward, x-stage per x-edge, y-stage per xy-face, z-stage
+// per element; after the pointwise integrands the transposed z-stage per
+// element, contributions summed per face, transposed y-stage per face, summed
+// per x-edge, transposed x-stage per x-edge, summed per node. The operations
+// on every quantity are those of interp_l (bitwise the same Gauss-point
+// values) and of accumulate_l up to the order of the sums. Per element and
+// field this takes about 40 FP64 operations for values and gradients (54 per
+// element alone), 24 for values alone (36), and about 76 for the accumulation
+// with the node sums (90).
+//
+// Included by residual.cu inside namespace tusas, after ElemArgs.
+#pragma once
+
+struct T3 {
+  static const int TX = Tile<3>::X, TY = Tile<3>::Y, TZ = Tile<3>::Z;
+  static const int NX = TX + 1, NY = TY + 1, NZ = TZ + 1;
+  static const int NT = NX * NY * NZ;  // nodes
+  static const int NE = TX * TY * TZ;  // elements = threads
+  static const int UX = TX * NY * NZ;  // x-edges (ex, ny, nz)
+  static const int UY = TX * TY * NZ;  // xy-faces (ex, ey, nz)
+  // transposed buffers (doubles), aliased over the forward ones once those are read
+  static const int ZC = 32 * NE;  // [2 fields][2 levels][8][NE]
+  static const int YC = 12 * UY;  // [2 fields][2 slots][3][UY]
+  static const int XC = 4 * UX;   // [2 fields][2 slots][UX]
+  static const int BWD = ZC + YC;
+  // forward buffers of one field: x-stage (3 or 2 arrays of UX), y-stage (8 or 4 of UY)
+  static const int XG = 3 * UX, XV = 2 * UX, YG = 8 * UY, YV = 4 * UY;
+};
+
+// ---- forward stages, one field ----------------------------------------------------
+// x-stage per x-edge: [0] value at the lower x Gauss point, [1] upper, [2] difference (GRAD)
+template <bool GRAD>
+__device__ __forceinline__ void t3_x(const double* sN, double* X, int tid) {
+  const double t = TUSAS_GP_T;
+  for (int u = tid; u < T3::UX; u += T3::NE) {
+    const int n0 = u % T3::TX + T3::NX * (u / T3::TX);
+    const double x0 = sN[n0], x1 = sN[n0 + 1];
+    const double bb = x1 - x0;
+    X[u] = fma(t, bb, x0);
+    X[T3::UX + u] = fma(-t, bb, x1);
+    if (GRAD) X[2 * T3::UX + u] = bb;
+  }
+}
+
+// y-stage per xy-face from the x-edges at ny = ey, ey + 1: [0..3] values at
+// (x bit, y bit) = (k & 1, k >> 1); GRAD: [4, 5] y-differences at x bit, [6, 7] x-differences at y bit
+template <bool GRAD>
+__device__ __forceinline__ void t3_y(const double* X, double* Y, int tid) {
+  constexpr int TX = T3::TX, TY = T3::TY, NY = T3::NY, UX = T3::UX, UY = T3::UY;
+  const double t = TUSAS_GP_T;
+  for (int u = tid; u < UY; u += T3::NE) {
+    const int ex = u % TX, ey = (u / TX) % TY, nz = u / (TX * TY);
+    const int lo = ex + TX * (ey + NY * nz), hi = lo + TX;
+    if (GRAD) {  // x-differences along y first (the order of interp_l)
+      const double x0 = X[2 * UX + lo], x1 = X[2 * UX + hi];
+      const double bb = x1 - x0;
+      Y[6 * UY + u] = fma(t, bb, x0);
+      Y[7 * UY + u] = fma(-t, bb, x1);
+    }
+#pragma unroll
+    for (int xb = 0; xb < 2; ++xb) {
+      const double x0 = X[xb * UX + lo], x1 = X[xb * UX + hi];
+      const double bb = x1 - x0;
+      if (GRAD) Y[(4 + xb) * UY + u] = bb;
+      Y[xb * UY + u] = fma(t, bb, x0);
+      Y[(xb + 2) * UY + u] = fma(-t, bb, x1);
+    }
+  }
+}
+
+// z-stage of element tid from the faces below and above it: val[g] and, if GRAD,
+// grd[d][j] = h dv/dx_d at the Gauss points whose other-axis bits are j (interp_l's layout)
+template <bool GRAD>
+__device__ __forceinline__ void t3_z(const double* Y, int tid, double* val, double (*grd)[4]) {
+  constexpr int UY = T3::UY;
+  const double t = TUSAS_GP_T;
+  const int u0 = tid, u1 = tid + T3::TX * T3::TY;
+  if (GRAD) {
+#pragma unroll
+    for (int yb = 0; yb < 2; ++yb) {  // x-differences along z: grd[0][y + 2 z]
+      const double x0 = Y[(6 + yb) * UY + u0], x1 = Y[(6 + yb) * UY + u1];
+      const double bb = x1 - x0;
+      grd[0][yb] = fma(t, bb, x0);
+      grd[0][yb + 2] = fma(-t, bb, x1);
+    }
+#pragma unroll
+    for (int xb = 0; xb < 2; ++xb) {  // y-differences along z: grd[1][x + 2 z]
+      const double x0 = Y[(4 + xb) * UY + u0], x1 = Y[(4 + xb) * UY + u1];
+      const double bb = x1 - x0;
+      grd[1][xb] = fma(t, bb, x0);
+      grd[1][xb + 2] = fma(-t, bb, x1);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // values along z; z-differences grd[2][x + 2 y]
+    const double x0 = Y[k * UY + u0], x1 = Y[k * UY + u1];
+    const double bb = x1 - x0;
+    if (GRAD) grd[2][k] = bb;
+    val[k] = fma(t, bb, x0);
+    val[k + 4] = fma(-t, bb, x1);
+  }
+}
+
+// ---- transposed stages ----------------------------------------------------------------
+// Transposed z-stage of one element and field (integrands sv at the Gauss points, fluxes
+// fl[d][g]): contributions to the face below (lo) and above (hi) in the face layout.
+__device__ __forceinline__ void t3_zt(const double* sv, double (*fl)[8], double* lo, double* hi) {
+  const double t = TUSAS_GP_T;
+  double F[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) F[d][j] = fl[d][insert_bit(j, d, 0)] + fl[d][insert_bit(j, d, 1)];
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {  // values with the z-differences
+    const double yL = sv[k], yR = sv[k + 4];
+    const double q = fma(t, yL - yR, F[2][k]);
+    lo[k] = yL - q;
+    hi[k] = yR + q;
+  }
+#pragma unroll
+  for (int yb = 0; yb < 2; ++yb) {  // x-differences: transposed interpolation along z
+    const double yL = F[0][yb], yR = F[0][yb + 2];
+    const double dd = yL - yR;
+    lo[6 + yb] = fma(-t, dd, yL);
+    hi[6 + yb] = fma(t, dd, yR);
+  }
+#pragma unroll
+  for (int xb = 0; xb < 2; ++xb) {  // y-differences
+    const double yL = F[1][xb], yR = F[1][xb + 2];
+    const double dd = yL - yR;
+    lo[4 + xb] = fma(-t, dd, yL);
+    hi[4 + xb] = fma(t, dd, yR);
+  }
+}
+
+// Tile-level transposed y- and x-stages and node sums of the two output fields, given
+// each element's transposed z-stage outputs (zlo, zhi; zero for elements outside the
+// mesh). Starts with a barrier: the shared buffers alias the forward ones. The node
+// sums are multiplied by `scale` if SCALE and added to out.
+template <bool SCALE>
+__device__ __forceinline__ void t3_tile_t(double* sm, const double (*zlo)[8], const double (*zhi)[8], int tid,
+                                          const DevMesh& m, int ex0, int ey0, int ez0, double scale, double* out) {
+  constexpr int TX = T3::TX, TY = T3::TY, TZ = T3::TZ, NX = T3::NX, NY = T3::NY;
+  constexpr int NT = T3::NT, NE = T3::NE, UX = T3::UX, UY = T3::UY;
+  const double t = TUSAS_GP_T;
+  double* sZc = sm;
+  double* sYc = sm + T3::ZC;
+  double* sXc = sm;
+  __syncthreads();  // every forward read is done
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      sZc[((f * 2 + 0) * 8 + k) * NE + tid] = zlo[f][k];
+      sZc[((f * 2 + 1) * 8 + k) * NE + tid] = zhi[f][k];
+    }
+  }
+  __syncthreads();
+
+  // per face: the element above (its lower level) plus the element below (upper level),
+  // transposed y-stage to the x-edges at ny = ey (slot 0) and ey + 1 (slot 1)
+  for (int u = tid; u < UY; u += NE) {
+    const int nz = u / (TX * TY);  // uniform across a warp (32 faces per level)
+    const int e_up = u, e_dn = u - TX * TY;
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      double c[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const double a = nz < TZ ? sZc[((f * 2 + 0) * 8 + k) * NE + e_up] : 0.0;
+        c[k] = nz > 0 ? a + sZc[((f * 2 + 1) * 8 + k) * NE + e_dn] : a;
+      }
+      double* Yc = sYc + 6 * f * UY;  // [slot][X0, X1, Xb][u]
+#pragma unroll
+      for (int xb = 0; xb < 2; ++xb) {
+        const double yL = c[xb], yR = c[xb + 2];
+        const double q = fma(t, yL - yR, c[4 + xb]);
+        Yc[(0 * 3 + xb) * UY + u] = yL - q;
+        Yc[(1 * 3 + xb) * UY + u] = yR + q;
+      }
+      const double dd = c[6] - c[7];
+      Yc[(0 * 3 + 2) * UY + u] = fma(-t, dd, c[6]);
+      Yc[(1 * 3 + 2) * UY + u] = fma(t, dd, c[7]);
+    }
+  }
+  __syncthreads();
+
+  // per x-edge (ex, ny, nz): the faces on both sides in y, transposed x-stage
+  for (int u = tid; u < UX; u += NE) {
+    const int ex = u % TX, ny = (u / TX) % NY, nz = u / (TX * NY);
+    const int fa = ex + TX * (ny + TY * nz);  // face (ex, ny, nz): slot 0
+    const int fb = fa - TX;                   // face (ex, ny - 1, nz): slot 1
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const double* Yc = sYc + 6 * f * UY;
+      double c[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double a = ny < TY ? Yc[(0 * 3 + k) * UY + fa] : 0.0;
+        const double bb = ny > 0 ? Yc[(1 * 3 + k) * UY + fb] : 0.0;
+        c[k] = a + bb;
+      }
+      const double q = fma(t, c[0] - c[1], c[2]);
+      sXc[(f * 2 + 0) * UX + u] = c[0] - q;
+      sXc[(f * 2 + 1) * UX + u] = c[1] + q;
+    }
+  }
+  __syncthreads();
+
+  // node sums in fixed order, read-modify-write
+  for (int s = tid; s < NT; s += NE) {
+    const int nx_ = s % NX, r = s / NX;
+    const int ny_ = r % NY, nz_ = r / NY;
+    const int gx = ex0 + nx_, gy = ey0 + ny_, gz = ez0 + nz_;
+    if (gx >= m.nnx || gy >= m.nny || gz >= m.nnz) continue;
+    const int ea = nx_ + TX * r;  // edge (nx, ny, nz): left node, slot 0
+    const int eb = ea - 1;        // edge (nx - 1, ny, nz): right node, slot 1
+    double acc[2];
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const double a = nx_ < TX ? sXc[(f * 2 + 0) * UX + ea] : 0.0;
+      const double bb = nx_ > 0 ? sXc[(f * 2 + 1) * UX + eb] : 0.0;
+      acc[f] = a + bb;
+      if (SCALE) acc[f] *= scale;
+    }
+    const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
+    out[node] += acc[0];
+    out[m.nn + node] += acc[1];
+  }
+}
+
+// tile coordinates of this block (colour-strided tile grid)
+struct T3Tile {
+  int tx, ty, tz, ex0, ey0, ez0;
+  __device__ __forceinline__ T3Tile(const ElemArgs& A) {
+    int b = blockIdx.x;
+    const int ix = b % A.ctx;
+    b /= A.ctx;
+    const int iy = b % A.cty;
+    const int iz = b / A.cty;
+    tx = 2 * ix + (A.color & 1);
+    ty = 2 * iy + ((A.color >> 1) & 1);
+    tz = 2 * iz + ((A.color >> 2) & 1);
+    ex0 = tx * T3::TX;
+    ey0 = ty * T3::TY;
+    ez0 = tz * T3::TZ;
+  }
+};
+
+// stage one nodal field of the tile (zero outside the mesh); x = f(node) for in-mesh nodes
+template <typename F>
+__device__ __forceinline__ void t3_stage(double* sN, const DevMesh& m, const T3Tile& T, int tid, F x) {
+  for (int s = tid; s < T3::NT; s += T3::NE) {
+    const int lx = s % T3::NX, ly = (s / T3::NX) % T3::NY, lz = s / (T3::NX * T3::NY);
+    const int gx = T.ex0 + lx, gy = T.ey0 + ly, gz = T.ez0 + lz;
+    const bool ok = gx < m.nnx && gy < m.nny && gz < m.nnz;
+    sN[s] = ok ? x(gx + (i64)m.nnx * (gy + (i64)m.nny * gz)) : 0.0;
+  }
+}
+
+// ---- tangent J v (TRANS = false) and J^T w (TRANS = true) ------------------------------
+struct Tan3 {
+  static const int OFF_X = 2 * T3::NT;             // [2][3][UX], after the staged nodes
+  static const int OFF_Y = OFF_X + 2 * T3::XG;     // [2][8][UY]
+  static const int FWD = OFF_Y + 2 * T3::YG;
+  static const int DOUBLES = FWD > T3::BWD ? FWD : T3::BWD;
+  static const size_t BYTES = sizeof(double) * DOUBLES;
+};
+static_assert(Tan3::BYTES <= 48 * 1024, "tan3_kernel launches without the large-shared-memory opt-in");
+
+template <int MODEL, bool TRANS>
+__global__ void __launch_bounds__(T3::NE, 3) tan3_kernel(const ElemArgs A) {
+  constexpr int NE = T3::NE;
+  constexpr int NC = NLin<3, MODEL>::VALUE;
+  extern __shared__ double sm[];
+  const DevMesh& m = A.m;
+  const T3Tile T(A);
+  const int tid = threadIdx.x;
+  double* sN = sm;
+  double* sX = sm + Tan3::OFF_X;
+  double* sY = sm + Tan3::OFF_Y;
+
+  t3_stage(sN, m, T, tid, [&](i64 n) { return A.V[n]; });
+  t3_stage(sN + T3::NT, m, T, tid, [&](i64 n) { return A.V[m.nn + n]; });
+  __syncthreads();
+  t3_x<true>(sN, sX, tid);
+  t3_x<true>(sN + T3::NT, sX + T3::XG, tid);
+  __syncthreads();
+  t3_y<true>(sX, sY, tid);
+  t3_y<true>(sX + T3::XG, sY + T3::YG, tid);
+  __syncthreads();
+
+  const int lx = tid % T3::TX, ly = (tid / T3::TX) % T3::TY, lz = tid / (T3::TX * T3::TY);
+  const bool valid = T.ex0 + lx < m.nx && T.ey0 + ly < m.ny && T.ez0 + lz < m.nz;
+  double zlo[2][8], zhi[2][8];
+  if (valid) {
+    double val[2][8], grd[2][3][4];
+    t3_z<true>(sY, tid, val[0], grd[0]);
+    t3_z<true>(sY + T3::YG, tid, val[1], grd[1]);
+    const i64 tile_id = T.tx + (i64)A.ntx * (T.ty + (i64)A.nty * T.tz);
+    const double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
+    double s0[8], s1[8], f0[3][8], f1[3][8];
+    GPOut<3> o;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      double L[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) L[c] = __ldg(linp + (c * 8 + g) * NE);
+      double xp[3], xg[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        xp[d] = grd[0][d][remove_bit(g, d)];
+        xg[d] = grd[1][d][remove_bit(g, d)];
+      }
+      lin_apply<3, MODEL, TRANS, true>(A.P, L, val[0][g], val[1][g], xp, xg, o, A.K);
+      s0[g] = o.sphi;
+      s1[g] = o.su;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        f0[d][g] = o.fphi[d];
+        f1[d][g] = o.fu[d];
+      }
+    }
+    t3_zt(s0, f0, zlo[0], zhi[0]);
+    t3_zt(s1, f1, zlo[1], zhi[1]);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) zlo[f][k] = zhi[f][k] = 0.0;
+    }
+  }
+  t3_tile_t<false>(sm, zlo, zhi, tid, m, T.ex0, T.ey0, T.ez0, 1.0, A.out);
+}
+
+// ---- residual (LIN = false) and residual + stored linearisation (LIN = true) -----------
+// Nodal fields: phi, u (with gradients), phi - phi^n, u - u^n (values), phi^n (with
+// gradients, for the difference-of-products time term) and phihat_old (values, for the
+// Eq. (theta) estimate); the optional ones are staged only when used.
+struct Res3 {
+  static const int NF = 6;
+  static const int OFF_X = 0;                                   // x-stage of the 6 fields
+  static const int X_PHI = 0, X_U = T3::XG, X_DP = 2 * T3::XG, X_DU = X_DP + T3::XV, X_PN = X_DU + T3::XV,
+                   X_PO = X_PN + T3::XG;
+  static const int XS = X_PO + T3::XV;
+  static const int OFF_N = XS;                                  // staged nodes [6][NT]
+  static const int OFF_Y = XS;                                  // y-stage (aliases the nodes)
+  static const int Y_PHI = 0, Y_U = T3::YG, Y_DP = 2 * T3::YG, Y_DU = Y_DP + T3::YV, Y_PN = Y_DU + T3::YV,
+                   Y_PO = Y_PN + T3::YG;
+  static const int YS = Y_PO + T3::YV;
+  static const int NS = NF * T3::NT;
+  static const int FWD = XS + (YS > NS ? YS : NS);
+  static const int DOUBLES = FWD > T3::BWD ? FWD : T3::BWD;
+  static const size_t BYTES = sizeof(double) * DOUBLES;
+};
+
+template <int MODEL, bool LIN>
+__global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
+  constexpr int NE = T3::NE, NT = T3::NT;
+  constexpr int NC = NLin<3, MODEL>::VALUE;
+  extern __shared__ double sm[];
+  const DevMesh& m = A.m;
+  const T3Tile T(A);
+  const int tid = threadIdx.x;
+  const bool tf1 = A.P.time_form != 0;
+  const bool pho_on = A.P.phihat_old && A.phold;
+  double* sN = sm + Res3::OFF_N;
+  double* sX = sm + Res3::OFF_X;
+  double* sY = sm + Res3::OFF_Y;
+
+  t3_stage(sN, m, T, tid, [&](i64 n) { return A.U[n]; });
+  t3_stage(sN + NT, m, T, tid, [&](i64 n) { return A.U[m.nn + n]; });
+  t3_stage(sN + 2 * NT, m, T, tid, [&](i64 n) { return A.U[n] - A.Un[n]; });
+  t3_stage(sN + 3 * NT, m, T, tid, [&](i64 n) { return A.U[m.nn + n] - A.Un[m.nn + n]; });
+  if (tf1) t3_stage(sN + 4 * NT, m, T, tid, [&](i64 n) { return A.Un[n]; });
+  if (pho_on) t3_stage(sN + 5 * NT, m, T, tid, [&](i64 n) { return A.phold[n]; });
+  __syncthreads();
+  t3_x<true>(sN, sX + Res3::X_PHI, tid);
+  t3_x<true>(sN + NT, sX + Res3::X_U, tid);
+  t3_x<false>(sN + 2 * NT, sX + Res3::X_DP, tid);
+  t3_x<false>(sN + 3 * NT, sX + Res3::X_DU, tid);
+  if (tf1) t3_x<true>(sN + 4 * NT, sX + Res3::X_PN, tid);
+  if (pho_on) t3_x<false>(sN + 5 * NT, sX + Res3::X_PO, tid);
+  __syncthreads();  // the y-stage overwrites the staged nodes
+  t3_y<true>(sX + Res3::X_PHI, sY + Res3::Y_PHI, tid);
+  t3_y<true>(sX + Res3::X_U, sY + Res3::Y_U, tid);
+  t3_y<false>(sX + Res3::X_DP, sY + Res3::Y_DP, tid);
+  t3_y<false>(sX + Res3::X_DU, sY + Res3::Y_DU, tid);
+  if (tf1) t3_y<true>(sX + Res3::X_PN, sY + Res3::Y_PN, tid);
+  if (pho_on) t3_y<false>(sX + Res3::X_PO, sY + Res3::Y_PO, tid);
+  __syncthreads();
+
+  const int lx = tid % T3::TX, ly = (tid / T3::TX) % T3::TY, lz = tid / (T3::TX * T3::TY);
+  const int ez = T.ez0 + lz;
+  const bool valid = T.ex0 + lx < m.nx && T.ey0 + ly < m.ny && ez < m.nz;
+  double zlo[2][8], zhi[2][8];
+  if (valid) {
+    double phi[8], u[8], dphi[8], du[8], pho[8], gp[3][4], gu[3][4], gpn[3][4];
+    t3_z<true>(sY + Res3::Y_PHI, tid, phi, gp);
+    t3_z<true>(sY + Res3::Y_U, tid, u, gu);
+    t3_z<false>(sY + Res3::Y_DP, tid, dphi, nullptr);
+    t3_z<false>(sY + Res3::Y_DU, tid, du, nullptr);
+    if (tf1) {
+      double vpn[8];
+      t3_z<true>(sY + Res3::Y_PN, tid, vpn, gpn);
+    }
+    if (pho_on) {
+      t3_z<false>(sY + Res3::Y_PO, tid, pho, nullptr);
+    } else {
+#pragma unroll
+      for (int g = 0; g < 8; ++g) pho[g] = 0.0;
+    }
+    const i64 tile_id = T.tx + (i64)A.ntx * (T.ty + (i64)A.nty * T.tz);
+    double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
+    double s0[8], s1[8], f0[3][8], f1[3][8];
+    GPOut<3> o;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) {
+      double p[3], gg[3], pn[3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        p[d] = gp[d][remove_bit(g, d)] * A.inv_h;
+        gg[d] = gu[d][remove_bit(g, d)] * A.inv_h;
+        pn[d] = tf1 ? gpn[d][remove_bit(g, d)] * A.inv_h : 0.0;
+      }
+      double G4 = 0.0;
+      if (MODEL == 1 && A.P.has_g4) G4 = (gp_last_coord<3>(m, ez, g) - A.P.zT - A.P.Vp * A.P.t_new) / A.P.lT;
+      double L[LIN ? NC : 1];
+      pointwise<3, MODEL, LIN>(A.P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L, A.K);
+      if (LIN) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) linp[(c * 8 + g) * NE] = L[c];
+      }
+      // true-unit integrands: values times h here, the node sums times w / h
+      s0[g] = o.sphi * A.h;
+      s1[g] = o.su * A.h;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        f0[d][g] = o.fphi[d];
+        f1[d][g] = o.fu[d];
+      }
+    }
+    t3_zt(s0, f0, zlo[0], zhi[0]);
+    t3_zt(s1, f1, zlo[1], zhi[1]);
+  } else {
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+#pragma unroll
+      for (int k = 0; k < 8; ++k) zlo[f][k] = zhi[f][k] = 0.0;
+    }
+  }
+  t3_tile_t<true>(sm, zlo, zhi, tid, m, T.ex0, T.ey0, T.ez0, A.wh, A.out);
+}
