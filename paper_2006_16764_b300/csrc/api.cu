@@ -573,8 +573,9 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
 
 // Flexible right-preconditioned restarted GMRES with classical Gram-Schmidt
 // applied twice, x0 = 0; solves J x = b (b = -F) to ||b - J x|| <= tol_abs.
+// resid_out: the final residual norm (the Givens estimate, or the true norm after a restart).
 static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol_abs, int* its_out,
-                 tusas_stats* stats, bool* converged = nullptr, int maxit = -1) {
+                 tusas_stats* stats, bool* converged = nullptr, int maxit = -1, double* resid_out = nullptr) {
   const int m = h->prm.gmres_restart;
   const i64 N = h->N;
   std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), col(64);
@@ -659,6 +660,7 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
   }
   *its_out = its;
   if (converged) *converged = resid <= tol_abs;
+  if (resid_out) *resid_out = resid;
   return TUSAS_OK;
 }
 
@@ -713,7 +715,8 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     TCK(tusas::vfill(N, 0.0, h->Ft, h->st));
     TCK(tusas::vaxpy(N, -1.0, h->F, h->Ft, h->st));
     int its = 0;
-    rc = gmres(h, exact ? OP_EXACT : OP_FD, h->Ft, h->dU, eta * S.fnorm, &its, &S);
+    double rlin = 0.0;
+    rc = gmres(h, exact ? OP_EXACT : OP_FD, h->Ft, h->dU, eta * S.fnorm, &its, &S, nullptr, -1, &rlin);
     if (rc) return rc;
     S.gmres_its += its;
     if (S.newton_its < 32) S.gmres_per_newton[S.newton_its] = its;
@@ -721,16 +724,30 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     bool accepted = false;
     for (int ls = 0; ls <= p.linesearch_max; ++ls) {
       TCK(tusas::vxpay(N, h->U, lam, nullptr, h->dU, h->Ut, h->st));
+      // When the linear model ||F + J dU|| is well below the Newton tolerance the full step
+      // is expected to converge: evaluate F alone, and store the linearisation at the trial
+      // point only if the Newton loop goes on.
+      const bool lin_now = exact && !(ls == 0 && rlin <= 0.1 * tol);
       t0 = tbeg(h);
-      TCK(tusas::elem_run(exact ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t,
+      TCK(tusas::elem_run(lin_now ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t,
                           h->st, old_init(h), old_ph(h)));
-      tend(h, exact ? TUSAS_T_RESIDUAL_LIN : TUSAS_T_RESIDUAL, t0);
+      tend(h, lin_now ? TUSAS_T_RESIDUAL_LIN : TUSAS_T_RESIDUAL, t0);
       S.residual_evals++;
       rc = host_norm(h, h->Ft, &ftn);
       if (rc) return rc;
       if (!isfinite(ftn)) return fail(h, TUSAS_ENONFINITE, "non-finite residual norm in the line search");
       if (ftn <= S.fnorm) {
         accepted = true;
+        if (exact && !lin_now && !(ftn < tol || ftn == 0.0)) {  // mispredicted: linearise here
+          t0 = tbeg(h);
+          TCK(tusas::elem_run(tusas::M_RES_LIN, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t, h->st, old_init(h),
+                              old_ph(h)));
+          tend(h, TUSAS_T_RESIDUAL_LIN, t0);
+          S.residual_evals++;
+          rc = host_norm(h, h->Ft, &ftn);
+          if (rc) return rc;
+          if (!isfinite(ftn)) return fail(h, TUSAS_ENONFINITE, "non-finite residual norm in the line search");
+        }
         break;
       }
       lam *= 0.5;
