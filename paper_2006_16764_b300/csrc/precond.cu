@@ -307,6 +307,38 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __
   return s;
 }
 
+// The same sum over a vector given by a functor val(j) (j = node index within the block):
+// for the fused Chebyshev kernels, whose input vector is formed on the fly.
+template <int DIM, typename T, int R, typename V>
+__device__ __forceinline__ T stencil_apply_f(const T* __restrict__ st, const DevMesh& m, i64 node, int ix, int iy,
+                                             int iz, V val) {
+  constexpr int NS = Sten<DIM, R>::V, W = Sten<DIM, R>::W;
+  const i64 sy = m.nnx, sz = (i64)m.nnx * m.nny;
+  T s = T(0);
+  const bool interior = ix >= R && ix < m.nnx - R && iy >= R && iy < m.nny - R &&
+                        (DIM == 2 || (iz >= R && iz < m.nnz - R));
+  if (interior) {
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+      const int ox = o % W - R, oy = (o / W) % W - R, oz = DIM == 3 ? o / (W * W) - R : 0;
+      const i64 off = ox + sy * oy + sz * oz;
+      const T a = o < NS / 2 ? __ldg(st + (NS - 1 - o) * m.nn + node + off) : __ldg(st + o * m.nn + node);
+      s += a * val(node + off);
+    }
+  } else {
+#pragma unroll
+    for (int o = 0; o < NS; ++o) {
+      const int ox = o % W - R, oy = (o / W) % W - R, oz = DIM == 3 ? o / (W * W) - R : 0;
+      const int jx = ix + ox, jy = iy + oy, jz = iz + oz;
+      if (jx < 0 || jx >= m.nnx || jy < 0 || jy >= m.nny || jz < 0 || jz >= m.nnz) continue;
+      const i64 off = ox + sy * oy + sz * oz;
+      const T a = o < NS / 2 ? st[(NS - 1 - o) * m.nn + node + off] : st[o * m.nn + node];
+      s += a * val(node + off);
+    }
+  }
+  return s;
+}
+
 static dim3 block3(const DevMesh& m) { return m.dim == 3 ? dim3(32, 4, 2) : dim3(32, 8, 1); }
 static dim3 grid3(const DevMesh& m) {
   const dim3 b = block3(m);
@@ -506,6 +538,49 @@ __global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_resid(DevMesh m, con
   }
 }
 
+// Fused first Chebyshev step from x = 0 (the zero-x k_cheb_init followed by the first
+// k_cheb_step, same arithmetic): r0 = D^-1 b, d0 = a0 r0, x = d0, r = r0 - D^-1 A d0,
+// dout = c1 d0 + c2 r (requires degree >= 2, so the first step is not the last).
+template <int DIM, typename T, int R = 1>
+__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB)
+    k_cheb_first(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
+                 T* __restrict__ x, T* __restrict__ r, T* __restrict__ dout, Coef2<T> it, Coef2<T> c) {
+  constexpr int NS = Sten<DIM, R>::V;
+  int ix, iy, iz, blk;
+  i64 i;
+  if (!node3b(m, ix, iy, iz, i, blk)) return;
+  const i64 k = blk * m.nn + i;
+  const T a0 = blk ? it.a[1] : it.a[0];
+  const T* dv = dinv + blk * m.nn;
+  const T* bv = bvec + blk * m.nn;
+  const T r0 = dinv[k] * bvec[k];
+  const T dk = r0 * a0;
+  x[k] = dk;
+  const T ad = stencil_apply_f<DIM, T, R>(st + blk * NS * m.nn, m, i, ix, iy, iz,
+                                          [&](i64 j) { return (__ldg(dv + j) * __ldg(bv + j)) * a0; });
+  const T rr = r0 - dinv[k] * ad;
+  r[k] = rr;
+  dout[k] = (blk ? c.a[1] : c.a[0]) * dk + (blk ? c.b[1] : c.b[0]) * rr;
+}
+
+// Residual with the last Chebyshev update folded in: x' = x + p (p the pending
+// direction), res = b - A x', x' written to xout (a buffer other than x and p).
+template <int DIM, typename T, int R = 1>
+__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB)
+    k_resid_p(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
+              const T* __restrict__ p, T* __restrict__ xout, T* __restrict__ res) {
+  constexpr int NS = Sten<DIM, R>::V;
+  int ix, iy, iz, blk;
+  i64 i;
+  if (!node3b(m, ix, iy, iz, i, blk)) return;
+  const i64 k = blk * m.nn + i;
+  const T* xv = x + blk * m.nn;
+  const T* pv = p + blk * m.nn;
+  xout[k] = x[k] + p[k];
+  res[k] = bvec[k] - stencil_apply_f<DIM, T, R>(st + blk * NS * m.nn, m, i, ix, iy, iz,
+                                                [&](i64 j) { return __ldg(xv + j) + __ldg(pv + j); });
+}
+
 // b_c(I) = sum_i P(i, I) res(i) over the fine nodes within distance 1 of 2I
 template <int DIM, typename T>
 __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T* __restrict__ bc) {
@@ -530,9 +605,11 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
   }
 }
 
-// x_f(i) += sum_J P(i, J) x_c(J)
+// x_f(i) += sum_J P(i, J) (x_c(J) + p_c(J)); p_c: the coarse level's pending Chebyshev
+// direction, or null
 template <int DIM, typename T>
-__global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, T* __restrict__ xf) {
+__global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, const T* __restrict__ pc,
+                          T* __restrict__ xf) {
   {
     int fx, fy, fz;
     i64 i;
@@ -558,7 +635,8 @@ __global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, T* _
           }
         }
         if (!ok) continue;
-        s += w * xc[blk * mc.nn + J[0] + (i64)mc.nnx * (J[1] + (i64)mc.nny * J[2])];
+        const i64 Jn = blk * mc.nn + J[0] + (i64)mc.nnx * (J[1] + (i64)mc.nny * J[2]);
+        s += w * (pc ? xc[Jn] + pc[Jn] : xc[Jn]);
       }
       xf[blk * mf.nn + i] += s;
     }
@@ -569,9 +647,11 @@ template <typename T>
 __global__ void k_to_t(i64 n, const double* __restrict__ r, T* __restrict__ b) {
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) b[i] = (T)r[i];
 }
+// z = x (+ p, the pending Chebyshev direction, if not null), widened to FP64
 template <typename T>
-__global__ void k_from_t(i64 n, const T* __restrict__ x, double* __restrict__ z) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) z[i] = (double)x[i];
+__global__ void k_from_t(i64 n, const T* __restrict__ x, const T* __restrict__ p, double* __restrict__ z) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    z[i] = (double)(p ? x[i] + p[i] : x[i]);
 }
 template <typename T>
 __global__ void k_recip(i64 n, const double* __restrict__ d, T* __restrict__ dinv) {
@@ -799,40 +879,60 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
     it.a[b] = (T)(1.0 / theta[b]);
     it.b[b] = T(0);
   }
-  const bool d3 = L.m.dim == 3;
-  if (d3)
-    k_cheb_init<3, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
-                                                         zero_x, (T*)L.r_, (T*)L.d, it);
-  else if (L.r == 2)
-    k_cheb_init<2, T, 2><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b,
-                                                            (T*)L.x, zero_x, (T*)L.r_, (T*)L.d, it);
-  else
-    k_cheb_init<2, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (const T*)L.b, (T*)L.x,
-                                                         zero_x, (T*)L.r_, (T*)L.d, it);
-  count_launches(1);
-  T* dcur = (T*)L.d;
-  T* dnext = (T*)L.d2;
-  for (int kk = 0; kk < degree; ++kk) {
-    const int last = kk == degree - 1;
+  auto next_coef = [&]() {
     for (int b = 0; b < 2; ++b) {
       const double rn = 1.0 / (2.0 * sigma[b] - rho[b]);
       cc.a[b] = (T)(rn * rho[b]);
       cc.b[b] = (T)(2.0 * rn / delta[b]);
       rho[b] = rn;
     }
+  };
+  const bool d3 = L.m.dim == 3;
+  const dim3 g = grid3b(L.m), bl = block3(L.m);
+  const T *S = (const T*)L.st, *Di = (const T*)L.dinv, *B = (const T*)L.b;
+  T *X = (T*)L.x, *Rr = (T*)L.r_;
+  T* dcur = (T*)L.d;
+  T* dnext = (T*)L.d2;
+  L.pend = nullptr;
+  // FP32: fused first step and deferred last step; the FP64 variants of the fused kernels
+  // spill at the 32-register budget of the smoother kernels and ran 40 % slower
+  constexpr bool fuse = sizeof(T) == sizeof(float);
+  int k0 = 0;
+  if (fuse && zero_x && degree >= 2) {  // zero start: initialisation and first step in one pass
+    next_coef();
     if (d3)
-      k_cheb_step<3, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
-                                                           dcur, dnext, cc, last);
+      k_cheb_first<3, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
     else if (L.r == 2)
-      k_cheb_step<2, T, 2><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x,
-                                                              (T*)L.r_, dcur, dnext, cc, last);
+      k_cheb_first<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
     else
-      k_cheb_step<2, T><<<grid3b(L.m), block3(L.m), 0, st>>>(L.m, (const T*)L.st, (const T*)L.dinv, (T*)L.x, (T*)L.r_,
-                                                           dcur, dnext, cc, last);
+      k_cheb_first<2, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
     count_launches(1);
-    T* tmp = dcur;
-    dcur = dnext;
-    dnext = tmp;
+    std::swap(dcur, dnext);
+    k0 = 1;
+  } else {
+    if (d3)
+      k_cheb_init<3, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
+    else if (L.r == 2)
+      k_cheb_init<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
+    else
+      k_cheb_init<2, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
+    count_launches(1);
+  }
+  for (int kk = k0; kk < degree; ++kk) {
+    const int last = kk == degree - 1;
+    if (fuse && last) {  // the last step is x += d only: left to the next reader of x
+      L.pend = dcur;
+      break;
+    }
+    next_coef();
+    if (d3)
+      k_cheb_step<3, T><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
+    else if (L.r == 2)
+      k_cheb_step<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
+    else
+      k_cheb_step<2, T><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
+    count_launches(1);
+    std::swap(dcur, dnext);
   }
   return cudaGetLastError();
 }
@@ -846,38 +946,41 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   PrecondLevel& F = lv[l];
   PrecondLevel& C = lv[l + 1];
   const bool d3 = F.m.dim == 3;
-  if (d3) {
-    {
-      k_resid<3, T><<<grid3b(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
-      count_launches(1);
-    }
-    {
-      k_restrict<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
-      count_launches(1);
-    }
-  } else {
-    if (F.r == 2)
-      k_resid<2, T, 2><<<grid3b(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
+  const dim3 g = grid3b(F.m), bl = block3(F.m);
+  const T *S = (const T*)F.st, *B = (const T*)F.b;
+  if (F.pend) {  // residual of x + pending direction; the updated x goes to the free direction buffer
+    void** xo = F.pend == F.d ? &F.d2 : &F.d;
+    const T *X = (const T*)F.x, *P = (const T*)F.pend;
+    if (d3)
+      k_resid_p<3, T><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
+    else if (F.r == 2)
+      k_resid_p<2, T, 2><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
     else
-      k_resid<2, T><<<grid3b(F.m), block3(F.m), 0, st>>>(F.m, (const T*)F.st, (const T*)F.b, (const T*)F.x, (T*)F.res);
-    count_launches(1);
-    {
-      k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
-      count_launches(1);
-    }
+      k_resid_p<2, T><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
+    std::swap(F.x, *xo);
+    F.pend = nullptr;
+  } else {
+    if (d3)
+      k_resid<3, T><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
+    else if (F.r == 2)
+      k_resid<2, T, 2><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
+    else
+      k_resid<2, T><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
   }
+  count_launches(1);
+  if (d3)
+    k_restrict<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+  else
+    k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+  count_launches(1);
   e = vcycle<T>(l + 1, st);
   if (e != cudaSuccess) return e;
   if (d3)
-    {
-      k_prolong<3, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
-      count_launches(1);
-    }
+    k_prolong<3, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend, (T*)F.x);
   else
-    {
-      k_prolong<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (T*)F.x);
-      count_launches(1);
-    }
+    k_prolong<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend, (T*)F.x);
+  count_launches(1);
+  C.pend = nullptr;
   return cheb<T>(l, false, cheb_degree, st);
 }
 
@@ -899,9 +1002,10 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
   cudaError_t e = vcycle<T>(0, st);
   if (e != cudaSuccess) return e;
   {
-    k_from_t<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.x, z);
+    k_from_t<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.x, (const T*)L0.pend, z);
     count_launches(1);
   }
+  L0.pend = nullptr;
   return cudaGetLastError();
 }
 

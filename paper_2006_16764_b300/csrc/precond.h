@@ -17,6 +17,7 @@ struct PrecondLevel {
   void* d;     // Chebyshev direction (double buffered with d2)
   void* d2;
   void* res;   // unscaled residual for the restriction
+  void* pend;  // after a smoothing: the last Chebyshev direction, not yet added to x (or null)
   double lmax[2];
   int r;       // stencil radius: 1 (3^dim points), 2 on the Q2 node lattice (5 x 5)
 };
@@ -54,6 +55,8 @@ class Precond {
   cudaError_t galerkin_and_bounds(cudaStream_t st);
   template <typename T>
   cudaError_t vcycle(int l, cudaStream_t st);
+  // Chebyshev smoothing of level l; the last step's x += d is left to the next reader of
+  // x (residual, prolongation or the FP64 output), which adds lv[l].pend
   template <typename T>
   cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st);
 };
