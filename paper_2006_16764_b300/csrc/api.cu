@@ -724,10 +724,10 @@ int tusas_step(tusas_handle* h, tusas_stats* stats) {
     bool accepted = false;
     for (int ls = 0; ls <= p.linesearch_max; ++ls) {
       TCK(tusas::vxpay(N, h->U, lam, nullptr, h->dU, h->Ut, h->st));
-      // When the linear model ||F + J dU|| is well below the Newton tolerance the full step
-      // is expected to converge: evaluate F alone, and store the linearisation at the trial
+      // When the linear model ||F + J dU|| is below the Newton tolerance the full step is
+      // expected to converge: evaluate F alone, and store the linearisation at the trial
       // point only if the Newton loop goes on.
-      const bool lin_now = exact && !(ls == 0 && rlin <= 0.1 * tol);
+      const bool lin_now = exact && !(ls == 0 && rlin <= tol);
       t0 = tbeg(h);
       TCK(tusas::elem_run(lin_now ? tusas::M_RES_LIN : tusas::M_RES, h->ec, h->Ut, h->Un, nullptr, h->Ft, h->lin_t,
                           h->st, old_init(h), old_ph(h)));
