@@ -1,15 +1,18 @@
 #!/usr/bin/env python
-"""Benchmark of the B300 hot path: backward-Euler Newton-Krylov steps of the
-3D dilute-alloy phase-field problem (256x256x128 Q1 hexes, 17,040,642 dofs).
+"""Benchmark of the B300 hot path on the 3D dilute-alloy phase-field problem
+(256x256x128 Q1 hexes, 17,040,642 dofs).
 
-One bench step = one implicit time step through the whole hot path: residual
-F(U), pointwise linearisation, exact tangent J v, FP32 block-Jacobi / GMG
-preconditioner fill and apply, FGMRES(30) with CGS2, Newton update and line
-search. The metric counts residual-type operator evaluations (F and J v, each
-over all 17.04M dofs) per second of whole-job device time; the same line
-reports the FD-J v + FP64-preconditioner path for comparison (s/step), the
-isolated kernel roofline, the end-to-end number through the C-ABI with host
-buffers, and the CPU oracle on a bounded sample.
+The timed steps are backward-Euler Newton-Krylov time steps through the whole
+hot path: residual F(U), pointwise linearisation, exact tangent J v, FP32
+block-Jacobi / GMG preconditioner fill and apply, FGMRES(30) with CGS2,
+Newton update and line search (`ms_per_step`). The headline `value` is the
+metric's residual rate: isolated evaluations of F over all dofs per second
+(CUDA events, `steps` evaluations of the converged state). The same line
+reports the dominant kernel's roofline (FP64 pipe, and HBM against the
+nodal bytes), exact tangent + FP32 multigrid against FD J v + FP64 multigrid
+over the same steps (at the workload's GMRES cap and at 30), end-to-end
+numbers through the C-ABI with host buffers, and the CPU oracle on a bounded
+sample.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -41,11 +44,14 @@ CPU_SAMPLE = (48, 48, 32)
 # from the compiled kernels (DADD + DMUL + 2 DFMA per element: ncu
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over the 8
 # colour launches of one pass on the 256x192x64 alloy box / its elements).
-# Algorithmic bytes per element: nodal reads/writes (8 B per field value, one
-# node per element) plus the stored linearisation (23 coefficients x 8 Gauss
-# points x 8 B).
 FP64_FLOPS_PER_ELEM = {"residual": 1323.3, "residual_lin": 2163.3, "jv": 802.7}
-BYTES_PER_ELEM = {"residual": 48.0, "residual_lin": 48.0 + 1472.0, "jv": 32.0 + 1472.0}
+# Algorithmic HBM bytes per node of the method's operators: F reads U, U^n and
+# writes F (6 doubles); J v also reads v (8 doubles). Coordinates are implicit.
+ALG_BYTES_PER_NODE = {"residual": 48.0, "residual_lin": 48.0, "jv": 64.0}
+# The stored pointwise linearisation (23 coefficients x 8 Gauss points per
+# element) is this implementation's trade of HBM traffic for FP64 work; it is
+# reported beside the roofline, not counted as algorithmic bytes.
+LIN_BYTES_PER_ELEM = 23 * 8 * 8.0
 # DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
 # with the elements processed (same tiles, same per-element streams).
@@ -59,9 +65,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
-    ap.add_argument("--fd-steps", type=int, default=2)
+    ap.add_argument("--fd-steps", type=int, default=5,
+                    help="FD-JFNK + FP64 steps from the same start state as the first timed steps")
+    ap.add_argument("--cap30-steps", type=int, default=3,
+                    help="steps of both arms with one full GMRES(30) cycle per Newton iteration")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--cpu-seconds", type=float, default=18.0)
     ap.add_argument("--report", default=None, choices=synth.WORKLOADS + ["q2"],
                     help="run one workload's full protocol (step counts, precision / tangent comparisons, "
                          "adjoint gradients) and print a JSON summary; q2: biquadratic vs Q1 elements on "
@@ -339,9 +348,8 @@ def run_report(name):
         out["exact_vs_fd_solution_rel_inf"] = float((Uex - Ufd).abs().max() / Ufd.abs().max())
         out["exact_fp32_vs_fd_fp64_solution_rel_inf"] = float((Uex - Ufd64).abs().max() / Ufd64.abs().max())
     elif name == "adjoint2d_512":
-        from paper_2006_16764_b300.adjoint import SolidFraction, SolidFractionProblem, solid_fraction_weights
+        from paper_2006_16764_b300.adjoint import SolidFraction, SolidFractionProblem
 
-        wts, c = solid_fraction_weights(w.mesh)
         nn = w.mesh.n_nodes
         # tight Newton tolerance for the finite-difference check (1e-13 and 1e-12 are at the
         # FP64 roundoff floor of ||F|| at this size: ||F||/||F0|| stalls near 5e-13 on some steps)
@@ -351,7 +359,7 @@ def run_report(name):
             h, prm, lambda d: torch.tensor(synth.initial_state(
                 synth.Workload(w.name, w.mesh, dataclasses.replace(prm, Delta=d), w.dt, w.steps)), device=dev),
             torch.tensor(np.concatenate([np.zeros(nn), -np.ones(nn)]), device=dev),
-            torch.tensor(wts, device=dev), c, 0.0, w.dt, w.steps, 10, 1e-12)
+            0.0, w.dt, w.steps, 10, 1e-12)
         r = synth.uniform01(3, 16)
         samples = []
         for i in range(8):
@@ -375,7 +383,7 @@ def run_report(name):
         for _ in samples:
             s_ = torch.cuda.Stream(dev)
             probs.append(SolidFractionProblem(
-                pkg.Tusas(w.mesh, prm, stream=s_), prm, pb.initial_state, pb.dU0_ddelta, pb.w, c, 0.0, w.dt,
+                pkg.Tusas(w.mesh, prm, stream=s_), prm, pb.initial_state, pb.dU0_ddelta, 0.0, w.dt,
                 w.steps, 10, 1e-12, stream=s_))
         sam = [(x["eps4"], x["Delta"]) for x in samples]
         solid_fraction_batch(probs[:1], sam[:1])  # allocate the first handle's checkpoints outside the timing
@@ -408,7 +416,8 @@ def run_report(name):
 
 
 def cpu_oracle_rate(seconds, warm=0):
-    """Oracle residual evaluations on the bounded sample; Mdof-evals/s on 1 host core."""
+    """Oracle residual evaluations on the bounded sample on 1 host core: the median of the
+    per-evaluation times over about `seconds`, as Mdof-evals/s."""
     from oracle import residual as OR
 
     w = synth.scaled(synth.workload(WORKLOAD), *CPU_SAMPLE)
@@ -416,15 +425,15 @@ def cpu_oracle_rate(seconds, warm=0):
     U = U0 + 0.01 * synth.uniform_pm1(5, w.mesh.n_dofs)
     for _ in range(warm):
         OR.residual(w.mesh, w.params, U, U0, 0.0, w.dt)
-    n = 0
+    per = []
     t0 = time.perf_counter()
     while True:
+        t1 = time.perf_counter()
         OR.residual(w.mesh, w.params, U, U0, 0.0, w.dt)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds:
+        per.append(time.perf_counter() - t1)
+        if time.perf_counter() - t0 >= seconds:
             break
-    return w.mesh.n_dofs * n / el / 1e6, n, el, w
+    return w.mesh.n_dofs / statistics.median(per) / 1e6, len(per), sum(per), w
 
 
 # ---- the oracle on all host cores: element chunks in spawned worker processes ----------
@@ -477,18 +486,23 @@ class OraclePool:
             F += p
         return F
 
-    def rate(self, seconds, warm=1):
+    def rate(self, seconds, warm=2):
+        """Mdof-evals/s from the median per-evaluation time over about `seconds` (the host is
+        shared, so a median is steadier than a mean); also the evaluations and their spread."""
         for _ in range(warm):
             self.evaluate()
-        n = 0
+        per = []
         t0 = time.perf_counter()
         while True:
+            t1 = time.perf_counter()
             self.evaluate()
-            n += 1
-            el = time.perf_counter() - t0
-            if el >= seconds:
+            per.append(time.perf_counter() - t1)
+            if time.perf_counter() - t0 >= seconds:
                 break
-        return self.w.mesh.n_dofs * n / el / 1e6, n, el
+        per.sort()
+        q = lambda f: per[min(len(per) - 1, int(f * len(per)))]  # noqa: E731
+        return (self.w.mesh.n_dofs / statistics.median(per) / 1e6, len(per), sum(per),
+                {"min_s": per[0], "median_s": statistics.median(per), "p90_s": q(0.9)})
 
     def close(self):
         self.pool.close()
@@ -582,6 +596,25 @@ def allreduce_sum(ws, x, dev):
 
 
 # ----------------------------------------------------------------------------
+def bench_config(w, ws):
+    """The `config` object of both arms (the workload, its solver controls, L2 policy)."""
+    prm, mesh = w.params, w.mesh
+    return {"workload": w.name, "mesh": f"{mesh.nx}x{mesh.ny}x{mesh.nz} Q1 hex, h={mesh.h}", "dofs": mesh.n_dofs,
+            "dt": w.dt, "jvp": "exact (stored pointwise linearisation)",
+            "precond": f"block Jacobi, GMG V-cycle ({prm.mg_levels} levels), Chebyshev({prm.cheb_degree}), "
+                       f"{'FP32' if prm.smoother_fp32 else 'FP64'}",
+            "newton_rtol": prm.newton_rtol, "gmres_restart": prm.gmres_restart,
+            "gmres_maxit_per_newton": prm.gmres_maxit,
+            "l2": "inputs larger than L2 (state 136 MB per vector, linearisation 12.3 GB), no flush",
+            "parallelism": f"{ws} independent replica(s)"}
+
+
+VALUE_DEF = ("value: isolated residual F(U) (tusas_residual, Eqs. pf2/conc2 with the 2x2x2 Gauss rule) "
+             "over all dofs, evaluations x dofs / s, CUDA events over `steps` back-to-back evaluations "
+             "of a converged alloy state; ms_per_step: one backward-Euler Newton-Krylov time step "
+             "(exact tangent, FP32 multigrid), the timed region of `steps` steps")
+
+
 def run_reference(args, ws, rank):
     """The CPU oracle as it stands, on rank 0 only: residual evaluations on the bounded sample."""
     if rank != 0:
@@ -597,19 +630,62 @@ def run_reference(args, ws, rank):
             per.append(time.perf_counter() - t0)
     pool.close()
     secs = sum(per)
-    value = len(per) * w.mesh.n_dofs / secs / 1e6
+    # median per-evaluation time: the host is shared, a median is steadier than the mean
+    value = w.mesh.n_dofs / statistics.median(per) / 1e6
     sample = (f"oracle residual on the {CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-box of {WORKLOAD} "
-              f"({w.mesh.n_dofs} dofs), one evaluation per step, element chunks over {pool.procs} processes")
+              f"({w.mesh.n_dofs} dofs), one evaluation per step (median of {len(per)}), element chunks over "
+              f"{pool.procs} processes")
+    full = synth.workload(WORKLOAD)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "sample": list(CPU_SAMPLE)},
+            "config": bench_config(full, args.gpus), "value_def": "oracle residual rate on the sample (Mdof-evals/s)",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": pool.procs, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+def _hbm_peak():
+    """HBM copy bandwidth (GB/s) written by the GPU-pool driver, else the profiling fallback."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback 6.4 TB/s (no MEASURED_PEAKS.json)"
+
+
+def _steps_timed(h, n, stream):
+    """n Newton-Krylov steps with one CUDA-event pair per step on `stream`: (seconds per step, stats)."""
+    import torch
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+    st = []
+    ev[0].record(stream)
+    for i in range(n):
+        st.append(h.step(allow_noconv=True))
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    return [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(n)], st
+
+
+def _arm(pkg, mesh, prm, Ustart, t_start, dt, n, stream):
+    """n steps of one solver variant from (Ustart, t_start): per-step seconds, Newton/GMRES counts, timers."""
+    h = pkg.Tusas(mesh, prm, stream=stream)
+    h.set_state(Ustart, t_start, dt)
+    h.timers(True)
+    secs, st = _steps_timed(h, n, stream)
+    tm = h.get_timers()
+    h.close()
+    return {"s_per_step": secs, "mean_s_per_step": sum(secs) / n,
+            "newton_its": [s["newton_its"] for s in st], "gmres_its": [s["gmres_its"] for s in st],
+            "converged": all(s["converged"] for s in st),
+            "timers_ms": {k: round(v[0], 3) for k, v in tm.items()}}
+
+
 def run_ours(args, ws, rank, local):
+    import dataclasses
+
     import torch
 
     import paper_2006_16764_b300 as pkg
@@ -621,9 +697,12 @@ def run_ours(args, ws, rank, local):
     prm = w.params
     mesh = w.mesh
     N = mesh.n_dofs
+    ne = mesh.n_elems
+    nn = mesh.n_nodes
     U0 = torch.tensor(synth.initial_state(w), device=dev)
     stream = torch.cuda.current_stream(dev)
     fp64_peak, fp32_peak = pkg.fma_peak()
+    hbm_peak, hbm_kind = _hbm_peak()
     h = pkg.Tusas(mesh, prm, stream=stream)
     h.set_state(U0, 0.0, w.dt)
     for _ in range(args.warmup):
@@ -631,144 +710,173 @@ def run_ours(args, ws, rank, local):
     Ustart = torch.empty_like(U0)
     h.get_state(Ustart)
     t_start = h.time
+
+    # ---- timed region: `steps` implicit time steps (the whole hot path) ----
     h.timers(True)
     l0 = pkg.kernel_launches()
     clocks = ClockSampler(local)
     barrier(ws)
     torch.cuda.synchronize(dev)
     clocks.start()
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
     stats = []
-    for _ in range(args.steps):
+    for i in range(args.steps):
         stats.append(h.step())
-    e1.record(stream)
+        ev[i + 1].record(stream)
     torch.cuda.synchronize(dev)
     barrier(ws)
-    clk = clocks.stop()
-    launches = pkg.kernel_launches() - l0
-    ms = e0.elapsed_time(e1)
+    step_launches = pkg.kernel_launches() - l0
+    step_s = [ev[i].elapsed_time(ev[i + 1]) / 1e3 for i in range(args.steps)]
+    ms = ev[0].elapsed_time(ev[-1])
     ms_max = allreduce_max(ws, ms, dev)
     timers = h.get_timers()
-    evals = sum(s["residual_evals"] + s["jv_evals"] for s in stats)
-    units = allreduce_sum(ws, float(evals) * N, dev)
-    value = units / (ms_max * 1e-3) / 1e6
 
-    # dominant kernel class and its roofline (per operator application = one launch set)
-    dom = max(("residual", "residual_lin", "jv"), key=lambda k: timers[k][0])
-    d_ms, d_cnt = timers[dom]
-    per_launch = d_ms / max(d_cnt, 1)
-    ne = mesh.n_elems
-    flops = FP64_FLOPS_PER_ELEM[dom] * ne
-    achieved = flops / (per_launch * 1e-3) / 1e12
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
-            "frac": achieved * 1e12 / fp64_peak, "traffic": NCU_BYTES_PER_ELEM[dom] * ne,
-            "kernel": ("tan3_kernel (3D alloy tangent J v)" if dom == "jv" else f"res3_kernel {dom} (3D alloy)")
-            + ", one operator application = 8 colour launches",
-            "launch_ms": per_launch, "launches": d_cnt,
-            "peak_kind": "fp64 FMA-chain throughput measured in this run (tusas_fma_peak)",
-            "hbm": {"achieved_gbs": BYTES_PER_ELEM[dom] * ne / (per_launch * 1e-3) / 1e9,
-                    "peak_gbs": 6489.6, "peak_kind": "measured (MEASURED_PEAKS.json hbm_gbs)"}}
-    roof["hbm"]["frac"] = roof["hbm"]["achieved_gbs"] / roof["hbm"]["peak_gbs"]
-
-    # isolated residual kernel (CUDA events on the same stream)
-    F = torch.empty_like(U0)
+    # ---- the headline: isolated residual evaluations of the converged state ----
     Ut = torch.empty_like(U0)
     h.get_state(Ut)
-    for _ in range(2):
+    F = torch.empty_like(U0)
+    for _ in range(3):
         h.residual(Ut, F)
+    l1 = pkg.kernel_launches()
+    barrier(ws)
+    torch.cuda.synchronize(dev)
     r0 = torch.cuda.Event(enable_timing=True)
     r1 = torch.cuda.Event(enable_timing=True)
     r0.record(stream)
-    nres = 5
-    for _ in range(nres):
+    for _ in range(args.steps):
         h.residual(Ut, F)
     r1.record(stream)
     torch.cuda.synchronize(dev)
-    res_ms = r0.elapsed_time(r1) / nres
-    residual_kernel = {"ms": res_ms, "Mdof_evals_per_s": N / (res_ms * 1e-3) / 1e6,
-                       "fp64_tflops": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_ms * 1e-3) / 1e12,
-                       "hbm_gbs": BYTES_PER_ELEM["residual"] * ne / (res_ms * 1e-3) / 1e9}
-    del F
+    barrier(ws)
+    clk = clocks.stop()
+    res_launches = pkg.kernel_launches() - l1
+    res_ms = r0.elapsed_time(r1)
+    res_ms_max = allreduce_max(ws, res_ms, dev)
+    value = allreduce_sum(ws, float(args.steps) * N, dev) / (res_ms_max * 1e-3) / 1e6
+    res_per = res_ms / args.steps
+    residual_kernel = {
+        "ms": res_per, "Mdof_evals_per_s": N / (res_per * 1e-3) / 1e6,
+        "kernel": "res3_kernel<1,0> (3D alloy residual), one evaluation = 8 colour launches",
+        "fp64": {"achieved_tflops": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / 1e12,
+                 "peak_tflops": fp64_peak / 1e12,
+                 "frac": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / fp64_peak},
+        "hbm": {"algorithmic_bytes": ALG_BYTES_PER_NODE["residual"] * nn,
+                "achieved_gbs": ALG_BYTES_PER_NODE["residual"] * nn / (res_per * 1e-3) / 1e9,
+                "peak_gbs": hbm_peak, "peak_kind": hbm_kind},
+        "measured_dram_bytes": NCU_BYTES_PER_ELEM["residual"] * ne}
+    residual_kernel["hbm"]["frac"] = residual_kernel["hbm"]["achieved_gbs"] / hbm_peak
 
-    # FD-FP64 comparison path from the same starting state
+    # ---- dominant kernel of the time step and its roofline ----
+    dom = max(("residual", "residual_lin", "jv"), key=lambda k: timers[k][0])
+    d_ms, d_cnt = timers[dom]
+    per_launch = d_ms / max(d_cnt, 1)
+    flops = FP64_FLOPS_PER_ELEM[dom] * ne
+    achieved = flops / (per_launch * 1e-3) / 1e12
+    alg_bytes = ALG_BYTES_PER_NODE[dom] * nn
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
+            "frac": achieved * 1e12 / fp64_peak, "traffic": NCU_BYTES_PER_ELEM[dom] * ne,
+            "kernel": ("tan3_kernel<1,false> (3D alloy tangent J v)" if dom == "jv" else f"res3_kernel {dom} (3D alloy)")
+            + ", one operator application = 8 colour launches",
+            "launch_ms": per_launch, "launches": d_cnt,
+            "peak_kind": "FP64 FMA-chain throughput measured in this run (tusas_fma_peak)",
+            "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (per_launch * 1e-3) / 1e9,
+                    "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
+                    "basis": "nodal vectors only (48 B/node for F, 64 B/node for J v)"},
+            "design_lever": {"stored_linearisation_bytes": LIN_BYTES_PER_ELEM * ne,
+                             "what": "the pointwise Jacobian read by every exact J v (written once per Newton "
+                                     "iteration): HBM traffic traded for FP64 work, not algorithmic bytes",
+                             "measured_dram_bytes": NCU_BYTES_PER_ELEM[dom] * ne}}
+    roof["hbm"]["frac"] = roof["hbm"]["achieved_gbs"] / hbm_peak
+
+    # ---- exact + FP32 against FD + FP64 over the same steps, at the workload's cap and at 30 ----
     jfnk = {"exact_fp32": {"s_per_step": ms / args.steps / 1e3, "steps_per_s": args.steps * 1e3 / ms,
+                           "per_step_s": step_s,
                            "newton_its": [s["newton_its"] for s in stats],
                            "gmres_its": [s["gmres_its"] for s in stats],
+                           "operator_evals_Mdof_per_s": sum(s["residual_evals"] + s["jv_evals"] for s in stats)
+                           * N / (ms * 1e-3) / 1e6,
                            "kappa": 2 * w.dt * (prm.D / (1 + prm.k)) / mesh.h ** 2}}
-    if args.fd_steps > 0:
-        import dataclasses
-
+    nfd = min(args.fd_steps, args.steps)
+    if nfd > 0:
         pfd = dataclasses.replace(prm, jvp_mode=0, smoother_fp32=0)
-        hf = pkg.Tusas(mesh, pfd, stream=stream)
-        hf.set_state(Ustart, t_start, w.dt)
-        hf.timers(True)
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize(dev)
-        f0.record(stream)
-        fst = [hf.step() for _ in range(args.fd_steps)]
-        f1.record(stream)
-        torch.cuda.synchronize(dev)
-        fms = f0.elapsed_time(f1)
-        jfnk["fd_fp64"] = {"s_per_step": fms / args.fd_steps / 1e3,
-                           "newton_its": [s["newton_its"] for s in fst],
-                           "gmres_its": [s["gmres_its"] for s in fst],
-                           "timers_ms": {k: round(v[0], 3) for k, v in hf.get_timers().items()}}
-        # the exact path over the same first fd_steps steps
-        ex = stats[: args.fd_steps]
-        jfnk["speedup_exact_fp32_over_fd_fp64"] = jfnk["fd_fp64"]["s_per_step"] / jfnk["exact_fp32"]["s_per_step"]
-        hf.close()
+        fd = _arm(pkg, mesh, pfd, Ustart, t_start, w.dt, nfd, stream)
+        ex_win = step_s[:nfd]
+        jfnk["fd_fp64"] = fd
+        jfnk["same_window"] = {
+            "steps": nfd, "from": "the state after the warm-up steps (both arms)",
+            "exact_fp32_mean_s": sum(ex_win) / nfd, "fd_fp64_mean_s": fd["mean_s_per_step"],
+            "speedup_exact_fp32_over_fd_fp64": fd["mean_s_per_step"] / (sum(ex_win) / nfd)}
+    if args.cap30_steps > 0:
+        c30 = {}
+        for name, over in (("exact_fp32", dict(jvp_mode=1, smoother_fp32=1)),
+                           ("fd_fp64", dict(jvp_mode=0, smoother_fp32=0))):
+            c30[name] = _arm(pkg, mesh, dataclasses.replace(prm, gmres_maxit=30, **over), Ustart, t_start, w.dt,
+                             args.cap30_steps, stream)
+        c30["speedup_exact_fp32_over_fd_fp64"] = (c30["fd_fp64"]["mean_s_per_step"]
+                                                  / c30["exact_fp32"]["mean_s_per_step"])
+        c30["note"] = "gmres_maxit 30: one full GMRES(30) cycle per Newton iteration, same start state and steps"
+        jfnk["gmres_cap_30"] = c30
 
-    # end to end through the C-ABI with pinned host buffers (H2D state in, D2H state out per step)
+    # ---- end to end through the C-ABI with pinned host buffers ----
     e2e = None
     if args.e2e_steps > 0:
+        # the headline metric: H2D of U, residual, D2H of F per evaluation
         Uh = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        Uh.copy_(Ustart.cpu())
+        Fh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        Uh.copy_(Ut.cpu())
+        Ud = torch.empty_like(U0)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            Ud.copy_(Uh, non_blocking=True)
+            h.residual(Ud, F)
+            Fh.copy_(F, non_blocking=True)
+            torch.cuda.synchronize(dev)
+        el = time.perf_counter() - t0
+        e2e = {"value": args.steps * N / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+               "d2h_bytes_per_step": 8 * N, "steps": args.steps,
+               "what": "tusas_residual from pinned host U to pinned host F, host clock"}
+        # the time step end to end: state in, step, state out
+        Sh = torch.empty(N, dtype=torch.float64, pin_memory=True)
+        Sh.copy_(Ustart.cpu())
         torch.cuda.synchronize(dev)
         tt = t_start
-        ev = 0
         t0 = time.perf_counter()
         for _ in range(args.e2e_steps):
-            h.set_state(Uh, tt, w.dt)
-            s = h.step()
-            h.get_state(Uh)
+            h.set_state(Sh, tt, w.dt)
+            h.step()
+            h.get_state(Sh)
             tt += w.dt
-            ev += s["residual_evals"] + s["jv_evals"]
         el = time.perf_counter() - t0
-        e2e = {"value": ev * N / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N,
-               "steps": args.e2e_steps}
+        e2e["time_step"] = {"s_per_step": el / args.e2e_steps, "steps": args.e2e_steps,
+                            "h2d_bytes_per_step": 8 * N, "d2h_bytes_per_step": 8 * N}
 
     line = None
     if rank == 0:
-        cpu_rate, n, el, wsub = cpu_oracle_rate(args.cpu_seconds / 2, warm=1)
+        cpu_rate, n1, el1, wsub = cpu_oracle_rate(args.cpu_seconds / 3, warm=1)
         pool = OraclePool()
-        mc_rate, mc_n, mc_el = pool.rate(args.cpu_seconds / 2, warm=1)
+        mc_rate, mc_n, mc_el, spread = pool.rate(2 * args.cpu_seconds / 3)
         pool.close()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "mesh": f"{mesh.nx}x{mesh.ny}x{mesh.nz} Q1 hex, h={mesh.h}",
-                       "dofs": N, "dt": w.dt, "jvp": "exact (stored pointwise linearisation)",
-                       "precond": f"block Jacobi, GMG V-cycle ({prm.mg_levels} levels), "
-                                  f"Chebyshev({prm.cheb_degree}), {'FP32' if prm.smoother_fp32 else 'FP64'}",
-                       "newton_rtol": prm.newton_rtol, "gmres_restart": prm.gmres_restart,
-                       "gmres_maxit_per_newton": prm.gmres_maxit,
-                       "l2": "inputs larger than L2 (state 136 MB per vector, linearisation 12.3 GB)",
-                       "parallelism": f"{ws} independent replica(s)"},
+            "config": bench_config(w, ws),
+            "value_def": VALUE_DEF,
             "roofline": roof,
+            "residual_kernel": residual_kernel,
             "cpu_baseline": {"value": mc_rate, "unit": UNIT, "cores": pool.procs, "kind": "oracle",
-                             "sample": f"numpy oracle residual, {mc_n} evaluations in {mc_el:.1f} s on the "
-                                       f"{CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} sub-box ({wsub.mesh.n_dofs} dofs), "
-                                       f"element chunks over {pool.procs} spawned processes",
-                             "single_core": {"value": cpu_rate, "cores": 1, "evaluations": n, "seconds": el}},
+                             "sample": f"numpy oracle residual on the {CPU_SAMPLE[0]}x{CPU_SAMPLE[1]}x{CPU_SAMPLE[2]} "
+                                       f"sub-box ({wsub.mesh.n_dofs} dofs), median of {mc_n} evaluations "
+                                       f"({mc_el:.1f} s), element chunks over {pool.procs} spawned processes",
+                             "spread_s": spread,
+                             "single_core": {"value": cpu_rate, "cores": 1, "evaluations": n1, "seconds": el1}},
             "e2e": e2e,
-            "gpu_launches": launches,
+            "gpu_launches": step_launches + res_launches,
+            "gpu_launches_split": {"time_steps": step_launches, "residual_evals": res_launches},
             "clocks": clk,
             "jfnk": jfnk,
-            "residual_kernel": residual_kernel,
             "timers_ms": {k: [round(v[0], 3), v[1]] for k, v in timers.items()},
             "fp64_fma_peak_tflops": fp64_peak / 1e12, "fp32_fma_peak_tflops": fp32_peak / 1e12,
         }

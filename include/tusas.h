@@ -199,6 +199,17 @@ int tusas_forward(tusas_handle* h, const double* U0, double t0, double dt, int n
 int tusas_adjoint(tusas_handle* h, const double* w, const double* d0, double* grad_eps4, double* grad_dir,
                   double* g0, double adj_rtol, tusas_stats* stats);
 
+/* Solid fraction S = int (1 + phi_h)/2 over the box (no counterpart in the
+ * paper: the functional whose discrete adjoint gradient tusas_adjoint gives):
+ * S = w^T U + |Omega|/2 with w = [(1/2) int psi_i ; 0], the exact integral of
+ * the Q1 (or Q2, Simpson node weights) interpolant of phi. If U != NULL
+ * (device vector), *S (host) receives S and the call synchronises; if
+ * w != NULL (device vector of 2 N_nodes doubles, not aliasing U), it receives
+ * the weights, which are dS/dU and the right-hand side of the adjoint. The
+ * handle computes the weights once (one vector of device memory).
+ * TUSAS_EINVAL if both U and w are NULL, or U is given without S. */
+int tusas_solid_fraction(tusas_handle* h, const double* U, double* S, double* w);
+
 /* Deterministic FP64 dot product x . y of n doubles (device vectors); the
  * result is written to *result (host pointer). Synchronises. */
 int tusas_dot(tusas_handle* h, const double* x, const double* y, long long n, double* result);
@@ -240,7 +251,10 @@ int tusas_fma_peak(double* fp64_flops, double* fp32_flops);
  * (TUSAS_NOALLOC_MAX_K x 296 + TUSAS_NOALLOC_MAX_K doubles, about 76 KB per
  * GPU, held until the process exits); nothing is allocated or freed. The
  * first call on a device looks up that array's address (cudaGetSymbolAddress
- * with the device current); make that first call before any stream capture.
+ * with the device current) and keeps it for the process; make that first call
+ * before any stream capture. A cudaDeviceReset of that device reloads the
+ * library's module and makes the kept address stale: do not call this entry
+ * point on a device after resetting it.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller. Works on `stream` (a cudaStream_t, NULL = legacy
  * default) and synchronises it. Returns TUSAS_EINVAL for k < 1,
@@ -249,6 +263,18 @@ int tusas_fma_peak(double* fp64_flops, double* fp32_flops);
 #define TUSAS_NOALLOC_MAX_K 32
 int tusas_multidot_noalloc(const double* X, long long ld, int k, const double* y, long long n, double* out,
                            void* stream);
+
+/* ---- Device memory accounting (no counterpart in the paper) --------------
+ * The library counts the device bytes its handles hold (state vectors, Krylov
+ * basis, linearisation store, multigrid hierarchy, checkpoints; not the
+ * fixed array of tusas_multidot_noalloc). With a cap set (bytes > 0) an
+ * allocation that would pass it fails as if the device were full: the call
+ * returns TUSAS_ENOMEM and frees what it had allocated. tusas_create checks
+ * its vectors and Krylov basis against the cap before any CUDA call. 0
+ * removes the cap (the default); TUSAS_EINVAL for bytes < 0. Process-wide. */
+int tusas_set_device_bytes_cap(long long bytes);
+/* Device bytes held by the library's handles at this moment. */
+long long tusas_device_bytes(void);
 
 /* Description of the last error on this handle (never NULL). */
 const char* tusas_last_error(const tusas_handle* h);

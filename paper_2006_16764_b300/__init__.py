@@ -22,7 +22,8 @@ EXPORTS = ["tusas_create", "tusas_destroy", "tusas_set_stream", "tusas_set_param
            "tusas_set_state", "tusas_set_history", "tusas_get_state", "tusas_time", "tusas_residual", "tusas_jvp",
            "tusas_jvp_fd", "tusas_jtvp", "tusas_jtvp_prev", "tusas_dFdp", "tusas_precond_setup",
            "tusas_precond_apply", "tusas_step", "tusas_dot", "tusas_last_error", "tusas_timers",
-           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak", "tusas_forward", "tusas_adjoint", "tusas_multidot_noalloc"]
+           "tusas_get_timers", "tusas_kernel_launches", "tusas_fma_peak", "tusas_forward", "tusas_adjoint", "tusas_solid_fraction",
+           "tusas_set_device_bytes_cap", "tusas_device_bytes", "tusas_multidot_noalloc"]
 
 TIMER_NAMES = ["residual", "residual_lin", "jv", "adjoint", "pc_apply", "pc_setup", "ortho"]
 
@@ -102,6 +103,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
         "tusas_adjoint": ([vp, dp, dp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), dp,
                            ctypes.c_double, ctypes.POINTER(CStats)], ctypes.c_int),
         "tusas_fma_peak": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "tusas_solid_fraction": ([vp, dp, ctypes.POINTER(ctypes.c_double), dp], ctypes.c_int),
+        "tusas_set_device_bytes_cap": ([i64], ctypes.c_int),
+        "tusas_device_bytes": ([], i64),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -132,6 +136,19 @@ def fma_peak():
     if rc != OK:
         raise TusasError(rc, "tusas_fma_peak failed")
     return a.value, b.value
+
+
+def set_device_bytes_cap(nbytes: int):
+    """Cap the device bytes the library's handles may hold (0: no cap); past it allocations fail
+    with TUSAS_ENOMEM as on a full device."""
+    rc = lib().tusas_set_device_bytes_cap(int(nbytes))
+    if rc != OK:
+        raise TusasError(rc, "tusas_set_device_bytes_cap failed")
+
+
+def device_bytes() -> int:
+    """Device bytes held by the library's handles."""
+    return int(lib().tusas_device_bytes())
 
 
 NOALLOC_MAX_K = 32
@@ -293,6 +310,17 @@ class Tusas:
         self._check(self._lib.tusas_adjoint(self._h, _ptr(w), _ptr(d0), ctypes.byref(ge), ctypes.byref(gd),
                                             _ptr(g0), float(rtol), ctypes.byref(st)))
         return ge.value, gd.value, st.as_dict()
+
+    def solid_fraction(self, U):
+        """S = int (1 + phi_h)/2 of the device state U (tusas_solid_fraction)."""
+        S = ctypes.c_double()
+        self._check(self._lib.tusas_solid_fraction(self._h, _ptr(U), ctypes.byref(S), None))
+        return S.value
+
+    def solid_fraction_weights(self, out):
+        """Write dS/dU = [(1/2) int psi_i ; 0] into the device vector ``out``."""
+        self._check(self._lib.tusas_solid_fraction(self._h, None, None, _ptr(out)))
+        return out
 
     def timers(self, enable=True):
         self._check(self._lib.tusas_timers(self._h, int(enable)))

@@ -1,47 +1,24 @@
 """Discrete-adjoint gradients of the final solid fraction behind a torch.autograd.Function.
 
 S(eps4, Delta) = int (1 + phi_N)/2 after N backward-Euler steps. The forward
-sweep (tusas_forward) records checkpoints; backward (tusas_adjoint) solves the
-transposed linearised steps in reverse with the library's J^T w kernels and
-contracts with dF/d eps4 and with dU_0/dDelta. Only argument marshalling here.
+sweep (tusas_forward) records checkpoints; S and its weights dS/dU_N come from
+tusas_solid_fraction; backward (tusas_adjoint) solves the transposed
+linearised steps in reverse with the library's J^T w kernels and contracts
+with dF/d eps4 and with dU_0/dDelta. Only argument marshalling here.
 """
 from __future__ import annotations
 
 import dataclasses
 
-import numpy as np
 import torch
-
-
-def solid_fraction_weights(mesh):
-    """(w, c) with int (1 + phi_h)/2 = w^T U + c: w is half the integral of each phi basis
-    function, zero on the u block; c = |Omega|/2. Basis integrals are products of 1D
-    node weights: h inside and h/2 at the ends for Q1; for Q2 (order 2) the Simpson
-    weights h/3 at shared vertices, 2h/3 at midpoints, h/6 at the ends."""
-    order = int(getattr(mesh, "order", 1))
-    ne = [mesh.nx, mesh.ny] + ([mesh.nz] if mesh.dim == 3 else [])
-    m = None
-    for n in ne:
-        if order == 2:
-            a = np.empty(2 * n + 1)
-            a[1::2] = 2.0 * mesh.h / 3.0
-            a[0::2] = mesh.h / 3.0
-            a[0] = a[-1] = mesh.h / 6.0
-        else:
-            a = np.full(n + 1, mesh.h)
-            a[0] = a[-1] = 0.5 * mesh.h
-        m = a if m is None else np.kron(a, m)
-    nodes = m.size
-    vol = float(np.prod([mesh.h * n for n in ne]))
-    return np.concatenate([0.5 * m, np.zeros(nodes)]), 0.5 * vol
 
 
 class SolidFraction(torch.autograd.Function):
     """S = SolidFraction.apply(eps4, Delta, problem); eps4 and Delta are 0-d float64 tensors.
 
     ``problem`` holds the handle, base parameters, the initial state as a
-    function of Delta (device tensor), dU_0/dDelta (device tensor), the
-    weights w (device tensor) and constant c, t0, dt, nsteps, ckpt_every.
+    function of Delta (device tensor), dU_0/dDelta (device tensor), t0, dt,
+    nsteps, ckpt_every.
     """
 
     @staticmethod
@@ -53,14 +30,14 @@ class SolidFraction(torch.autograd.Function):
         pb.last_forward = pb.handle.forward(U0, pb.t0, pb.dt, pb.nsteps, pb.ckpt_every)
         UN = torch.empty_like(U0)
         pb.handle.get_state(UN)
-        S = pb.handle.dot(pb.w, UN) + pb.c
+        S = pb.handle.solid_fraction(UN)
         ctx.problem = pb
         return torch.tensor(S, dtype=torch.float64)
 
     @staticmethod
     def backward(ctx, gS):
         pb = ctx.problem
-        ge, gd, st = pb.handle.adjoint(pb.w, pb.dU0_ddelta, rtol=pb.adj_rtol)
+        ge, gd, st = pb.handle.adjoint(pb.weights(), pb.dU0_ddelta, rtol=pb.adj_rtol)
         pb.last_adjoint = st
         g = gS.detach().to(torch.float64).cpu()
         return g * ge, g * gd, None
@@ -72,8 +49,6 @@ class SolidFractionProblem:
     params: object
     initial_state: object  # Delta -> device tensor U_0
     dU0_ddelta: torch.Tensor
-    w: torch.Tensor
-    c: float
     t0: float
     dt: float
     nsteps: int
@@ -82,6 +57,12 @@ class SolidFractionProblem:
     last_forward: dict = None
     last_adjoint: dict = None
     stream: object = None  # the handle's torch.cuda.Stream (solid_fraction_batch)
+    w: torch.Tensor = None  # dS/dU_N from the library, filled on first use
+
+    def weights(self):
+        if self.w is None:
+            self.w = self.handle.solid_fraction_weights(torch.empty_like(self.dU0_ddelta))
+        return self.w
 
 
 def solid_fraction_batch(problems, samples):
@@ -107,8 +88,8 @@ def solid_fraction_batch(problems, samples):
             fw = pb.handle.forward(U0, pb.t0, pb.dt, pb.nsteps, pb.ckpt_every)
             UN = torch.empty_like(U0)
             pb.handle.get_state(UN)
-            S = pb.handle.dot(pb.w, UN) + pb.c
-            ge, gd, st = pb.handle.adjoint(pb.w, pb.dU0_ddelta, rtol=pb.adj_rtol)
+            S = pb.handle.solid_fraction(UN)
+            ge, gd, st = pb.handle.adjoint(pb.weights(), pb.dU0_ddelta, rtol=pb.adj_rtol)
         return {"eps4": e4, "Delta": dl, "S": S, "dS_deps4": ge, "dS_dDelta": gd, "forward": fw, "adjoint": st}
 
     with ThreadPoolExecutor(max_workers=len(problems)) as ex:

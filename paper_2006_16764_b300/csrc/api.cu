@@ -55,6 +55,8 @@ struct tusas_handle {
   // nodal (phi^n - phi^{n-1})/dt of the Eq. (theta) estimate
   double *Unm1 = nullptr, *Fold = nullptr, *phold = nullptr;
   bool old_valid = false;
+  // weights of the solid fraction S = w^T U + |Omega|/2 (filled on first use)
+  double* sfw = nullptr;
 };
 
 namespace {
@@ -213,9 +215,11 @@ const double* old_ph(tusas_handle* h) { return h->ec.P.phihat_old ? h->phold : n
 int ensure_lin(tusas_handle* h, bool trial) {
   if (!h->lin) {
     h->lin_n = tusas::elem_lin_doubles(h->ec);
-    TCK(cudaMalloc(&h->lin, sizeof(double) * h->lin_n));
+    if (tusas::dev_malloc(&h->lin, sizeof(double) * h->lin_n) != cudaSuccess)
+      return fail(h, TUSAS_ENOMEM, "linearisation store allocation");
   }
-  if (trial && !h->lin_t) TCK(cudaMalloc(&h->lin_t, sizeof(double) * h->lin_n));
+  if (trial && !h->lin_t && tusas::dev_malloc(&h->lin_t, sizeof(double) * h->lin_n) != cudaSuccess)
+    return fail(h, TUSAS_ENOMEM, "trial linearisation store allocation");
   return TUSAS_OK;
 }
 
@@ -272,6 +276,13 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   std::string why;
   int rc = validate(mesh, params, why);
   if (rc) return rc;
+  {
+    // admission against the device-bytes cap before any CUDA call: the vectors and the Krylov basis
+    const int po = mesh->order == 2 ? 2 : 1;
+    const long long nn = (long long)(po * mesh->nx + 1) * (po * mesh->ny + 1) * (mesh->dim == 3 ? mesh->nz + 1 : 1);
+    const long long base = (long long)sizeof(double) * 2 * nn * (11 + 2 * params->gmres_restart + 1);
+    if (!tusas::dev_bytes_admit(base)) return TUSAS_ENOMEM;
+  }
   tusas_handle* h = new tusas_handle();
   h->mesh = *mesh;
   h->prm = *params;
@@ -296,17 +307,17 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   fill_phys(h);
   double** vecs[] = {&h->Un, &h->U, &h->F, &h->Ft, &h->dU, &h->Ut, &h->tmp, &h->tmp2, &h->Unm1, &h->Fold, &h->phold};
   for (double** v : vecs) {
-    cudaError_t e = cudaMalloc(v, sizeof(double) * h->N);
+    cudaError_t e = tusas::dev_malloc(v, sizeof(double) * h->N);
     if (e != cudaSuccess) {
       tusas_destroy(h);
       return TUSAS_ENOMEM;
     }
   }
   h->m = params->gmres_restart;
-  if (cudaMalloc(&h->V, sizeof(double) * h->N * (h->m + 1)) != cudaSuccess ||
-      cudaMalloc(&h->Z, sizeof(double) * h->N * h->m) != cudaSuccess ||
-      cudaMalloc(&h->partials, sizeof(double) * tusas::reduce_blocks() * 32) != cudaSuccess ||
-      cudaMalloc(&h->sc, sizeof(double) * 256) != cudaSuccess) {
+  if (tusas::dev_malloc(&h->V, sizeof(double) * h->N * (h->m + 1)) != cudaSuccess ||
+      tusas::dev_malloc(&h->Z, sizeof(double) * h->N * h->m) != cudaSuccess ||
+      tusas::dev_malloc(&h->partials, sizeof(double) * tusas::reduce_blocks() * 32) != cudaSuccess ||
+      tusas::dev_malloc(&h->sc, sizeof(double) * 256) != cudaSuccess) {
     tusas_destroy(h);
     return TUSAS_ENOMEM;
   }
@@ -328,14 +339,14 @@ void tusas_destroy(tusas_handle* h) {
   cudaDeviceSynchronize();
   double* vecs[] = {h->Un, h->U, h->F, h->Ft, h->dU, h->Ut, h->tmp, h->tmp2, h->lin, h->lin_t, h->V, h->Z,
                     h->partials, h->sc, h->Unm1, h->Fold, h->phold};
-  for (double* v : vecs)
-    if (v) cudaFree(v);
+  for (double* v : vecs) tusas::dev_free(v);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-  for (double* p : h->ckpt) cudaFree(p);
-  for (double* p : h->seg) cudaFree(p);
-  if (h->lam) cudaFree(h->lam);
-  if (h->lam_rhs) cudaFree(h->lam_rhs);
-  if (h->Ufinal) cudaFree(h->Ufinal);
+  for (double* p : h->ckpt) tusas::dev_free(p);
+  for (double* p : h->seg) tusas::dev_free(p);
+  tusas::dev_free(h->lam);
+  tusas::dev_free(h->lam_rhs);
+  tusas::dev_free(h->Ufinal);
+  tusas::dev_free(h->sfw);
   h->pc.destroy();
   delete h;
 }
@@ -787,13 +798,13 @@ namespace {
 int grow(tusas_handle* h, std::vector<double*>& v, size_t n) {
   while (v.size() < n) {
     double* p = nullptr;
-    if (cudaMalloc(&p, sizeof(double) * h->N) != cudaSuccess) return fail(h, TUSAS_ENOMEM, "checkpoint allocation");
+    if (tusas::dev_malloc(&p, sizeof(double) * h->N) != cudaSuccess) return fail(h, TUSAS_ENOMEM, "checkpoint allocation");
     v.push_back(p);
   }
   return TUSAS_OK;
 }
 int ensure_vec(tusas_handle* h, double** p) {
-  if (!*p && cudaMalloc(p, sizeof(double) * h->N) != cudaSuccess) return fail(h, TUSAS_ENOMEM, "vector allocation");
+  if (!*p && tusas::dev_malloc(p, sizeof(double) * h->N) != cudaSuccess) return fail(h, TUSAS_ENOMEM, "vector allocation");
   return TUSAS_OK;
 }
 int set_state_dev(tusas_handle* h, const double* U, double t) {
@@ -955,5 +966,57 @@ extern "C" int tusas_adjoint(tusas_handle* h, const double* w, const double* d0,
   TCK(cudaStreamSynchronize(h->st));
   *grad_eps4 = geps;
   if (stats) *stats = S;
+  return TUSAS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Solid fraction S = int (1 + phi_h)/2, the functional of the discrete adjoint
+// ---------------------------------------------------------------------------
+namespace {
+// Integral of the 1D nodal basis function of node i among nnodes: Q1 h (h/2 at
+// the two ends); Q2 h/3 at shared element vertices, 2h/3 at midpoints, h/6 at the ends.
+__device__ __forceinline__ double sf_weight_1d(int i, int nnodes, int order, double h) {
+  if (order == 2) {
+    if (i & 1) return 2.0 * h / 3.0;
+    return (i == 0 || i == nnodes - 1) ? h / 6.0 : h / 3.0;
+  }
+  return (i == 0 || i == nnodes - 1) ? 0.5 * h : h;
+}
+
+// w = [ (1/2) int psi_node ; 0 ]: S = w^T U + |Omega|/2 (products of 1D integrals on the box)
+__global__ void k_sf_weights(tusas::DevMesh m, double* __restrict__ w) {
+  for (i64 n = blockIdx.x * (i64)blockDim.x + threadIdx.x; n < m.nn; n += (i64)gridDim.x * blockDim.x) {
+    const int i = (int)(n % m.nnx);
+    const i64 r = n / m.nnx;
+    const int j = (int)(r % m.nny), k = (int)(r / m.nny);
+    double v = 0.5 * sf_weight_1d(i, m.nnx, m.order, m.h) * sf_weight_1d(j, m.nny, m.order, m.h);
+    if (m.dim == 3) v *= sf_weight_1d(k, m.nnz, m.order, m.h);
+    w[n] = v;
+    w[m.nn + n] = 0.0;
+  }
+}
+}  // namespace
+
+extern "C" int tusas_solid_fraction(tusas_handle* h, const double* U, double* S, double* w) {
+  if (!h) return TUSAS_EINVAL;
+  if ((U && !S) || (!U && !w) || (w && w == U)) return fail(h, TUSAS_EINVAL, "bad solid-fraction arguments");
+  if (!h->sfw) {
+    int rc = ensure_vec(h, &h->sfw);
+    if (rc) return rc;
+    const i64 nb = std::min<i64>((h->nn + 255) / 256, 148 * 16);
+    k_sf_weights<<<(int)nb, 256, 0, h->st>>>(h->dm, h->sfw);
+    tusas::count_launches(1);
+    TCK(cudaGetLastError());
+  }
+  if (w) TCK(tusas::vcopy(h->N, h->sfw, w, h->st));
+  if (U) {
+    TCK(tusas::multidot(h->nn, 1, h->sfw, 0, U, h->partials, h->sc + 200, h->st));
+    double v;
+    TCK(cudaMemcpyAsync(&v, h->sc + 200, sizeof(double), cudaMemcpyDeviceToHost, h->st));
+    TCK(cudaStreamSynchronize(h->st));
+    const tusas::DevMesh& m = h->dm;
+    const double vol = m.h * m.nx * m.h * m.ny * (m.dim == 3 ? m.h * m.nz : 1.0);
+    *S = v + 0.5 * vol;
+  }
   return TUSAS_OK;
 }

@@ -32,7 +32,8 @@ std::mutex g_mu;
 double* g_ptr[kMaxDevices] = {nullptr};
 
 // Device address of the scratch array for the current device; looked up once
-// per device (cudaGetSymbolAddress with that device current).
+// per device (cudaGetSymbolAddress with that device current) and kept for the
+// process, so it goes stale if the device is reset (callers must not reset).
 int scratch_for_current_device(double** out) {
   int dev = -1;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return TUSAS_ECUDA;

@@ -11,6 +11,17 @@ namespace tusas {
 void count_launches(long long n);
 long long launches();
 
+// Device allocations of the handles, counted against the cap of
+// tusas_set_device_bytes_cap (cudaErrorMemoryAllocation past it, without
+// calling cudaMalloc). dev_bytes_admit: whether `bytes` more would fit.
+cudaError_t dev_malloc(void** p, size_t bytes);
+void dev_free(void* p);
+bool dev_bytes_admit(long long bytes);
+template <typename T>
+inline cudaError_t dev_malloc(T** p, size_t bytes) {
+  return dev_malloc(reinterpret_cast<void**>(p), bytes);
+}
+
 // M_DIAG (Q2 only): the diagonals of the preconditioner blocks M11, M22.
 enum ElemMode { M_RES = 0, M_RES_LIN = 1, M_JV = 2, M_JTV = 3, M_DEPS = 4, M_PREV_T = 5, M_OLD = 6, M_DIAG = 7 };
 

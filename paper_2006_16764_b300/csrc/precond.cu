@@ -699,11 +699,11 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
     PrecondLevel L = {};
     L.m = m;
     L.nn = m.nn;
-    cudaError_t e = cudaMalloc(&L.dinv, esz * 2 * m.nn);
+    cudaError_t e = dev_malloc(&L.dinv, esz * 2 * m.nn);
     if (e != cudaSuccess) return e;
-    lv.push_back(L);
+    lv.push_back(L);  // destroy() frees what was allocated
     bytes += (esz + sizeof(double)) * 2 * m.nn;
-    return cudaMalloc(&diag, sizeof(double) * 2 * m.nn);
+    return dev_malloc(&diag, sizeof(double) * 2 * m.nn);
   }
   const int nlev = kind == 1 ? 1 : (levels < 1 ? 1 : levels);
   // Q2 (2D): the finest level is the node lattice of spacing h/2 with 25-point stencils; its
@@ -721,35 +721,36 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
     L.nn = cur.nn;
     L.r = (l == 0 && m.order == 2) ? 2 : 1;
     const int NS = L.r == 2 ? 25 : (m.dim == 3 ? 27 : 9);
-    void** bufs[] = {&L.dinv, &L.b, &L.x, &L.r_, &L.d, &L.d2, &L.res};
-    cudaError_t e = cudaMalloc(&L.st, esz * 2 * NS * cur.nn);
+    lv.push_back(L);  // allocated in place: destroy() frees a partly allocated level too
+    PrecondLevel& Lb = lv.back();
+    void** bufs[] = {&Lb.dinv, &Lb.b, &Lb.x, &Lb.r_, &Lb.d, &Lb.d2, &Lb.res};
+    cudaError_t e = dev_malloc(&Lb.st, esz * 2 * NS * cur.nn);
     if (e != cudaSuccess) return e;
     bytes += esz * 2 * NS * cur.nn;
     const int nvec = kind == 1 ? 1 : 7;
     for (int v = 0; v < nvec; ++v) {
-      e = cudaMalloc(bufs[v], esz * 2 * cur.nn);
+      e = dev_malloc(bufs[v], esz * 2 * cur.nn);
       if (e != cudaSuccess) return e;
       bytes += esz * 2 * cur.nn;
     }
-    lv.push_back(L);
     if (!can_coarsen(cur)) break;
     cur = coarsen(cur);
   }
-  cudaError_t e = cudaMalloc(&gersh_partials, sizeof(double) * 2 * 148 * 32);
+  cudaError_t e = dev_malloc(&gersh_partials, sizeof(double) * 2 * 148 * 32);
   if (e != cudaSuccess) return e;
-  return cudaMalloc(&lmax_dev, sizeof(double) * 2 * lv.size());
+  return dev_malloc(&lmax_dev, sizeof(double) * 2 * lv.size());
 }
 
 void Precond::destroy() {
   for (auto& L : lv) {
     void* bufs[] = {L.st, L.dinv, L.b, L.x, L.r_, L.d, L.d2, L.res};
     for (void* p : bufs)
-      if (p) cudaFree(p);
+      if (p) dev_free(p);
   }
   lv.clear();
-  if (gersh_partials) cudaFree(gersh_partials);
-  if (lmax_dev) cudaFree(lmax_dev);
-  if (diag) cudaFree(diag);
+  dev_free(gersh_partials);
+  dev_free(lmax_dev);
+  dev_free(diag);
   gersh_partials = lmax_dev = diag = nullptr;
 }
 

@@ -79,3 +79,26 @@ def test_mesh_validation_rejects_bad_orders_before_gpu_work():
         cm, cp = pkg.make_mesh(mesh), pkg.make_params(prm)
         assert lib.tusas_create(ctypes.byref(cm), ctypes.byref(cp), ctypes.byref(h)) == pkg.EINVAL
         assert not h.value
+
+
+def test_device_bytes_cap_gives_enomem_before_gpu_work():
+    """An allocation failure simulated by a size cap: tusas_create checks its vectors and
+    Krylov basis against the cap before any CUDA call and returns TUSAS_ENOMEM."""
+    import ctypes
+
+    import paper_2006_16764_b300 as pkg
+    from synth import Mesh, Params
+
+    lib = pkg.lib()
+    h = ctypes.c_void_p()
+    mesh = Mesh(3, 32, 32, 32, 1.0)
+    need = 8 * mesh.n_dofs * (11 + 2 * 30 + 1)  # vectors + GMRES(30) basis
+    cm, cp = pkg.make_mesh(mesh), pkg.make_params(Params(precond=2))
+    assert lib.tusas_set_device_bytes_cap(-1) == pkg.EINVAL
+    try:
+        pkg.set_device_bytes_cap(need - 8)
+        assert lib.tusas_create(ctypes.byref(cm), ctypes.byref(cp), ctypes.byref(h)) == pkg.ENOMEM
+        assert not h.value
+        assert pkg.device_bytes() == 0
+    finally:
+        pkg.set_device_bytes_cap(0)

@@ -77,16 +77,13 @@ def test_checkpoint_spacing_does_not_change_the_gradient():
 def test_autograd_function_matches_central_differences():
     import torch
 
-    from paper_2006_16764_b300.adjoint import SolidFraction, SolidFractionProblem, solid_fraction_weights
+    from paper_2006_16764_b300.adjoint import SolidFraction, SolidFractionProblem
 
     mesh, prm, U0f, dt, n = _problem("alloy")
-    w, c = solid_fraction_weights(mesh)
-    wo, co = OA.solid_fraction_weights(mesh)
-    assert np.abs(w - wo).max() < 1e-15 and abs(c - co) < 1e-12
     h = handle(mesh, prm)
     nn = mesh.n_nodes
     pb = SolidFractionProblem(h, prm, lambda d: dev(U0f(dataclasses.replace(prm, Delta=d))),
-                              dev(np.concatenate([np.zeros(nn), -np.ones(nn)])), dev(w), c, 0.0, dt, n, 1, 1e-12)
+                              dev(np.concatenate([np.zeros(nn), -np.ones(nn)])), 0.0, dt, n, 1, 1e-12)
     eps = torch.tensor(prm.eps4, dtype=torch.float64, requires_grad=True)
     dl = torch.tensor(prm.Delta, dtype=torch.float64, requires_grad=True)
     S = SolidFraction.apply(eps, dl, pb)
@@ -108,19 +105,18 @@ def test_concurrent_samples_match_sequential_bitwise():
     import torch
 
     import paper_2006_16764_b300 as pkg
-    from paper_2006_16764_b300.adjoint import SolidFractionProblem, solid_fraction_batch, solid_fraction_weights
+    from paper_2006_16764_b300.adjoint import SolidFractionProblem, solid_fraction_batch
 
     mesh, prm, U0f, dt, n = _problem("alloy")
-    w, c = solid_fraction_weights(mesh)
+    w, _ = OA.solid_fraction_weights(mesh)
     nn = mesh.n_nodes
     d0 = dev(np.concatenate([np.zeros(nn), -np.ones(nn)]))
-    tw = dev(w)
     init = lambda d: dev(U0f(dataclasses.replace(prm, Delta=d)))
     samples = [(0.03, 0.5), (0.045, 0.42), (0.02, 0.61)]
     probs = []
     for _ in samples:
         s = torch.cuda.Stream()
-        probs.append(SolidFractionProblem(pkg.Tusas(mesh, prm, stream=s), prm, init, d0, tw, c, 0.0, dt, n, 1, 1e-12,
+        probs.append(SolidFractionProblem(pkg.Tusas(mesh, prm, stream=s), prm, init, d0, 0.0, dt, n, 1, 1e-12,
                                           stream=s))
     seq = [solid_fraction_batch([pb], [sm])[0] for pb, sm in zip(probs, samples)]
     conc = solid_fraction_batch(probs, samples)
@@ -131,3 +127,20 @@ def test_concurrent_samples_match_sequential_bitwise():
                     0.0, dt, n)
     g_eps, g0 = OA.gradient(mesh, dataclasses.replace(prm, eps4=0.045, Delta=0.42), st, 0.0, dt, w)
     assert abs(conc[1]["dS_deps4"] - g_eps) <= 1e-10 * abs(g_eps)
+
+
+@pytest.mark.parametrize("dim,order", [(2, 1), (3, 1), (2, 2)])
+def test_solid_fraction_matches_oracle(dim, order):
+    """tusas_solid_fraction: S and its weights against the oracle's exact integral of phi_h."""
+    if dim == 2:
+        mesh = Mesh(2, 7, 5, 0, 0.9, order=order)
+    else:
+        mesh = Mesh(3, 5, 4, 6, 0.8)
+    prm = Params(model=0, precond=0)
+    w, c = OA.solid_fraction_weights(mesh)
+    U = synth.uniform_pm1(11, mesh.n_dofs)
+    h = handle(mesh, prm)
+    tw = h.solid_fraction_weights(dev(np.zeros(mesh.n_dofs)))
+    assert np.abs(host(tw) - w).max() <= 1e-15 * np.abs(w).max()
+    S = h.solid_fraction(dev(U))
+    assert abs(S - (w @ U + c)) <= 1e-13 * abs(w @ U + c)

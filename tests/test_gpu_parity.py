@@ -209,6 +209,38 @@ def test_error_codes():
     assert e.value.code == pkg.ENOCONV
 
 
+def test_allocation_cap_gives_enomem_and_frees_everything():
+    """A size cap makes the multigrid hierarchy (tusas_create) and the linearisation store
+    (first exact-tangent step) fail with TUSAS_ENOMEM; nothing stays allocated."""
+    import paper_2006_16764_b300 as pkg
+
+    import gc
+
+    gc.collect()  # handles of earlier tests that are no longer referenced
+    mesh = Mesh(3, 16, 16, 16, 1.0)
+    base = 8 * mesh.n_dofs * (11 + 2 * 30 + 1) + 8 * (296 * 32 + 256)
+    held = pkg.device_bytes()
+    try:
+        pkg.set_device_bytes_cap(held + base + 4096)
+        with pytest.raises(pkg.TusasError) as e:
+            pkg.Tusas(mesh, Params(model=0, precond=2, jvp_mode=1))
+        assert e.value.code == pkg.ENOMEM
+        assert pkg.device_bytes() == held
+        pkg.set_device_bytes_cap(0)
+        h = pkg.Tusas(mesh, Params(model=0, precond=1, jvp_mode=1))
+        pkg.set_device_bytes_cap(pkg.device_bytes() + 1024)
+        h.set_state(dev(synth.seed_state(mesh, PURE, 3.0)), 0.0, 0.5)
+        with pytest.raises(pkg.TusasError) as e:
+            h.step()
+        assert e.value.code == pkg.ENOMEM
+        pkg.set_device_bytes_cap(0)
+        assert h.step()["converged"]
+        h.close()
+        assert pkg.device_bytes() == held
+    finally:
+        pkg.set_device_bytes_cap(0)
+
+
 def test_dendrite2d_128_ten_steps_match_oracle():
     """The 128^2 pure-metal workload, all 10 backward-Euler steps (FD-JFNK, point Jacobi)."""
     w = synth.workload("dendrite2d_128")

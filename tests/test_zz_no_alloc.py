@@ -37,13 +37,21 @@ def test_noalloc_dot_matches_tusas_dot_on_two_calls():
     y = torch.tensor(synth.uniform_pm1(7, n), device="cuda")
     h = pkg.Tusas(mesh, Params(model=0, precond=0))
     want = [h.dot(X[j * n:(j + 1) * n], y, n) for j in range(k)]
-    for _ in range(2):  # the shared scratch keeps the previous call's contents
+    torch.cuda.synchronize()
+    free0 = None
+    for call in range(2):  # the shared scratch keeps the previous call's contents
         rc, got = _call(lib, X, n, k, y, n)
         assert rc == pkg.OK
-        for g, w in zip(got, want):
-            assert abs(g - w) <= 1e-12 * max(abs(w), 1e-300)
+        # same partition and summation order as tusas_dot: bitwise equal, for every k
+        assert got == want
         rc, got1 = _call(lib, X, n, 1, y, n)
-        assert rc == pkg.OK and abs(got1[0] - want[0]) <= 1e-12 * abs(want[0])
+        assert rc == pkg.OK and got1[0] == want[0]
+        torch.cuda.synchronize()
+        free = torch.cuda.mem_get_info()[0]
+        if call == 0:
+            free0 = free
+        else:
+            assert free == free0, "the second call changed the free device memory"
     # the Python wrapper is the same call
     assert pkg.multidot_noalloc(X, 2, y, n)[1] == got[1]
     h.close()

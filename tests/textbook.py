@@ -79,9 +79,17 @@ def stiff1_q2(n, h):
 
 
 def mass_q2(mesh):
-    return sp.kron(mass1_q2(mesh.ny, mesh.h), mass1_q2(mesh.nx, mesh.h)).tocsr()
+    """Q2 (bi- or triquadratic) mass matrix: the Kronecker product of the 1D quadratic ones."""
+    ns = [mesh.nx, mesh.ny] + ([mesh.nz] if mesh.dim == 3 else [])
+    return _kron_list([mass1_q2(n, mesh.h) for n in ns][::-1])
 
 
 def stiffness_q2(mesh):
-    return (sp.kron(mass1_q2(mesh.ny, mesh.h), stiff1_q2(mesh.nx, mesh.h))
-            + sp.kron(stiff1_q2(mesh.ny, mesh.h), mass1_q2(mesh.nx, mesh.h))).tocsr()
+    """Q2 stiffness matrix: per axis the 1D quadratic stiffness times the 1D masses of the others."""
+    ns = [mesh.nx, mesh.ny] + ([mesh.nz] if mesh.dim == 3 else [])
+    total = None
+    for d in range(mesh.dim):
+        parts = [stiff1_q2(n, mesh.h) if e == d else mass1_q2(n, mesh.h) for e, n in enumerate(ns)]
+        term = _kron_list(parts[::-1])
+        total = term if total is None else total + term
+    return total.tocsr()
