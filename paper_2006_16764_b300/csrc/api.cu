@@ -122,12 +122,16 @@ int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
     why = "h must be positive and finite";
     return TUSAS_EINVAL;
   }
-  if (m->order < 0 || m->order > 2 || (m->order == 2 && m->dim != 2)) {
-    why = "order must be 0 or 1 (Q1) or 2 (Q2, 2D only)";
+  if (m->order < 0 || m->order > 2) {
+    why = "order must be 0 or 1 (Q1) or 2 (Q2)";
+    return TUSAS_EINVAL;
+  }
+  if (m->order == 2 && m->dim == 3 && p && p->precond == 2) {
+    why = "triquadratic hexes take precond 0 or 1 (no multigrid on the 3D Q2 node lattice)";
     return TUSAS_EINVAL;
   }
   const int po = m->order == 2 ? 2 : 1;
-  const double nodes = (double)(po * m->nx + 1) * (po * m->ny + 1) * (m->dim == 3 ? m->nz + 1 : 1);
+  const double nodes = (double)(po * m->nx + 1) * (po * m->ny + 1) * (m->dim == 3 ? po * m->nz + 1 : 1);
   if (nodes > 2.0e9) {
     why = "mesh too large (more than 2e9 nodes)";
     return TUSAS_EINVAL;
@@ -279,7 +283,7 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   {
     // admission against the device-bytes cap before any CUDA call: the vectors and the Krylov basis
     const int po = mesh->order == 2 ? 2 : 1;
-    const long long nn = (long long)(po * mesh->nx + 1) * (po * mesh->ny + 1) * (mesh->dim == 3 ? mesh->nz + 1 : 1);
+    const long long nn = (long long)(po * mesh->nx + 1) * (po * mesh->ny + 1) * (mesh->dim == 3 ? po * mesh->nz + 1 : 1);
     const long long base = (long long)sizeof(double) * 2 * nn * (11 + 2 * params->gmres_restart + 1);
     if (!tusas::dev_bytes_admit(base)) return TUSAS_ENOMEM;
   }
@@ -295,7 +299,7 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   d.nz = mesh->dim == 3 ? mesh->nz : 0;
   d.nnx = d.order * mesh->nx + 1;
   d.nny = d.order * mesh->ny + 1;
-  d.nnz = mesh->dim == 3 ? mesh->nz + 1 : 1;
+  d.nnz = mesh->dim == 3 ? d.order * mesh->nz + 1 : 1;
   d.nn = (i64)d.nnx * d.nny * d.nnz;
   d.ne = (i64)d.nx * d.ny * (mesh->dim == 3 ? d.nz : 1);
   d.h = mesh->h;

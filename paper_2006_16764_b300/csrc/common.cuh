@@ -41,6 +41,10 @@ template <int DIM> struct Tile;
 template <> struct Tile<2> { static const int X = 16, Y = 8, Z = 1; };
 template <> struct Tile<3> { static const int X = 8, Y = 4, Z = 4; };
 
+// Tile of the triquadratic (Q2 hex) kernels: one warp per element, the lanes
+// taking the 27 Gauss points (and the 27 element nodes in the transposed pass).
+struct Q2HexTile { static const int X = 4, Y = 2, Z = 2; };
+
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
 }  // namespace tusas

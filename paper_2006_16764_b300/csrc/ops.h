@@ -57,6 +57,9 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
 cudaError_t q2_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
                    double* lin, cudaStream_t st, const double* phold);
 void q2_tables(Q2Tab& T, double h);
+// The same pass on a 3D box of triquadratic (Q2) hexes with the 3 x 3 x 3 Gauss rule.
+cudaError_t q2h_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
+                    double* lin, cudaStream_t st, const double* phold);
 // 25-point stencils [2][25][nodes] of the preconditioner blocks of a Q2 box on its node
 // lattice, at the iterate U with U^n (T = float or double).
 template <typename T>

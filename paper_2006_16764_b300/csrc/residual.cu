@@ -319,7 +319,12 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
   c.K.gf = w / (m.h * m.h);
   lin_consts(c.K, P);
   c.Ku = lin_unit(P);
-  if (dim == 3) {
+  if (dim == 3 && m.order == 2) {
+    c.ntx = ceil_div(m.nx, Q2HexTile::X);
+    c.nty = ceil_div(m.ny, Q2HexTile::Y);
+    c.ntz = ceil_div(m.nz, Q2HexTile::Z);
+    c.nlin = P.model == 0 ? NLin<3, 0>::VALUE : NLin<3, 1>::VALUE;
+  } else if (dim == 3) {
     c.ntx = ceil_div(m.nx, Tile<3>::X);
     c.nty = ceil_div(m.ny, Tile<3>::Y);
     c.ntz = ceil_div(m.nz, Tile<3>::Z);
@@ -335,6 +340,8 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
 
 size_t elem_lin_doubles(const ElemCtx& c) {
   const int dim = c.m.dim;
+  if (dim == 3 && c.m.order == 2)  // [tile][coefficient][element warp][32 lanes: 27 Gauss points]
+    return (size_t)c.ntx * c.nty * c.ntz * (Q2HexTile::X * Q2HexTile::Y * Q2HexTile::Z) * 32 * c.nlin;
   const size_t ne_tile = dim == 3 ? Tile<3>::X * Tile<3>::Y * Tile<3>::Z : Tile<2>::X * Tile<2>::Y;
   const size_t ng = c.m.order == 2 ? 9 : (dim == 3 ? 8 : 4);
   return (size_t)c.ntx * c.nty * c.ntz * ne_tile * ng * c.nlin;
@@ -389,6 +396,7 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
   cudaError_t e = init ? cudaMemcpyAsync(out, init, sizeof(double) * 2 * (size_t)c.m.nn, cudaMemcpyDeviceToDevice, st)
                        : cudaMemsetAsync(out, 0, sizeof(double) * 2 * (size_t)c.m.nn, st);
   if (e != cudaSuccess) return e;
+  if (c.m.order == 2 && c.m.dim == 3) return q2h_run(mode, c, U, Un, V, out, lin, st, phold);
   if (c.m.order == 2) return q2_run(mode, c, U, Un, V, out, lin, st, phold);
   ElemArgs a;
   a.m = c.m;

@@ -1,0 +1,383 @@
+// Element-tile kernels for triquadratic (Q2) hexahedra on 3D structured boxes
+// with the 3 x 3 x 3 Gauss rule (Sec. 2.1.1, the higher-order elements of the
+// tip-velocity study, Sec. 4.1, in three dimensions): the operator modes of
+// the Q1 path (residual, residual + stored linearisation, tangent, adjoint,
+// dF/d eps4, (dF/dU^n)^T w, level-n spatial part) and the diagonals of the
+// preconditioner blocks.
+//
+// Data path of one CTA (Q2HexTile = 4 x 2 x 2 elements, one warp per element):
+//   1. the tile's 9 x 5 x 5 nodes are staged in shared memory;
+//   2. the warp interpolates its element's fields to the 27 Gauss points by
+//      sum factorisation spread over the lanes: lane l = i0 + 3 i1 + 9 i2
+//      first contracts a node line along x (Gauss point i0, node row
+//      (i1, i2)), then the lanes exchange these partial sums by shuffles
+//      for the contraction along y and along z, so that lane l ends with
+//      the value and gradient at Gauss point (i0, i1, i2): 27 FP64 FMAs per
+//      lane and field (729 per element, the cost of full sum factorisation,
+//      against 2916 for direct basis sums);
+//   3. each lane evaluates the pointwise integrands of its Gauss point
+//      (element.cuh) and the transposed stages (z, y, x) bring the test-side
+//      sums back to the lanes, lane l now holding the contribution to local
+//      node (i0, i1, i2);
+//   4. contributions go to shared memory and each tile node sums its <= 8
+//      element contributions in a fixed order before a read-modify-write of
+//      the global vector. Tiles run in 8 colours (tile-index parity per
+//      axis), so no atomics and bitwise reproducible results.
+// Lanes 27..31 mirror lane 26 and are never read.
+#include <math.h>
+
+#include "ops.h"
+
+namespace tusas {
+
+namespace {
+constexpr int HX = Q2HexTile::X, HY = Q2HexTile::Y, HZ = Q2HexTile::Z;
+constexpr int HNE = HX * HY * HZ;  // elements (warps) per tile
+constexpr int HNX = 2 * HX + 1, HNY = 2 * HY + 1, HNZ = 2 * HZ + 1;
+constexpr int HNT = HNX * HNY * HNZ;  // staged nodes per field
+constexpr int HTHREADS = 32 * HNE;
+constexpr unsigned FULL = 0xffffffffu;
+}  // namespace
+
+struct Q2HArgs {
+  DevMesh m;
+  DevPhys P;
+  Q2Tab T;
+  LinScale Ku;  // unit factors: the Q2 linearisation is stored in true units
+  const double* U;
+  const double* Un;
+  const double* V;
+  double* out;
+  double* lin;
+  const double* phold;
+  int color;
+  int ctx, cty, ctz;  // tiles of this colour per axis
+  int ntx, nty;       // tiles per axis (tile id)
+};
+
+// 1D tables in shared memory (lane-dependent indices)
+struct Q2HTab {
+  double B[3][3], G[3][3], BW[3][3], GW[3][3], BB[3][3], GG[3][3];
+};
+
+// Value (and gradient) at Gauss point (i0, i1, i2) of the field staged at sN, element
+// corner node `nb` of the tile (see the file comment). Warp-uniform call.
+template <bool GRAD>
+__device__ __forceinline__ void q2h_interp(const Q2HTab& T, const double* sN, int nb, int i0, int i1, int i2,
+                                           double& val, double* grad) {
+  // x: Gauss point i0 of the node row (y = i1, z = i2)
+  const double* np = sN + nb + HNX * (i1 + HNY * i2);
+  const double n0 = np[0], n1 = np[1], n2 = np[2];
+  const double xv = fma(T.B[i0][2], n2, fma(T.B[i0][1], n1, T.B[i0][0] * n0));
+  const double xd = GRAD ? fma(T.G[i0][2], n2, fma(T.G[i0][1], n1, T.G[i0][0] * n0)) : 0.0;
+  // y: Gauss points (i0, i1) of node layer z = i2, from lanes (i0, a, i2)
+  double yv = 0.0, ydy = 0.0, ydx = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int src = i0 + 3 * a + 9 * i2;
+    const double v = __shfl_sync(FULL, xv, src);
+    yv = fma(T.B[i1][a], v, yv);
+    if (GRAD) {
+      ydy = fma(T.G[i1][a], v, ydy);
+      ydx = fma(T.B[i1][a], __shfl_sync(FULL, xd, src), ydx);
+    }
+  }
+  // z: Gauss point (i0, i1, i2), from lanes (i0, i1, a)
+  double v = 0.0, dx = 0.0, dy = 0.0, dz = 0.0;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int src = i0 + 3 * i1 + 9 * a;
+    const double w = __shfl_sync(FULL, yv, src);
+    v = fma(T.B[i2][a], w, v);
+    if (GRAD) {
+      dz = fma(T.G[i2][a], w, dz);
+      dx = fma(T.B[i2][a], __shfl_sync(FULL, ydx, src), dx);
+      dy = fma(T.B[i2][a], __shfl_sync(FULL, ydy, src), dy);
+    }
+  }
+  val = v;
+  if (GRAD) {
+    grad[0] = dx;
+    grad[1] = dy;
+    grad[2] = dz;
+  }
+}
+
+// Test-side sum: lane (i0, i1, i2) returns sum_g w_g (s_g N_a(g) + f_g . grad N_a(g)) for local
+// node a = (i0, i1, i2), from the Gauss-point integrands (s, f) held by lane g. DIAG: squared
+// tables, the diagonal sum_g w_g (s_g N_a^2 + sum_d f_dg (dN_a/dx_d)^2). Warp-uniform call.
+template <bool DIAG>
+__device__ __forceinline__ double q2h_accum(const Q2HTab& T, double s, double fx, double fy, double fz, int i0, int i1,
+                                            int i2) {
+  const double(*BW)[3] = DIAG ? T.BB : T.BW;
+  const double(*GW)[3] = DIAG ? T.GG : T.GW;
+  // z: lane (gx = i0, gy = i1, node layer i2) from lanes (i0, i1, gz)
+  double V = 0.0, X = 0.0, Y = 0.0;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const int src = i0 + 3 * i1 + 9 * g;
+    V = fma(BW[g][i2], __shfl_sync(FULL, s, src), V);
+    V = fma(GW[g][i2], __shfl_sync(FULL, fz, src), V);
+    X = fma(BW[g][i2], __shfl_sync(FULL, fx, src), X);
+    Y = fma(BW[g][i2], __shfl_sync(FULL, fy, src), Y);
+  }
+  // y: lane (gx = i0, node row i1, layer i2) from lanes (i0, gy, i2)
+  double V2 = 0.0, X2 = 0.0;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const int src = i0 + 3 * g + 9 * i2;
+    V2 = fma(BW[g][i1], __shfl_sync(FULL, V, src), V2);
+    V2 = fma(GW[g][i1], __shfl_sync(FULL, Y, src), V2);
+    X2 = fma(BW[g][i1], __shfl_sync(FULL, X, src), X2);
+  }
+  // x: node (i0, i1, i2) from lanes (gx, i1, i2)
+  double r = 0.0;
+#pragma unroll
+  for (int g = 0; g < 3; ++g) {
+    const int src = g + 3 * i1 + 9 * i2;
+    r = fma(BW[g][i0], __shfl_sync(FULL, V2, src), r);
+    r = fma(GW[g][i0], __shfl_sync(FULL, X2, src), r);
+  }
+  return r;
+}
+
+template <int MODEL, int MODE>
+__global__ void __launch_bounds__(HTHREADS, 1) q2h_kernel(const Q2HArgs A) {
+  constexpr int NC = NLin<3, MODEL>::VALUE;
+  constexpr bool needU = MODE != M_JV && MODE != M_JTV;
+  constexpr bool needV = MODE == M_JV || MODE == M_JTV || MODE == M_PREV_T;
+  constexpr int NUF = needU ? 7 : 1;  // phi, u, phi - phi^n, u - u^n, phi^n, phihat_old, u^n
+  constexpr int NVF = needV ? 2 : 1;
+  __shared__ double sU[NUF * HNT];
+  __shared__ double sV[NVF * HNT];
+  __shared__ double sC[2 * 27 * HNE];
+  __shared__ Q2HTab sT;
+
+  const DevMesh& m = A.m;
+  const DevPhys& P = A.P;
+  int b = blockIdx.x;
+  const int bx = b % A.ctx;
+  b /= A.ctx;
+  const int by = b % A.cty;
+  const int bz = b / A.cty;
+  const int tile_x = 2 * bx + (A.color & 1);
+  const int tile_y = 2 * by + ((A.color >> 1) & 1);
+  const int tile_z = 2 * bz + ((A.color >> 2) & 1);
+  const int ex0 = tile_x * HX, ey0 = tile_y * HY, ez0 = tile_z * HZ;
+  const int nx0 = 2 * ex0, ny0 = 2 * ey0, nz0 = 2 * ez0;
+  const bool tf1 = P.time_form != 0;
+
+  // ---- 1. stage the tile's nodes and the tables ---------------------------------------
+  if (threadIdx.x < 9) {
+    const int g = threadIdx.x / 3, a = threadIdx.x % 3;
+    sT.B[g][a] = A.T.B[g][a];
+    sT.G[g][a] = A.T.G[g][a];
+    sT.BW[g][a] = A.T.BW[g][a];
+    sT.GW[g][a] = A.T.GW[g][a];
+    sT.BB[g][a] = A.T.BB[g][a];
+    sT.GG[g][a] = A.T.GG[g][a];
+  }
+  for (int s = threadIdx.x; s < HNT; s += HTHREADS) {
+    const int lx = s % HNX, ly = (s / HNX) % HNY, lz = s / (HNX * HNY);
+    const int gx = nx0 + lx, gy = ny0 + ly, gz = nz0 + lz;
+    const bool ok = gx < m.nnx && gy < m.nny && gz < m.nnz;
+    const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
+    if (needU) {
+      double phi = 0.0, u = 0.0, phin = 0.0, un = 0.0, pho = 0.0;
+      if (ok) {
+        phi = A.U[node];
+        u = A.U[m.nn + node];
+        phin = A.Un[node];
+        un = A.Un[m.nn + node];
+        if (A.phold) pho = A.phold[node];
+      }
+      sU[0 * HNT + s] = phi;
+      sU[1 * HNT + s] = u;
+      sU[2 * HNT + s] = phi - phin;
+      sU[3 * HNT + s] = u - un;
+      sU[4 * HNT + s] = phin;
+      sU[5 * HNT + s] = pho;
+      sU[6 * HNT + s] = un;
+    }
+    if (needV) {
+      sV[0 * HNT + s] = ok ? A.V[node] : 0.0;
+      sV[1 * HNT + s] = ok ? A.V[m.nn + node] : 0.0;
+    }
+  }
+  __syncthreads();
+
+  // ---- 2./3. element arithmetic: warp e, lane l ---------------------------------------------
+  const int e = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = lane < 27 ? lane : 26;
+  const int i0 = l % 3, i1 = (l / 3) % 3, i2 = l / 9;
+  const int lx = e % HX, ly = (e / HX) % HY, lz = e / (HX * HY);
+  const int ex = ex0 + lx, ey = ey0 + ly, ez = ez0 + lz;
+  const bool valid = ex < m.nx && ey < m.ny && ez < m.nz;  // uniform across the warp
+  double r0 = 0.0, r1 = 0.0;
+  if (valid) {
+    const Q2HTab& T = sT;
+    const int nb = 2 * lx + HNX * (2 * ly + HNY * 2 * lz);
+    const i64 tile_id = tile_x + (i64)A.ntx * (tile_y + (i64)A.nty * tile_z);
+    double* linp = A.lin + tile_id * (i64)(NC * HNE * 32) + e * 32 + lane;  // [c][element][lane]
+    GPOut<3> o;
+    if constexpr (MODE == M_JV || MODE == M_JTV) {
+      double v0, v1, xp[3], xg[3];
+      q2h_interp<true>(T, sV, nb, i0, i1, i2, v0, xp);
+      q2h_interp<true>(T, sV + HNT, nb, i0, i1, i2, v1, xg);
+      double L[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) L[c] = __ldg(linp + c * HNE * 32);
+      lin_apply<3, MODEL, MODE == M_JTV>(P, L, v0, v1, xp, xg, o);
+    } else {
+      double phi, u, dphi, du, p[3], gg[3];
+      q2h_interp<true>(T, sU, nb, i0, i1, i2, phi, p);
+      q2h_interp<true>(T, sU + HNT, nb, i0, i1, i2, u, gg);
+      q2h_interp<false>(T, sU + 2 * HNT, nb, i0, i1, i2, dphi, nullptr);
+      q2h_interp<false>(T, sU + 3 * HNT, nb, i0, i1, i2, du, nullptr);
+      // grad(phi^n): literal time term; level-n flux of the theta-method in the adjoint modes
+      const bool oldn = (MODE == M_DEPS || MODE == M_PREV_T) && P.theta != 1.0;
+      double pn[3] = {0.0, 0.0, 0.0};
+      if ((tf1 || oldn) && MODE != M_OLD && MODE != M_DIAG) {
+        double pnv;
+        q2h_interp<true>(T, sU + 4 * HNT, nb, i0, i1, i2, pnv, pn);
+      }
+      double pho = 0.0;
+      if ((MODE == M_RES || MODE == M_RES_LIN) && P.phihat_old)
+        q2h_interp<false>(T, sU + 5 * HNT, nb, i0, i1, i2, pho, nullptr);
+      double G4 = 0.0, G4n = 0.0;
+      if (MODEL == 1 && P.has_g4) {
+        const double z = fma(m.h, ez + A.T.xg[i2], m.z0);
+        G4 = (z - P.zT - P.Vp * (MODE == M_OLD ? P.t_new - P.dt : P.t_new)) / P.lT;
+        G4n = (z - P.zT - P.Vp * (P.t_new - P.dt)) / P.lT;
+      }
+      if (MODE == M_DIAG) {
+        // Eqs. (pref2), (preconc2) at the Gauss point: mass and stiffness coefficients of M11, M22
+        Aniso<3> An;
+        An.eval(p, P.eps4);
+        const double a2 = An.a * An.a;
+        const double B = fma(1.0 - P.k, u, 1.0);
+        const double phin = phi - dphi;
+        const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - (1.0 - P.k) * phin);
+        const double q = MODEL == 0 ? 1.0 : 0.5 * (1.0 - phi);
+        o.sphi = P.tau0 * B * a2 * P.idt;
+        o.fphi[0] = o.fphi[1] = o.fphi[2] = P.thW2 * a2;
+        o.su = Acoef * P.idt;
+        o.fu[0] = o.fu[1] = o.fu[2] = P.thD * q;
+      } else if (MODE == M_OLD) {
+        spatial_old<3, MODEL>(P, phi, u, p, gg, G4, o);
+      } else if (MODE == M_RES || MODE == M_RES_LIN) {
+        double L[MODE == M_RES_LIN ? NC : 1];
+        pointwise<3, MODEL, MODE == M_RES_LIN>(P, phi, u, dphi, du, pho, p, gg, pn, G4, o, L, A.Ku);
+        if (MODE == M_RES_LIN && lane < 27) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) linp[c * HNE * 32] = L[c];
+        }
+      } else if (MODE == M_DEPS) {
+        gp_deps<3>(P, tf1, phi, u, dphi, du, p, pn, o);
+      } else {  // M_PREV_T
+        double w0, w1, gw0[3], gw1[3];
+        q2h_interp<true>(T, sV, nb, i0, i1, i2, w0, gw0);
+        q2h_interp<true>(T, sV + HNT, nb, i0, i1, i2, w1, gw1);
+        double unv = 0.0, gn[3] = {0.0, 0.0, 0.0};
+        if (oldn) q2h_interp<true>(T, sU + 6 * HNT, nb, i0, i1, i2, unv, gn);
+        gp_prev_t<3, MODEL>(P, tf1, phi, u, dphi, du, p, pn, w0, w1, gw1, o);
+        if (oldn) old_spatial_t<3, MODEL>(P, phi - dphi, u - du, pn, gn, G4n, w0, gw0, gw1, o);
+      }
+    }
+    r0 = q2h_accum<MODE == M_DIAG>(T, o.sphi, o.fphi[0], o.fphi[1], o.fphi[2], i0, i1, i2);
+    r1 = q2h_accum<MODE == M_DIAG>(T, o.su, o.fu[0], o.fu[1], o.fu[2], i0, i1, i2);
+  }
+  if (lane < 27) {
+    sC[lane * HNE + e] = r0;
+    sC[(27 + lane) * HNE + e] = r1;
+  }
+  __syncthreads();
+
+  // ---- 4. node sums in fixed order, read-modify-write ---------------------------------------
+  for (int s = threadIdx.x; s < HNT; s += HTHREADS) {
+    const int nxl = s % HNX, nyl = (s / HNX) % HNY, nzl = s / (HNX * HNY);
+    const int gx = nx0 + nxl, gy = ny0 + nyl, gz = nz0 + nzl;
+    if (gx >= m.nnx || gy >= m.nny || gz >= m.nnz) continue;
+    double acc0 = 0.0, acc1 = 0.0;
+    // along each axis a node is local node 2 of element i/2 - 1 and local node 0 of
+    // element i/2 (i even), or local node 1 of element (i - 1)/2 (i odd)
+#pragma unroll
+    for (int cz = 0; cz < 2; ++cz) {
+      const int elz = (nzl & 1) ? (cz == 0 ? (nzl - 1) / 2 : -1) : nzl / 2 - 1 + cz;
+      const int az = (nzl & 1) ? 1 : 2 - 2 * cz;
+#pragma unroll
+      for (int cy = 0; cy < 2; ++cy) {
+        const int ely = (nyl & 1) ? (cy == 0 ? (nyl - 1) / 2 : -1) : nyl / 2 - 1 + cy;
+        const int ay = (nyl & 1) ? 1 : 2 - 2 * cy;
+#pragma unroll
+        for (int cx = 0; cx < 2; ++cx) {
+          const int elx = (nxl & 1) ? (cx == 0 ? (nxl - 1) / 2 : -1) : nxl / 2 - 1 + cx;
+          const int ax = (nxl & 1) ? 1 : 2 - 2 * cx;
+          if (elx >= 0 && elx < HX && ely >= 0 && ely < HY && elz >= 0 && elz < HZ) {
+            const int el = elx + HX * (ely + HY * elz);
+            const int a = ax + 3 * (ay + 3 * az);
+            acc0 += sC[a * HNE + el];
+            acc1 += sC[(27 + a) * HNE + el];
+          }
+        }
+      }
+    }
+    const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
+    A.out[node] += acc0;
+    A.out[m.nn + node] += acc1;
+  }
+}
+
+template <int MODEL, int MODE>
+static cudaError_t q2h_colours(const ElemCtx& c, Q2HArgs a, cudaStream_t st) {
+  for (int col = 0; col < 8; ++col) {
+    const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
+    a.color = col;
+    a.ctx = (c.ntx - cx + 1) / 2;
+    a.cty = (c.nty - cy + 1) / 2;
+    a.ctz = (c.ntz - cz + 1) / 2;
+    const long long blocks = (long long)a.ctx * a.cty * a.ctz;
+    if (blocks <= 0) continue;
+    q2h_kernel<MODEL, MODE><<<(unsigned)blocks, HTHREADS, 0, st>>>(a);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+template <int MODEL>
+static cudaError_t q2h_dispatch(int mode, const ElemCtx& c, const Q2HArgs& a, cudaStream_t st) {
+  switch (mode) {
+    case M_RES: return q2h_colours<MODEL, M_RES>(c, a, st);
+    case M_RES_LIN: return q2h_colours<MODEL, M_RES_LIN>(c, a, st);
+    case M_JV: return q2h_colours<MODEL, M_JV>(c, a, st);
+    case M_JTV: return q2h_colours<MODEL, M_JTV>(c, a, st);
+    case M_DEPS: return q2h_colours<MODEL, M_DEPS>(c, a, st);
+    case M_PREV_T: return q2h_colours<MODEL, M_PREV_T>(c, a, st);
+    case M_OLD: return q2h_colours<MODEL, M_OLD>(c, a, st);
+    case M_DIAG: return q2h_colours<MODEL, M_DIAG>(c, a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+cudaError_t q2h_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
+                    double* lin, cudaStream_t st, const double* phold) {
+  if (c.m.dim != 3 || c.m.order != 2) return cudaErrorInvalidValue;
+  Q2HArgs a;
+  a.m = c.m;
+  a.P = c.P;
+  a.T = c.q2;
+  a.Ku = c.Ku;
+  a.U = U;
+  a.Un = Un;
+  a.V = V;
+  a.out = out;
+  a.lin = lin;
+  a.phold = phold;
+  a.ntx = c.ntx;
+  a.nty = c.nty;
+  a.color = 0;
+  a.ctx = a.cty = a.ctz = 0;
+  return c.P.model == 0 ? q2h_dispatch<0>(mode, c, a, st) : q2h_dispatch<1>(mode, c, a, st);
+}
+
+}  // namespace tusas

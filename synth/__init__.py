@@ -64,8 +64,8 @@ def uniform_pm1(seed: int, n: int) -> np.ndarray:
 class Mesh:
     """Structured box of nx x ny (x nz) elements of size h; nz = 0 in 2D.
 
-    order 1: Q1 elements, node (i,j,k) at x0 + i*h; order 2: Q2 (biquadratic,
-    2D only), node (i,j) at x0 + i*h/2.
+    order 1: Q1 elements, node (i,j,k) at x0 + i*h; order 2: Q2 (biquadratic
+    quads, triquadratic hexes), node (i,j,k) at x0 + i*h/2.
     """
     dim: int
     nx: int

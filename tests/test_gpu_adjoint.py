@@ -129,13 +129,13 @@ def test_concurrent_samples_match_sequential_bitwise():
     assert abs(conc[1]["dS_deps4"] - g_eps) <= 1e-10 * abs(g_eps)
 
 
-@pytest.mark.parametrize("dim,order", [(2, 1), (3, 1), (2, 2)])
+@pytest.mark.parametrize("dim,order", [(2, 1), (3, 1), (2, 2), (3, 2)])
 def test_solid_fraction_matches_oracle(dim, order):
     """tusas_solid_fraction: S and its weights against the oracle's exact integral of phi_h."""
     if dim == 2:
         mesh = Mesh(2, 7, 5, 0, 0.9, order=order)
     else:
-        mesh = Mesh(3, 5, 4, 6, 0.8)
+        mesh = Mesh(3, 5, 4, 6, 0.8, order=order)
     prm = Params(model=0, precond=0)
     w, c = OA.solid_fraction_weights(mesh)
     U = synth.uniform_pm1(11, mesh.n_dofs)
