@@ -71,10 +71,10 @@ def parse():
                     help="steps of both arms with one full GMRES(30) cycle per Newton iteration")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-seconds", type=float, default=18.0)
-    ap.add_argument("--report", default=None, choices=synth.WORKLOADS + ["q2"],
+    ap.add_argument("--report", default=None, choices=synth.WORKLOADS + ["q2", "q2hex"],
                     help="run one workload's full protocol (step counts, precision / tangent comparisons, "
                          "adjoint gradients) and print a JSON summary; q2: biquadratic vs Q1 elements on "
-                         "the dendrite2d_1024 box")
+                         "the dendrite2d_1024 box; q2hex: triquadratic vs Q1 hexes on the dendrite3d_192 box")
     ap.add_argument("--kernels", nargs="?", const="alloy3d", default=None, choices=["alloy3d", "q2", "pc"],
                     help="profiling case: a few residual / linearisation / tangent passes on a 256x192x64 "
                          "sub-box of the alloy workload (inputs > L2, about 5 GB on the device), or (q2) on "
@@ -247,6 +247,53 @@ def run_q2_report(stream):
     print(json.dumps(out), flush=True)
 
 
+def run_q2hex_report(stream):
+    """Triquadratic (Q2 hex, 3x3x3 Gauss) against trilinear (Q1) elements in 3D.
+
+    Kernel rates at equal node counts (Q2 with n elements per axis against Q1 with 2n) on the
+    [-76.8, 76.8]^3 box of the 3D dendrite, and backward-Euler Newton-Krylov steps of its
+    centred seed at the same node spacing (0.8): Q2 48^3 with point Jacobi against Q1 96^3
+    with point Jacobi and with the FP32 multigrid V-cycle.
+    """
+    import dataclasses
+
+    import torch
+
+    w = synth.workload("dendrite3d_192")
+    out = {"report": "q2hex"}
+    rates = []
+    for n in (32, 64, 96):
+        hq = 153.6 / n
+        m2 = synth.Mesh(3, n, n, n, hq, -76.8, -76.8, -76.8, order=2)
+        m1 = synth.Mesh(3, 2 * n, 2 * n, 2 * n, hq / 2, -76.8, -76.8, -76.8)
+        rates.append({"q2_elems_per_axis": n, "q2": _operator_rates(m2, w.params, stream),
+                      "q1_same_nodes": _operator_rates(m1, w.params, stream)})
+    out["operator_rates"] = rates
+    dev = torch.device("cuda", 0)
+    nsteps = 5
+    m2 = synth.Mesh(3, 48, 48, 48, 1.6, -38.4, -38.4, -38.4, order=2)
+    m1 = synth.Mesh(3, 96, 96, 96, 0.8, -38.4, -38.4, -38.4)
+    variants = [("q2hex_48_exact_jacobi", m2, dict(precond=1, jvp_mode=1)),
+                ("q1_96_exact_jacobi", m1, dict(precond=1, jvp_mode=1)),
+                ("q1_96_exact_gmg_fp32", m1, dict(precond=2, jvp_mode=1, smoother_fp32=1))]
+    sols = {}
+    for name, mesh, opts in variants:
+        prm = dataclasses.replace(w.params, newton_maxit=30, gmres_maxit=300, **opts)
+        U0 = torch.tensor(synth.seed_state(mesh, prm, radius=10.0, centred=True), device=dev)
+        ws = synth.Workload(name, mesh, prm, w.dt, nsteps)
+        r, U = _run_variant(ws, prm, U0, nsteps, stream)
+        out[name] = r
+        sols[name] = U
+    # solid fraction of the two discretisations after the same steps (the accuracy lever of Sec. 4.1)
+    import paper_2006_16764_b300 as pkg
+
+    for name, mesh, opts in variants[:2]:
+        h = pkg.Tusas(mesh, dataclasses.replace(w.params, precond=0), stream=stream)
+        out[name]["solid_fraction"] = h.solid_fraction(sols[name])
+        h.close()
+    print(json.dumps(out), flush=True)
+
+
 def run_report(name):
     """Each workload's protocol: step counts, tangent / precision comparisons, adjoint gradients."""
     import dataclasses
@@ -257,6 +304,8 @@ def run_report(name):
 
     if name == "q2":
         return run_q2_report(torch.cuda.current_stream(torch.device("cuda", 0)))
+    if name == "q2hex":
+        return run_q2hex_report(torch.cuda.current_stream(torch.device("cuda", 0)))
     w = synth.workload(name)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream(dev)

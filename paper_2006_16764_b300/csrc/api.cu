@@ -320,7 +320,8 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
   h->m = params->gmres_restart;
   if (tusas::dev_malloc(&h->V, sizeof(double) * h->N * (h->m + 1)) != cudaSuccess ||
       tusas::dev_malloc(&h->Z, sizeof(double) * h->N * h->m) != cudaSuccess ||
-      tusas::dev_malloc(&h->partials, sizeof(double) * tusas::reduce_blocks() * 32) != cudaSuccess ||
+      tusas::dev_malloc(&h->partials, sizeof(double) * std::max(tusas::reduce_blocks(), tusas::gs_blocks()) * 32) !=
+          cudaSuccess ||
       tusas::dev_malloc(&h->sc, sizeof(double) * 256) != cudaSuccess) {
     tusas_destroy(h);
     return TUSAS_ENOMEM;
@@ -624,10 +625,11 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       // classical Gram-Schmidt applied twice (CGS2): h = V^T w; w -= V h; h2 = V^T w;
       // w -= V h2 fused with ||w||^2; h += h2
       const size_t to = tbeg(h);
-      TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc, h->st));
-      TCK(tusas::multi_axpy(N, j + 1, h->V, N, h->sc, w, nullptr, h->st));
-      TCK(tusas::multidot(N, j + 1, h->V, N, w, h->partials, h->sc + 64, h->st));
-      TCK(tusas::multi_axpy_norm(N, j + 1, h->V, N, h->sc + 64, w, h->partials, h->sc + 63, h->st));
+      // three passes over the basis: h = V^T w; w -= V h fused with h2 = V^T w; w -= V h2 fused
+      // with ||w||^2
+      TCK(tusas::gs_pass(0, N, j + 1, h->V, N, nullptr, w, h->partials, h->sc, h->st));
+      TCK(tusas::gs_pass(1, N, j + 1, h->V, N, h->sc, w, h->partials, h->sc + 64, h->st));
+      TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, w, h->partials, h->sc + 63, h->st));
       std::vector<double> col2(64);
       TCK(cudaMemcpyAsync(col.data(), h->sc, sizeof(double) * 64, cudaMemcpyDeviceToHost, h->st));
       TCK(cudaMemcpyAsync(col2.data(), h->sc + 64, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->st));

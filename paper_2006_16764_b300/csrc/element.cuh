@@ -258,11 +258,12 @@ template <int DIM>
 struct Aniso {
   double a, sn, r;
   double n[DIM], n2[DIM];
-  __device__ __forceinline__ void eval(const double* p, double eps) {
+  // guard_q: the guard threshold on |p|^2 in the units of p (1e-20 for true gradients)
+  __device__ __forceinline__ void eval(const double* p, double eps, double guard_q = TUSAS_GUARD_Q) {
     double q = p[0] * p[0];
 #pragma unroll
     for (int d = 1; d < DIM; ++d) q = fma(p[d], p[d], q);
-    if (q < TUSAS_GUARD_Q) {
+    if (q < guard_q) {
       a = 1.0;
       sn = 0.0;
       r = 0.0;
@@ -305,6 +306,46 @@ inline LinScale lin_unit(const DevPhys& P) {
   return K;
 }
 
+// Constants of pointwise() for gradients given as gsc times the true gradient (true
+// units: gsc = 1; the staged forms of the 3D tile residual pass h-scaled differences,
+// gsc = 1/h), with the linearisation factors K. Where a gradient enters linearly its unit
+// rides on a uniform constant, and 1/|p| is rescaled the same way, so the integrands cost
+// no conversions per Gauss point. Also the frozen gradient G4 = z ilT + g4off.
+struct PwConst {
+  double guard_q;   // small-gradient guard on |p|^2 in the caller's units: 1e-20 / gsc^2
+  double gsc;       // true gradient = gsc x caller gradient
+  double thW2g;     // theta W0^2 gsc
+  double thDg;      // theta D gsc (pure-metal diffusion flux)
+  double halfthDg;  // theta D gsc / 2 (alloy: D q(phi) grad u)
+  double cw, cwg;   // W0/(2 sqrt 2): antitrapping along n; and times gsc, along the printed grad phi
+  double tau2c;     // K.tau2_gv 16 eps / gsc: alpha_p = tau2c B (phi - phi^n)/dt a / |p_caller| R
+  double kapc;      // K.cw_gf / gsc: kappa = kapc B phihat / |p_caller|
+  double mhthDg;    // K.m_half_thD_vf gsc: gamma_phi = mhthDg grad u_caller + ...
+  double e32g, e256g;  // K.thW2_gf 32 eps, K.thW2_gf 256 eps^2 (flux Hessian)
+  double thW2gf;    // K.thW2_gf
+  double ilT, g4off;   // G4 = z / lT - (zT + Vp t^{n+1}) / lT
+};
+
+inline PwConst pw_consts(const DevPhys& P, const LinScale& K, double gsc) {
+  PwConst c{};
+  c.guard_q = TUSAS_GUARD_Q / (gsc * gsc);
+  c.gsc = gsc;
+  c.thW2g = P.thW2 * gsc;
+  c.thDg = P.thD * gsc;
+  c.halfthDg = 0.5 * P.thD * gsc;
+  c.cw = TUSAS_INV_2SQRT2 * P.W0;
+  c.cwg = c.cw * gsc;
+  c.tau2c = K.tau2_gv * 16.0 * P.eps4 / gsc;
+  c.kapc = K.cw_gf / gsc;
+  c.mhthDg = K.m_half_thD_vf * gsc;
+  c.e32g = K.thW2_gf * 32.0 * P.eps4;
+  c.e256g = K.thW2_gf * 256.0 * P.eps4 * P.eps4;
+  c.thW2gf = K.thW2_gf;
+  c.ilT = P.has_g4 ? 1.0 / P.lT : 0.0;
+  c.g4off = P.has_g4 ? -(P.zT + P.Vp * P.t_new) / P.lT : 0.0;
+  return c;
+}
+
 // symmetric index (i <= j) -> 0..SYM-1: diagonal first, then (0,1),(0,2),(1,2)
 template <int DIM>
 __host__ __device__ constexpr int sym_index(int i, int j) {
@@ -313,109 +354,120 @@ __host__ __device__ constexpr int sym_index(int i, int j) {
 
 // Residual integrands and, if LIN, the pointwise Jacobian written to L[c]
 // (c-th coefficient of this Gauss point; stride given by the caller's writer).
-// The stored coefficients L carry the LinScale factors of their type (K; unit
-// factors give the coefficients in true units): the factors ride on constants
-// that are uniform across threads, so they cost no work per Gauss point.
+// p, g, pn are the gradients of phi, u, phi^n in the caller's units (C.gsc times
+// them is the true gradient); the outputs are in true units: sphi, su the
+// source terms, fphi, fu the fluxes. The stored coefficients L carry the
+// LinScale factors of their type (K; unit factors give the coefficients in true
+// units): the factors ride on constants that are uniform across threads, so
+// they cost no work per Gauss point. The pure metal (MODEL 0) has k = 1, so
+// B(u) = 1 and A(phi^n) = 1 are constants there.
 template <int DIM, int MODEL, bool LIN>
-__device__ __forceinline__ void pointwise(const DevPhys& P, double phi, double u, double dphi, double du,
-                                          double phold, const double* p, const double* g, const double* pn,
-                                          double G4, GPOut<DIM>& o, double* L, const LinScale& K) {
+__device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, double phi, double u, double dphi,
+                                          double du, double phold, const double* p, const double* g,
+                                          const double* pn, double G4, GPOut<DIM>& o, double* L,
+                                          const LinScale& K) {
   Aniso<DIM> A;
-  A.eval(p, P.eps4);
+  A.eval(p, P.eps4, C.guard_q);
   const double eps = P.eps4;
   const double c16 = 16.0 * eps;
-  // anisotropic flux f = theta W0^2 a p_i (a + 16 eps (n_i^2 - sn))
-  const double W2a = P.thW2 * A.a;
+  double m[DIM];  // n_i^2 - sum n^4
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, A.n2[d] - A.sn, A.a);
+  for (int d = 0; d < DIM; ++d) m[d] = A.n2[d] - A.sn;
+  // anisotropic flux f = theta W0^2 a p_i (a + 16 eps (n_i^2 - sn))
+  const double W2a = C.thW2g * A.a;
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, m[d], A.a);
   const double dphidt = dphi * P.idt;  // time term
   const double phihat = P.phihat_old ? fma(P.theta, dphidt, (1.0 - P.theta) * phold) : dphidt;  // source, j
   const double omk = 1.0 - P.k;
-  const double B = fma(omk, u, 1.0);
+  const double B = MODEL == 0 ? 1.0 : fma(omk, u, 1.0);
   const double a2 = A.a * A.a;
   const double phi2 = phi * phi;
   const double om = 1.0 - phi2;
   const double ug = u + G4;
+  const double phom = phi * om;
+  const double om2 = om * om;
+  const double Bt = MODEL == 0 ? dphidt : B * dphidt;
+  const double phin = phi - dphi;
   double time;
-  double an2 = 0.0, Bn = 0.0, phin = phi - dphi;
   if (P.time_form == 0) {
-    time = P.tau0 * B * a2 * dphidt;
+    time = P.tau0 * a2 * Bt;
   } else {
     Aniso<DIM> An;
-    An.eval(pn, eps);
-    an2 = An.a * An.a;
-    Bn = fma(omk, u - du, 1.0);
-    time = P.tau0 * (B * a2 * phi - Bn * an2 * phin) * P.idt;
+    An.eval(pn, eps, C.guard_q);
+    const double Bn = MODEL == 0 ? 1.0 : fma(omk, u - du, 1.0);
+    time = P.tau0 * (B * a2 * phi - Bn * (An.a * An.a) * phin) * P.idt;
   }
-  o.sphi = fma(-P.theta, phi * om - P.lam * om * om * ug, time);
+  o.sphi = fma(-P.theta, fma(-P.lam * om2, ug, phom), time);
   const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - omk * phin);
-  o.su = Acoef * du * P.idt - 0.5 * phihat * B;
-  double Dq = P.thD, jn = 0.0;
+  const double Bp = MODEL == 0 ? phihat : B * phihat;
+  o.su = fma(-0.5, Bp, Acoef * du * P.idt);
+  double Bpr = 0.0;
   if (MODEL == 0) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) o.fu[d] = P.thD * g[d];
+    for (int d = 0; d < DIM; ++d) o.fu[d] = C.thDg * g[d];
   } else {
-    Dq = 0.5 * P.thD * (1.0 - phi);
-    const double cj = TUSAS_INV_2SQRT2 * P.W0 * B * phihat;
-    jn = P.jat_norm ? cj * A.r : cj;
+    const double Dq = C.halfthDg * (1.0 - phi);
+    Bpr = Bp * A.r;
+    const double jn = P.jat_norm ? C.cw * Bpr : C.cwg * Bp;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) o.fu[d] = fma(Dq, g[d], jn * p[d]);
   }
   if constexpr (LIN) {
-  // ---- pointwise Jacobian -------------------------------------------------
-  // m_i = n_i^2 - sn, R_i = n_i m_i: da/dp_i = 16 eps R_i / |p|
-  double R[DIM];
+    // ---- pointwise Jacobian -------------------------------------------------
+    // m_i = n_i^2 - sn, R_i = n_i m_i: da/dp_i = 16 eps R_i / |p|
+    double R[DIM];
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) R[d] = A.n[d] * (A.n2[d] - A.sn);
-  const double dbulk = (1.0 - 3.0 * phi2) + 4.0 * P.lam * phi * om * ug;
-  const double tfac = P.time_form == 0 ? dphidt : phi * P.idt;  // multiplies d(B a^2)
-  L[0] = fma(K.m_th_vv, dbulk, K.tau_idt_vv * B * a2);           // alpha_phi
-  L[1] = fma(K.thlam_vv, om * om, K.tau_vv * omk * a2 * tfac);  // alpha_u
-  const double c2a = K.tau2_gv * B * tfac * A.a * (c16 * A.r);
+    for (int d = 0; d < DIM; ++d) R[d] = A.n[d] * m[d];
+    const double dbulk = fma(4.0 * P.lam * phom, ug, fma(-3.0, phi2, 1.0));
+    // with the literal time term the coefficients of d(B a^2) multiply phi/dt instead of phihat
+    const double tfac = P.time_form == 0 ? dphidt : phi * P.idt;
+    const double Btf = P.time_form == 0 ? Bt : (MODEL == 0 ? tfac : B * tfac);
+    L[0] = fma(K.m_th_vv, dbulk, K.tau_idt_vv * B * a2);  // alpha_phi
+    L[1] = MODEL == 0 ? K.thlam_vv * om2 : fma(K.thlam_vv, om2, K.tau_vv * omk * a2 * tfac);  // alpha_u
+    const double c2a = C.tau2c * Btf * (A.a * A.r);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * R[d];  // alpha_p = 2 tau0 B a da/dp
-  // H = theta W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn)) + n_i n_j B_ij ],
-  //   B_ij = 256 eps^2 m_i m_j + 32 eps a (sn - n_i^2 - n_j^2) = 256 eps^2 m_i m_j - 32 eps a (m_i + m_j + sn).
-  // With n_i^2 = m_i + sn: n_i n_j B_ij = P_i R_j - T_i n_j, P_i = n_i (256 eps^2 m_i - 32 eps a),
-  // T_i = 32 eps a n_i^3, and the diagonal term is a^2 + 32 eps a sn + 48 eps a m_i;
-  // theta W0^2 and the coefficient factor ride on P_i, T_i and the diagonal constants.
-  const double e32a = 32.0 * eps * A.a, e256 = 256.0 * eps * eps;
-  const double kt = K.thW2_gf * e32a;
-  const double kd0 = K.thW2_gf * fma(e32a, A.sn, a2), kd1 = 1.5 * kt;
-  double Pk[DIM], Tk[DIM];
+    for (int d = 0; d < DIM; ++d) L[2 + d] = c2a * R[d];  // alpha_p = 2 tau0 B a da/dp
+    // H = theta W0^2 [ delta_ij (a^2 + 16 eps a (3 n_i^2 - sn)) + n_i n_j B_ij ],
+    //   B_ij = 256 eps^2 m_i m_j - 32 eps a (m_i + m_j + sn); n_i n_j B_ij = P_i R_j - T_i n_j with
+    //   P_i = n_i (256 eps^2 m_i - 32 eps a), T_i = 32 eps a n_i^3; the diagonal term is
+    //   a^2 + 32 eps a sn + 48 eps a m_i. theta W0^2 and the coefficient factor ride on the constants.
+    const double kt = C.e32g * A.a;
+    const double kd0 = fma(kt, A.sn, C.thW2gf * a2), kd1 = 1.5 * kt;
+    double Pk[DIM], Tk[DIM];
 #pragma unroll
-  for (int i = 0; i < DIM; ++i) {
-    Pk[i] = K.thW2_gf * A.n[i] * fma(e256, A.n2[i] - A.sn, -e32a);
-    Tk[i] = kt * A.n[i] * A.n2[i];
-  }
-#pragma unroll
-  for (int i = 0; i < DIM; ++i) {
-#pragma unroll
-    for (int j = i; j < DIM; ++j) {
-      double v = fma(Pk[i], R[j], -Tk[i] * A.n[j]);
-      if (i == j) v += fma(kd1, A.n2[i] - A.sn, kd0);
-      L[2 + DIM + sym_index<DIM>(i, j)] = v;
+    for (int i = 0; i < DIM; ++i) {
+      Pk[i] = A.n[i] * fma(C.e256g, m[i], -kt);
+      Tk[i] = kt * (A.n[i] * A.n2[i]);
     }
-  }
-  if (MODEL == 1) {
-    constexpr int o0 = NLin<DIM, 1>::PHI;
-    L[o0 + 0] = K.mdphat * B;                                // beta_phi
-    L[o0 + 1] = fma(Acoef, K.idt, -K.half_omk_vv * phihat);  // beta_u
-    // direction of the antitrapping current and its derivative factors
-    double nv[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) nv[d] = P.jat_norm ? A.n[d] : p[d];
-    const double kap = P.jat_norm ? K.cw_gf * B * phihat * A.r : K.cw_gf * B * phihat;
-    const double cgp = K.cw_dphat_vf * B;
+    for (int i = 0; i < DIM; ++i) {
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(K.m_half_thD_vf, g[d], cgp * nv[d]);  // gamma_phi
-    L[o0 + 2 + DIM] = K.cw_omk_vf * phihat;                                                 // c_u
-    L[o0 + 3 + DIM] = K.half_thD_gf * (1.0 - phi);                                          // gamma_g
-    L[o0 + 4 + DIM] = kap;                                                                            // kappa1
-    L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                                         // kappa2
+      for (int j = i; j < DIM; ++j) {
+        double v = fma(Pk[i], R[j], -Tk[i] * A.n[j]);
+        if (i == j) v += fma(kd1, m[i], kd0);
+        L[2 + DIM + sym_index<DIM>(i, j)] = v;
+      }
+    }
+    if (MODEL == 1) {
+      constexpr int o0 = NLin<DIM, 1>::PHI;
+      L[o0 + 0] = K.mdphat * B;                                // beta_phi
+      L[o0 + 1] = fma(Acoef, K.idt, -K.half_omk_vv * phihat);  // beta_u
+      // direction of the antitrapping current (true units) and its derivative factors
+      double nv[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];                                       // nvec
-  }
+      for (int d = 0; d < DIM; ++d) nv[d] = P.jat_norm ? A.n[d] : C.gsc * p[d];
+      const double kap = P.jat_norm ? C.kapc * Bpr : K.cw_gf * Bp;
+      const double cgp = K.cw_dphat_vf * B;
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(C.mhthDg, g[d], cgp * nv[d]);  // gamma_phi
+      L[o0 + 2 + DIM] = K.cw_omk_vf * phihat;                                           // c_u
+      L[o0 + 3 + DIM] = K.half_thD_gf * (1.0 - phi);                                    // gamma_g
+      L[o0 + 4 + DIM] = kap;                                                            // kappa1
+      L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                         // kappa2
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];  // nvec
+    }
   }
 }
 

@@ -40,6 +40,7 @@ struct ElemCtx {
   Scales S;
   LinScale K;   // scaled linearisation of the Q1 tangent / adjoint passes
   LinScale Ku;  // unit factors (Q2 passes)
+  PwConst pw_elem, pw_res3, pw_q2;  // pointwise constants per kernel family (gradient units, factors)
   Q2Tab q2;
   int ntx, nty, ntz;  // tiles per axis
   int nlin;           // linearisation coefficients per Gauss point
@@ -91,6 +92,14 @@ cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, d
 // y -= sum_j c[j] X_j fused with the deterministic norm: *out_norm2 = ||y||^2
 cudaError_t multi_axpy_norm(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* partials,
                             double* out_norm2, cudaStream_t st);
+// Gram-Schmidt passes of the GMRES orthogonalisation over X_0..X_{k-1} (k <= 32) and w,
+// deterministic; partials holds gs_blocks() x 32 doubles; c and out are device arrays:
+//   pass 0: out[j] = X_j . w
+//   pass 1: w -= sum_j c[j] X_j, then out[j] = X_j . w
+//   pass 2: w -= sum_j c[j] X_j, then out[0] = ||w||^2
+int gs_blocks();
+cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w, double* partials,
+                    double* out, cudaStream_t st);
 // x = sum_j c[j] X_j + x (c on host memory passed by value through a device array)
 cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st);
 

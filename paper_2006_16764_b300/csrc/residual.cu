@@ -25,6 +25,7 @@ struct ElemArgs {
   double h, inv_h;  // element size and its inverse
   double wh;        // Gauss weight over h, w / h: the node-sum factor of the residual-type passes
   LinScale K;       // staged-form linearisation factors (tangent / adjoint passes)
+  PwConst C;        // pointwise constants for the gradient units of the kernel (true, or staged in 3D)
   const double* U;
   const double* Un;
   const double* V;
@@ -223,8 +224,8 @@ elem_kernel(const ElemArgs A) {
           spatial_old<DIM, MODEL>(A.P, phi[g], u[g], p, gg, G4, o);
         } else if (MODE == M_RES || MODE == M_RES_LIN) {
           double L[MODE == M_RES_LIN ? NC : 1];
-          pointwise<DIM, MODEL, MODE == M_RES_LIN>(A.P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L,
-                                                   A.K);
+          pointwise<DIM, MODEL, MODE == M_RES_LIN>(A.P, A.C, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o,
+                                                   L, A.K);
           if (MODE == M_RES_LIN) {
 #pragma unroll
             for (int c = 0; c < NC; ++c) linp[(c * NN + g) * NE] = L[c];
@@ -319,6 +320,9 @@ void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P) {
   c.K.gf = w / (m.h * m.h);
   lin_consts(c.K, P);
   c.Ku = lin_unit(P);
+  c.pw_elem = pw_consts(P, c.K, 1.0);       // elem_kernel: true gradients, staged linearisation
+  c.pw_res3 = pw_consts(P, c.K, 1.0 / m.h);  // res3_kernel: staged gradients and linearisation
+  c.pw_q2 = pw_consts(P, c.Ku, 1.0);         // Q2 kernels: true units throughout
   if (dim == 3 && m.order == 2) {
     c.ntx = ceil_div(m.nx, Q2HexTile::X);
     c.nty = ceil_div(m.ny, Q2HexTile::Y);
@@ -405,6 +409,7 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
   a.inv_h = 1.0 / c.m.h;
   a.wh = (c.m.dim == 3 ? 0.125 * c.m.h * c.m.h : 0.25 * c.m.h);
   a.K = c.K;
+  a.C = c.m.dim == 3 ? c.pw_res3 : c.pw_elem;
   a.U = U;
   a.Un = Un;
   a.V = V;

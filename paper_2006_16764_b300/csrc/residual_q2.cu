@@ -29,6 +29,7 @@ struct Q2Args {
   DevPhys P;
   Q2Tab T;
   LinScale Ku;  // unit factors: the Q2 linearisation is stored in true units
+  PwConst C;    // pointwise constants, true units
   const double* U;
   const double* Un;
   const double* V;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
           spatial_old<2, MODEL>(P, phi[g], u[g], p, gg, G4, o);
         } else if (MODE == M_RES || MODE == M_RES_LIN) {
           double L[MODE == M_RES_LIN ? NC : 1];
-          pointwise<2, MODEL, MODE == M_RES_LIN>(P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L,
+          pointwise<2, MODEL, MODE == M_RES_LIN>(P, A.C, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L,
                                                  A.Ku);
           if (MODE == M_RES_LIN) {
 #pragma unroll
@@ -558,6 +559,7 @@ cudaError_t q2_run(int mode, const ElemCtx& c, const double* U, const double* Un
   a.P = c.P;
   a.T = c.q2;
   a.Ku = c.Ku;
+  a.C = c.pw_q2;
   a.U = U;
   a.Un = Un;
   a.V = V;

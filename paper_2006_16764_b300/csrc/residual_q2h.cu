@@ -44,6 +44,7 @@ struct Q2HArgs {
   DevPhys P;
   Q2Tab T;
   LinScale Ku;  // unit factors: the Q2 linearisation is stored in true units
+  PwConst C;    // pointwise constants, true units
   const double* U;
   const double* Un;
   const double* V;
@@ -267,7 +268,7 @@ __global__ void __launch_bounds__(HTHREADS, 1) q2h_kernel(const Q2HArgs A) {
         spatial_old<3, MODEL>(P, phi, u, p, gg, G4, o);
       } else if (MODE == M_RES || MODE == M_RES_LIN) {
         double L[MODE == M_RES_LIN ? NC : 1];
-        pointwise<3, MODEL, MODE == M_RES_LIN>(P, phi, u, dphi, du, pho, p, gg, pn, G4, o, L, A.Ku);
+        pointwise<3, MODEL, MODE == M_RES_LIN>(P, A.C, phi, u, dphi, du, pho, p, gg, pn, G4, o, L, A.Ku);
         if (MODE == M_RES_LIN && lane < 27) {
 #pragma unroll
           for (int c = 0; c < NC; ++c) linp[c * HNE * 32] = L[c];
@@ -367,6 +368,7 @@ cudaError_t q2h_run(int mode, const ElemCtx& c, const double* U, const double* U
   a.P = c.P;
   a.T = c.q2;
   a.Ku = c.Ku;
+  a.C = c.pw_q2;
   a.U = U;
   a.Un = Un;
   a.V = V;

@@ -423,19 +423,24 @@ __global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
     double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
     double s0[8], s1[8], f0[3][8], f1[3][8];
     GPOut<3> o;
+    // frozen gradient at the two Gauss-point levels of the element (z = z0 + h (ez + t), h (ez + 1 - t))
+    double G4z[2] = {0.0, 0.0};
+    if (MODEL == 1 && A.P.has_g4) {
+      G4z[0] = fma(fma(m.h, ez + TUSAS_GP_T, m.z0), A.C.ilT, A.C.g4off);
+      G4z[1] = fma(fma(m.h, ez + (1.0 - TUSAS_GP_T), m.z0), A.C.ilT, A.C.g4off);
+    }
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
+      // gradients stay in the staged units (h times the gradient): A.C carries the factors
       double p[3], gg[3], pn[3];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        p[d] = gp[d][remove_bit(g, d)] * A.inv_h;
-        gg[d] = gu[d][remove_bit(g, d)] * A.inv_h;
-        pn[d] = tf1 ? gpn[d][remove_bit(g, d)] * A.inv_h : 0.0;
+        p[d] = gp[d][remove_bit(g, d)];
+        gg[d] = gu[d][remove_bit(g, d)];
+        pn[d] = tf1 ? gpn[d][remove_bit(g, d)] : 0.0;
       }
-      double G4 = 0.0;
-      if (MODEL == 1 && A.P.has_g4) G4 = (gp_last_coord<3>(m, ez, g) - A.P.zT - A.P.Vp * A.P.t_new) / A.P.lT;
       double L[LIN ? NC : 1];
-      pointwise<3, MODEL, LIN>(A.P, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4, o, L, A.K);
+      pointwise<3, MODEL, LIN>(A.P, A.C, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4z[g >> 2], o, L, A.K);
       if (LIN) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) linp[(c * 8 + g) * NE] = L[c];

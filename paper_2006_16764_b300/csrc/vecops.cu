@@ -281,4 +281,178 @@ cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, d
   return multi_axpy_sign(n, k, X, ld, c, 1.0, x, st);
 }
 
+// ---- Gram-Schmidt passes of the GMRES orthogonalisation ---------------------------
+// Streaming kernels over the basis X_0..X_{k-1} (stride ld) and the new vector w,
+// 16-byte loads (pairs of doubles) when n, ld and the pointers allow it. Fixed
+// partition of the pairs into GS_BLOCKS contiguous chunks, thread-stride order
+// inside a chunk, fixed in-block tree, and one warp per output for the sum of the
+// per-block partials: deterministic.
+static const int GS_BLOCKS = 148 * 4;
+static const int GS_T = 256;
+
+template <int VEC> struct Vec;
+template <> struct Vec<1> {
+  typedef double T;
+  static __device__ __forceinline__ double dot(T a, T b, double acc) { return fma(a, b, acc); }
+  static __device__ __forceinline__ T axpy(double c, T x, T y) { return fma(c, x, y); }
+};
+template <> struct Vec<2> {
+  typedef double2 T;
+  static __device__ __forceinline__ double dot(T a, T b, double acc) { return fma(a.y, b.y, fma(a.x, b.x, acc)); }
+  static __device__ __forceinline__ T axpy(double c, T x, T y) { return make_double2(fma(c, x.x, y.x), fma(c, x.y, y.y)); }
+};
+
+// Sum of KM per-thread accumulators over the block into partials[blockIdx.x * 32 + j], j < k.
+template <int KM>
+__device__ __forceinline__ void gs_block_sum(const double* acc, int k, double* __restrict__ partials) {
+  __shared__ double red[GS_T / 32][KM];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    if (j < k) {
+      double v = acc[j];
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+      if (lane == 0) red[warp][j] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < k) {
+    double s = 0.0;
+#pragma unroll
+    for (int w = 0; w < GS_T / 32; ++w) s += red[w][threadIdx.x];
+    partials[blockIdx.x * 32 + threadIdx.x] = s;
+  }
+}
+
+// partials[b][j] of X_j . w
+template <int KM, int VEC>
+__global__ void __launch_bounds__(GS_T) k_gs_dots(i64 nv, int k, const double* __restrict__ X, i64 ldv,
+                                                  const double* __restrict__ w, double* __restrict__ partials) {
+  typedef typename Vec<VEC>::T T;
+  const T* Xv = reinterpret_cast<const T*>(X);
+  const T* wv = reinterpret_cast<const T*>(w);
+  double acc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+  const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
+  const i64 lo = blockIdx.x * chunk;
+  const i64 hi = lo + chunk < nv ? lo + chunk : nv;
+  for (i64 i = lo + threadIdx.x; i < hi; i += GS_T) {
+    const T wi = wv[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) acc[j] = Vec<VEC>::dot(Xv[j * ldv + i], wi, acc[j]);
+  }
+  gs_block_sum<KM>(acc, k, partials);
+}
+
+// w -= sum_j c_j X_j, then partials[b][j] of X_j . w (the updated w)
+template <int KM, int VEC>
+__global__ void __launch_bounds__(GS_T) k_gs_update_dots(i64 nv, int k, const double* __restrict__ X, i64 ldv,
+                                                         const double* __restrict__ c, double* __restrict__ w,
+                                                         double* __restrict__ partials) {
+  typedef typename Vec<VEC>::T T;
+  const T* Xv = reinterpret_cast<const T*>(X);
+  T* wv = reinterpret_cast<T*>(w);
+  double cc[KM], acc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) {
+    cc[j] = j < k ? -c[j] : 0.0;
+    acc[j] = 0.0;
+  }
+  const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
+  const i64 lo = blockIdx.x * chunk;
+  const i64 hi = lo + chunk < nv ? lo + chunk : nv;
+  for (i64 i = lo + threadIdx.x; i < hi; i += GS_T) {
+    T x[KM];
+    T wi = wv[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) {
+        x[j] = Xv[j * ldv + i];
+        wi = Vec<VEC>::axpy(cc[j], x[j], wi);
+      }
+    wv[i] = wi;
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) acc[j] = Vec<VEC>::dot(x[j], wi, acc[j]);
+  }
+  gs_block_sum<KM>(acc, k, partials);
+}
+
+// w -= sum_j c_j X_j, then partials[b][0] of ||w||^2
+template <int KM, int VEC>
+__global__ void __launch_bounds__(GS_T) k_gs_update_norm(i64 nv, int k, const double* __restrict__ X, i64 ldv,
+                                                         const double* __restrict__ c, double* __restrict__ w,
+                                                         double* __restrict__ partials) {
+  typedef typename Vec<VEC>::T T;
+  const T* Xv = reinterpret_cast<const T*>(X);
+  T* wv = reinterpret_cast<T*>(w);
+  double cc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) cc[j] = j < k ? -c[j] : 0.0;
+  double acc[1] = {0.0};
+  const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
+  const i64 lo = blockIdx.x * chunk;
+  const i64 hi = lo + chunk < nv ? lo + chunk : nv;
+  for (i64 i = lo + threadIdx.x; i < hi; i += GS_T) {
+    T wi = wv[i];
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j < k) wi = Vec<VEC>::axpy(cc[j], Xv[j * ldv + i], wi);
+    wv[i] = wi;
+    acc[0] = Vec<VEC>::dot(wi, wi, acc[0]);
+  }
+  gs_block_sum<1>(acc, 1, partials);
+}
+
+template <int VEC>
+static cudaError_t gs_launch(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
+                             double* partials, cudaStream_t st) {
+  const i64 nv = n / VEC, ldv = ld / VEC;
+  const int g = GS_BLOCKS;
+#define TUSAS_GS(KM)                                                                              \
+  do {                                                                                            \
+    if (pass == 0)                                                                                \
+      k_gs_dots<KM, VEC><<<g, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);                         \
+    else if (pass == 1)                                                                           \
+      k_gs_update_dots<KM, VEC><<<g, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);               \
+    else                                                                                          \
+      k_gs_update_norm<KM, VEC><<<g, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);               \
+  } while (0)
+  if (k <= 4)
+    TUSAS_GS(4);
+  else if (k <= 8)
+    TUSAS_GS(8);
+  else if (k <= 16)
+    TUSAS_GS(16);
+  else
+    TUSAS_GS(32);
+#undef TUSAS_GS
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+int gs_blocks() { return GS_BLOCKS; }
+
+cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w, double* partials,
+                    double* out, cudaStream_t st) {
+  if (k < 1 || k > 32) return cudaErrorInvalidValue;
+  const bool vec = n % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)w % 16) == 0;
+  if (pass == 1 && k > 16) {
+    // the fused update + dots would spill with 32 vectors in registers: update, then dots
+    cudaError_t e = multi_axpy_sign(n, k, X, ld, c, -1.0, w, st);
+    if (e != cudaSuccess) return e;
+    pass = 0;
+  }
+  cudaError_t e = vec ? gs_launch<2>(pass, n, k, X, ld, c, w, partials, st)
+                      : gs_launch<1>(pass, n, k, X, ld, c, w, partials, st);
+  if (e != cudaSuccess) return e;
+  const int kout = pass == 2 ? 1 : k;
+  k_reduce_partials<<<1, 32 * kout, 0, st>>>(GS_BLOCKS, kout, 32, partials, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
+
 }  // namespace tusas

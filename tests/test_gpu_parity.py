@@ -218,7 +218,7 @@ def test_allocation_cap_gives_enomem_and_frees_everything():
 
     gc.collect()  # handles of earlier tests that are no longer referenced
     mesh = Mesh(3, 16, 16, 16, 1.0)
-    base = 8 * mesh.n_dofs * (11 + 2 * 30 + 1) + 8 * (296 * 32 + 256)
+    base = 8 * mesh.n_dofs * (11 + 2 * 30 + 1) + 8 * (592 * 32 + 256)
     held = pkg.device_bytes()
     try:
         pkg.set_device_bytes_cap(held + base + 4096)
