@@ -75,11 +75,11 @@ def parse():
                     help="run one workload's full protocol (step counts, precision / tangent comparisons, "
                          "adjoint gradients) and print a JSON summary; q2: biquadratic vs Q1 elements on "
                          "the dendrite2d_1024 box; q2hex: triquadratic vs Q1 hexes on the dendrite3d_192 box")
-    ap.add_argument("--kernels", nargs="?", const="alloy3d", default=None, choices=["alloy3d", "q2", "pc"],
+    ap.add_argument("--kernels", nargs="?", const="alloy3d", default=None, choices=["alloy3d", "q2", "pc", "gmres"],
                     help="profiling case: a few residual / linearisation / tangent passes on a 256x192x64 "
                          "sub-box of the alloy workload (inputs > L2, about 5 GB on the device), or (q2) on "
                          "a 1536^2 Q2 box of the 2D dendrite (about 2 GB), or (pc) 2 preconditioner setups and "
-                         "3 applies (FP32 GMG) on the same alloy sub-box")
+                         "3 applies (FP32 GMG) on the same alloy sub-box, or (gmres) one FD-JFNK step there")
     return ap.parse_args()
 
 
@@ -92,6 +92,18 @@ def run_kernels(kind="alloy3d"):
 
     import paper_2006_16764_b300 as pkg
 
+    if kind == "gmres":
+        # one FD-JFNK step with the FP32 multigrid (no linearisation store: about 4 GB on the device)
+        w = synth.scaled(synth.workload(WORKLOAD), 256, 192, 64)
+        prm = dataclasses.replace(w.params, jvp_mode=0, smoother_fp32=1)
+        dev = torch.device("cuda", 0)
+        h = pkg.Tusas(w.mesh, prm)
+        h.set_state(torch.tensor(synth.initial_state(w), device=dev), 0.0, w.dt)
+        st = h.step()
+        torch.cuda.synchronize()
+        print(json.dumps({"kernels": kind, "dofs": w.mesh.n_dofs, "gmres_its": st["gmres_its"]}))
+        h.close()
+        return
     if kind == "pc":
         w = synth.scaled(synth.workload(WORKLOAD), 256, 192, 64)
         dev = torch.device("cuda", 0)

@@ -325,11 +325,28 @@ __device__ __forceinline__ void gs_block_sum(const double* acc, int k, double* _
   }
 }
 
-// partials[b][j] of X_j . w
-template <int KM, int VEC>
+// Unrolled streaming: each thread takes UNR elements of its chunk per trip (stride GS_T) and
+// issues all their loads before the arithmetic, so UNR x (k + 1) 16-byte loads are in flight per
+// thread. On B300 these passes are bound by the FP64 pipe (2 DFMA per clock per SM: one FMA per
+// 8 bytes of basis read runs at most at 4.8 TB/s), so the vector count is a template argument:
+// predicated-off FMAs of a rounded-up count still occupy the pipe. KM = exact count when EXACT,
+// else an upper bound with k the runtime count.
+template <int KM> struct GsUnroll { static const int V = KM <= 4 ? 4 : (KM <= 8 ? 2 : 1); };
+
+template <int VEC>
+__device__ __forceinline__ typename Vec<VEC>::T gs_zero();
+template <>
+__device__ __forceinline__ double gs_zero<1>() { return 0.0; }
+template <>
+__device__ __forceinline__ double2 gs_zero<2>() { return make_double2(0.0, 0.0); }
+
+// pass 0: partials[b][j] of X_j . w
+template <int KM, int VEC, bool EXACT>
 __global__ void __launch_bounds__(GS_T) k_gs_dots(i64 nv, int k, const double* __restrict__ X, i64 ldv,
                                                   const double* __restrict__ w, double* __restrict__ partials) {
   typedef typename Vec<VEC>::T T;
+  constexpr int UNR = GsUnroll<KM>::V;
+  if (EXACT) k = KM;
   const T* Xv = reinterpret_cast<const T*>(X);
   const T* wv = reinterpret_cast<const T*>(w);
   double acc[KM];
@@ -338,98 +355,152 @@ __global__ void __launch_bounds__(GS_T) k_gs_dots(i64 nv, int k, const double* _
   const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < nv ? lo + chunk : nv;
-  for (i64 i = lo + threadIdx.x; i < hi; i += GS_T) {
-    const T wi = wv[i];
+  for (i64 i = lo + threadIdx.x; i < hi; i += (i64)GS_T * UNR) {
+    T wi[UNR], x[KM][UNR];
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) acc[j] = Vec<VEC>::dot(Xv[j * ldv + i], wi, acc[j]);
+    for (int u = 0; u < UNR; ++u) {
+      const i64 e = i + (i64)u * GS_T;
+      wi[u] = e < hi ? wv[e] : gs_zero<VEC>();
+#pragma unroll
+      for (int j = 0; j < KM; ++j) x[j][u] = ((EXACT || j < k) && e < hi) ? Xv[j * ldv + e] : gs_zero<VEC>();
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (EXACT || j < k) acc[j] = Vec<VEC>::dot(x[j][u], wi[u], acc[j]);
+    }
   }
   gs_block_sum<KM>(acc, k, partials);
 }
 
-// w -= sum_j c_j X_j, then partials[b][j] of X_j . w (the updated w)
-template <int KM, int VEC>
+// pass 1: w -= sum_j c_j X_j, then partials[b][j] of X_j . w (the updated w)
+template <int KM, int VEC, bool EXACT>
 __global__ void __launch_bounds__(GS_T) k_gs_update_dots(i64 nv, int k, const double* __restrict__ X, i64 ldv,
                                                          const double* __restrict__ c, double* __restrict__ w,
                                                          double* __restrict__ partials) {
   typedef typename Vec<VEC>::T T;
+  constexpr int UNR = GsUnroll<KM>::V;
+  if (EXACT) k = KM;
   const T* Xv = reinterpret_cast<const T*>(X);
   T* wv = reinterpret_cast<T*>(w);
   double cc[KM], acc[KM];
 #pragma unroll
   for (int j = 0; j < KM; ++j) {
-    cc[j] = j < k ? -c[j] : 0.0;
+    cc[j] = (EXACT || j < k) ? -c[j] : 0.0;
     acc[j] = 0.0;
   }
   const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < nv ? lo + chunk : nv;
-  for (i64 i = lo + threadIdx.x; i < hi; i += GS_T) {
-    T x[KM];
-    T wi = wv[i];
+  for (i64 i = lo + threadIdx.x; i < hi; i += (i64)GS_T * UNR) {
+    T wi[UNR], x[KM][UNR];
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) {
-        x[j] = Xv[j * ldv + i];
-        wi = Vec<VEC>::axpy(cc[j], x[j], wi);
-      }
-    wv[i] = wi;
+    for (int u = 0; u < UNR; ++u) {
+      const i64 e = i + (i64)u * GS_T;
+      wi[u] = e < hi ? wv[e] : gs_zero<VEC>();
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) acc[j] = Vec<VEC>::dot(x[j], wi, acc[j]);
+      for (int j = 0; j < KM; ++j) x[j][u] = ((EXACT || j < k) && e < hi) ? Xv[j * ldv + e] : gs_zero<VEC>();
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (EXACT || j < k) wi[u] = Vec<VEC>::axpy(cc[j], x[j][u], wi[u]);
+      const i64 e = i + (i64)u * GS_T;
+      if (e < hi) wv[e] = wi[u];
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (EXACT || j < k) acc[j] = Vec<VEC>::dot(x[j][u], wi[u], acc[j]);
+    }
   }
   gs_block_sum<KM>(acc, k, partials);
 }
 
-// w -= sum_j c_j X_j, then partials[b][0] of ||w||^2
-template <int KM, int VEC>
+// pass 2: w -= sum_j c_j X_j, then partials[b][0] of ||w||^2
+template <int KM, int VEC, bool EXACT>
 __global__ void __launch_bounds__(GS_T) k_gs_update_norm(i64 nv, int k, const double* __restrict__ X, i64 ldv,
                                                          const double* __restrict__ c, double* __restrict__ w,
                                                          double* __restrict__ partials) {
   typedef typename Vec<VEC>::T T;
+  constexpr int UNR = GsUnroll<KM>::V;
+  if (EXACT) k = KM;
   const T* Xv = reinterpret_cast<const T*>(X);
   T* wv = reinterpret_cast<T*>(w);
   double cc[KM];
 #pragma unroll
-  for (int j = 0; j < KM; ++j) cc[j] = j < k ? -c[j] : 0.0;
+  for (int j = 0; j < KM; ++j) cc[j] = (EXACT || j < k) ? -c[j] : 0.0;
   double acc[1] = {0.0};
   const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < nv ? lo + chunk : nv;
-  for (i64 i = lo + threadIdx.x; i < hi; i += GS_T) {
-    T wi = wv[i];
+  for (i64 i = lo + threadIdx.x; i < hi; i += (i64)GS_T * UNR) {
+    T wi[UNR], x[KM][UNR];
 #pragma unroll
-    for (int j = 0; j < KM; ++j)
-      if (j < k) wi = Vec<VEC>::axpy(cc[j], Xv[j * ldv + i], wi);
-    wv[i] = wi;
-    acc[0] = Vec<VEC>::dot(wi, wi, acc[0]);
+    for (int u = 0; u < UNR; ++u) {
+      const i64 e = i + (i64)u * GS_T;
+      wi[u] = e < hi ? wv[e] : gs_zero<VEC>();
+#pragma unroll
+      for (int j = 0; j < KM; ++j) x[j][u] = ((EXACT || j < k) && e < hi) ? Xv[j * ldv + e] : gs_zero<VEC>();
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (EXACT || j < k) wi[u] = Vec<VEC>::axpy(cc[j], x[j][u], wi[u]);
+      const i64 e = i + (i64)u * GS_T;
+      if (e < hi) wv[e] = wi[u];
+      acc[0] = Vec<VEC>::dot(wi[u], wi[u], acc[0]);
+    }
   }
   gs_block_sum<1>(acc, 1, partials);
 }
 
-template <int VEC>
-static cudaError_t gs_launch(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
-                             double* partials, cudaStream_t st) {
-  const i64 nv = n / VEC, ldv = ld / VEC;
-  const int g = GS_BLOCKS;
-#define TUSAS_GS(KM)                                                                              \
-  do {                                                                                            \
-    if (pass == 0)                                                                                \
-      k_gs_dots<KM, VEC><<<g, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);                         \
-    else if (pass == 1)                                                                           \
-      k_gs_update_dots<KM, VEC><<<g, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);               \
-    else                                                                                          \
-      k_gs_update_norm<KM, VEC><<<g, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);               \
-  } while (0)
-  if (k <= 4)
-    TUSAS_GS(4);
-  else if (k <= 8)
-    TUSAS_GS(8);
-  else if (k <= 16)
-    TUSAS_GS(16);
+template <int KM, int VEC, bool EXACT>
+static void gs_kernel(int pass, i64 nv, int k, const double* X, i64 ldv, const double* c, double* w,
+                      double* partials, cudaStream_t st) {
+  if (pass == 0)
+    k_gs_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);
+  else if (pass == 1)
+    k_gs_update_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
   else
-    TUSAS_GS(32);
-#undef TUSAS_GS
+    k_gs_update_norm<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
+}
+
+// 16-byte loads: one instantiation per vector count up to 16; rounded counts above (GMRES
+// cycles longer than 16 vectors) and for the scalar-load fallback.
+static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
+                                  double* partials, cudaStream_t st) {
+  const i64 nv = n / 2, ldv = ld / 2;
+  switch (k) {
+#define TUSAS_GS_K(K) \
+  case K:             \
+    gs_kernel<K, 2, true>(pass, nv, k, X, ldv, c, w, partials, st); \
+    break;
+    TUSAS_GS_K(1) TUSAS_GS_K(2) TUSAS_GS_K(3) TUSAS_GS_K(4) TUSAS_GS_K(5) TUSAS_GS_K(6) TUSAS_GS_K(7)
+    TUSAS_GS_K(8) TUSAS_GS_K(9) TUSAS_GS_K(10) TUSAS_GS_K(11) TUSAS_GS_K(12) TUSAS_GS_K(13) TUSAS_GS_K(14)
+    TUSAS_GS_K(15) TUSAS_GS_K(16)
+#undef TUSAS_GS_K
+    default:
+      if (k <= 24)
+        gs_kernel<24, 2, false>(pass, nv, k, X, ldv, c, w, partials, st);
+      else
+        gs_kernel<32, 2, false>(pass, nv, k, X, ldv, c, w, partials, st);
+  }
+  count_launches(1);
+  return cudaGetLastError();
+}
+
+static cudaError_t gs_launch_scalar(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
+                                    double* partials, cudaStream_t st) {
+  if (k <= 4)
+    gs_kernel<4, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+  else if (k <= 8)
+    gs_kernel<8, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+  else if (k <= 16)
+    gs_kernel<16, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+  else
+    gs_kernel<32, 1, false>(pass, n, k, X, ld, c, w, partials, st);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -446,8 +517,8 @@ cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const doubl
     if (e != cudaSuccess) return e;
     pass = 0;
   }
-  cudaError_t e = vec ? gs_launch<2>(pass, n, k, X, ld, c, w, partials, st)
-                      : gs_launch<1>(pass, n, k, X, ld, c, w, partials, st);
+  cudaError_t e = vec ? gs_launch_vec2(pass, n, k, X, ld, c, w, partials, st)
+                      : gs_launch_scalar(pass, n, k, X, ld, c, w, partials, st);
   if (e != cudaSuccess) return e;
   const int kout = pass == 2 ? 1 : k;
   k_reduce_partials<<<1, 32 * kout, 0, st>>>(GS_BLOCKS, kout, 32, partials, out);
