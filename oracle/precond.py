@@ -203,9 +203,10 @@ def q2_lattice(mesh):
     (bi)linear prolongation between the two is the exact embedding of the Q1
     space of the elements in their Q2 space, so the Galerkin product P^T A P of
     the assembled Q2 block is the Q1 operator with the Q2 quadrature
-    (9-point); the levels below are the Q1 hierarchy.
+    (9-point, 27-point for hexes); the levels below are the Q1 hierarchy.
     """
-    return dataclasses.replace(mesh, nx=2 * mesh.nx, ny=2 * mesh.ny, h=mesh.h / 2, order=1)
+    return dataclasses.replace(mesh, nx=2 * mesh.nx, ny=2 * mesh.ny, nz=2 * mesh.nz if mesh.dim == 3 else 0,
+                               h=mesh.h / 2, order=1)
 
 
 class Preconditioner:

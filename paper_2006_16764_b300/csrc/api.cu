@@ -126,10 +126,6 @@ int validate(const tusas_mesh* m, const tusas_params* p, std::string& why) {
     why = "order must be 0 or 1 (Q1) or 2 (Q2)";
     return TUSAS_EINVAL;
   }
-  if (m->order == 2 && m->dim == 3 && p && p->precond == 2) {
-    why = "triquadratic hexes take precond 0 or 1 (no multigrid on the 3D Q2 node lattice)";
-    return TUSAS_EINVAL;
-  }
   const int po = m->order == 2 ? 2 : 1;
   const double nodes = (double)(po * m->nx + 1) * (po * m->ny + 1) * (m->dim == 3 ? po * m->nz + 1 : 1);
   if (nodes > 2.0e9) {

@@ -58,6 +58,10 @@ cudaError_t elem_run(int mode, const ElemCtx& c, const double* U, const double* 
 cudaError_t q2_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
                    double* lin, cudaStream_t st, const double* phold);
 void q2_tables(Q2Tab& T, double h);
+// Stencils of the preconditioner blocks of a triquadratic box: [2][125][nn] on its node
+// lattice and, if stv, [2][27][nv] on its element-vertex grid (T = float or double).
+template <typename T>
+cudaError_t q2h_stencil_fill(const ElemCtx& c, const double* U, const double* Un, T* st, T* stv, cudaStream_t s);
 // The same pass on a 3D box of triquadratic (Q2) hexes with the 3 x 3 x 3 Gauss rule.
 cudaError_t q2h_run(int mode, const ElemCtx& c, const double* U, const double* Un, const double* V, double* out,
                     double* lin, cudaStream_t st, const double* phold);

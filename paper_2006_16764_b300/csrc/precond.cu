@@ -25,7 +25,7 @@ template <int DIM>
 struct Pow3 {
   static const int V = DIM == 2 ? 9 : 27;
 };
-// stencil of radius R: (2R + 1)^dim entries (R = 2 only for the 2D Q2 node lattice)
+// stencil of radius R: (2R + 1)^dim entries (R = 2 only on the Q2 node lattice)
 template <int DIM, int R>
 struct Sten {
   static const int W = 2 * R + 1;
@@ -479,6 +479,12 @@ __global__ void k_max_partials(int nb, const double* __restrict__ partials, doub
 #define TUSAS_SMOOTH_MINB 8
 #endif
 
+// the 125-point kernels of the hex lattice get a larger register budget (4 blocks per SM)
+template <int DIM, int R>
+struct SmoothMinB {
+  static const int V = (DIM == 3 && R == 2) ? 4 : TUSAS_SMOOTH_MINB;
+};
+
 template <typename T>
 struct Coef2 {
   T a[2], b[2];
@@ -486,7 +492,7 @@ struct Coef2 {
 
 // r = D^-1 (b - A x) (or D^-1 b if x == nullptr, and then x = 0); d = r * it
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
+__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -506,7 +512,7 @@ __global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_cheb_init(DevMesh m,
 
 // x += d; if !last: r -= D^-1 A d; dout = c1 d + c2 r
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
+__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -526,7 +532,7 @@ __global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_cheb_step(DevMesh m,
 }
 
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
+__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -542,7 +548,7 @@ __global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB) k_resid(DevMesh m, con
 // k_cheb_step, same arithmetic): r0 = D^-1 b, d0 = a0 r0, x = d0, r = r0 - D^-1 A d0,
 // dout = c1 d0 + c2 r (requires degree >= 2, so the first step is not the last).
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB)
+__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V))
     k_cheb_first(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                  T* __restrict__ x, T* __restrict__ r, T* __restrict__ dout, Coef2<T> it, Coef2<T> c) {
   constexpr int NS = Sten<DIM, R>::V;
@@ -566,7 +572,7 @@ __global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB)
 // Residual with the last Chebyshev update folded in: x' = x + p (p the pending
 // direction), res = b - A x', x' written to xout (a buffer other than x and p).
 template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, TUSAS_SMOOTH_MINB)
+__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V))
     k_resid_p(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
               const T* __restrict__ p, T* __restrict__ xout, T* __restrict__ res) {
   constexpr int NS = Sten<DIM, R>::V;
@@ -713,6 +719,8 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
     cur.order = 1;
     cur.nx = 2 * m.nx;
     cur.ny = 2 * m.ny;
+    if (m.dim == 3) cur.nz = 2 * m.nz;
+    cur.ne = (i64)cur.nx * cur.ny * (m.dim == 3 ? cur.nz : 1);
     cur.h = 0.5 * m.h;
   }
   for (int l = 0; l < nlev; ++l) {
@@ -720,7 +728,7 @@ cudaError_t Precond::create(const DevMesh& m, int kind_, int fp32_, int levels, 
     L.m = cur;
     L.nn = cur.nn;
     L.r = (l == 0 && m.order == 2) ? 2 : 1;
-    const int NS = L.r == 2 ? 25 : (m.dim == 3 ? 27 : 9);
+    const int NS = L.r == 2 ? (m.dim == 3 ? 125 : 25) : (m.dim == 3 ? 27 : 9);
     lv.push_back(L);  // allocated in place: destroy() frees a partly allocated level too
     PrecondLevel& Lb = lv.back();
     void** bufs[] = {&Lb.dinv, &Lb.b, &Lb.x, &Lb.r_, &Lb.d, &Lb.d2, &Lb.res};
@@ -767,8 +775,10 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
     return cudaGetLastError();
   }
   if (m.order == 2) {
-    // multigrid: 25-point stencils on the Q2 node lattice, then the Galerkin levels below
-    cudaError_t e = q2_stencil_fill<T>(c, U, Un, (T*)L0.st, st);
+    // multigrid: 25- or 125-point stencils on the Q2 node lattice, then the Galerkin levels
+    // below (for hexes the vertex level comes from the same fill)
+    cudaError_t e = m.dim == 3 ? q2h_stencil_fill<T>(c, U, Un, (T*)L0.st, lv.size() > 1 ? (T*)lv[1].st : nullptr, st)
+                               : q2_stencil_fill<T>(c, U, Un, (T*)L0.st, st);
     if (e != cudaSuccess) return e;
     return galerkin_and_bounds<T>(st);
   }
@@ -827,6 +837,7 @@ cudaError_t Precond::galerkin_and_bounds(cudaStream_t st) {
   for (size_t l = 1; l < lv.size(); ++l) {
     const PrecondLevel& F = lv[l - 1];
     const PrecondLevel& C = lv[l];
+    if (dim == 3 && F.r == 2) continue;  // the hex vertex level is filled with the lattice level
     if (dim == 3)
       k_rap<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.st, (T*)C.st);
     else if (F.r == 2)
@@ -837,7 +848,9 @@ cudaError_t Precond::galerkin_and_bounds(cudaStream_t st) {
   }
   for (size_t l = 0; l < lv.size(); ++l) {
     const int nb = grid_nodes(lv[l].nn);
-    if (dim == 3)
+    if (dim == 3 && lv[l].r == 2)
+      k_gersh<3, T, 2><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
+    else if (dim == 3)
       k_gersh<3, T><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
     else if (lv[l].r == 2)
       k_gersh<2, T, 2><<<nb, 256, 0, st>>>(lv[l].m, (const T*)lv[l].st, (T*)lv[l].dinv, gersh_partials);
@@ -901,7 +914,9 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   int k0 = 0;
   if (fuse && zero_x && degree >= 2) {  // zero start: initialisation and first step in one pass
     next_coef();
-    if (d3)
+    if (d3 && L.r == 2)
+      k_cheb_first<3, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
+    else if (d3)
       k_cheb_first<3, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
     else if (L.r == 2)
       k_cheb_first<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
@@ -911,7 +926,9 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
     std::swap(dcur, dnext);
     k0 = 1;
   } else {
-    if (d3)
+    if (d3 && L.r == 2)
+      k_cheb_init<3, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
+    else if (d3)
       k_cheb_init<3, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
     else if (L.r == 2)
       k_cheb_init<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
@@ -926,7 +943,9 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
       break;
     }
     next_coef();
-    if (d3)
+    if (d3 && L.r == 2)
+      k_cheb_step<3, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
+    else if (d3)
       k_cheb_step<3, T><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
     else if (L.r == 2)
       k_cheb_step<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
@@ -952,7 +971,9 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   if (F.pend) {  // residual of x + pending direction; the updated x goes to the free direction buffer
     void** xo = F.pend == F.d ? &F.d2 : &F.d;
     const T *X = (const T*)F.x, *P = (const T*)F.pend;
-    if (d3)
+    if (d3 && F.r == 2)
+      k_resid_p<3, T, 2><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
+    else if (d3)
       k_resid_p<3, T><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
     else if (F.r == 2)
       k_resid_p<2, T, 2><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
@@ -961,7 +982,9 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
     std::swap(F.x, *xo);
     F.pend = nullptr;
   } else {
-    if (d3)
+    if (d3 && F.r == 2)
+      k_resid<3, T, 2><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
+    else if (d3)
       k_resid<3, T><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
     else if (F.r == 2)
       k_resid<2, T, 2><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);

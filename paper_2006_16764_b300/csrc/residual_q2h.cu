@@ -63,11 +63,12 @@ struct Q2HTab {
 
 // Value (and gradient) at Gauss point (i0, i1, i2) of the field staged at sN, element
 // corner node `nb` of the tile (see the file comment). Warp-uniform call.
-template <bool GRAD>
+// SY, SZ: strides of the staged node array along y and z (the tile's, by default).
+template <bool GRAD, int SY = HNX, int SZ = HNX * HNY>
 __device__ __forceinline__ void q2h_interp(const Q2HTab& T, const double* sN, int nb, int i0, int i1, int i2,
                                            double& val, double* grad) {
   // x: Gauss point i0 of the node row (y = i1, z = i2)
-  const double* np = sN + nb + HNX * (i1 + HNY * i2);
+  const double* np = sN + nb + SY * i1 + SZ * i2;
   const double n0 = np[0], n1 = np[1], n2 = np[2];
   const double xv = fma(T.B[i0][2], n2, fma(T.B[i0][1], n1, T.B[i0][0] * n0));
   const double xd = GRAD ? fma(T.G[i0][2], n2, fma(T.G[i0][1], n1, T.G[i0][0] * n0)) : 0.0;
@@ -381,5 +382,207 @@ cudaError_t q2h_run(int mode, const ElemCtx& c, const double* U, const double* U
   a.ctx = a.cty = a.ctz = 0;
   return c.P.model == 0 ? q2h_dispatch<0>(mode, c, a, st) : q2h_dispatch<1>(mode, c, a, st);
 }
+
+
+// ---------------------------------------------------------------------------
+// Preconditioner blocks M11, M22 (Eqs. pref2, preconc2) of a triquadratic box for
+// the multigrid: 125-point stencils [2][125][nn] on its node lattice (spacing h/2),
+// and 27-point stencils [2][27][nv] on the grid of element vertices. The vertex
+// level is P^T A P for the trilinear prolongation, which embeds the trilinear space
+// of each element exactly in its triquadratic one, so it is built directly as the
+// trilinear element matrices with the same 27 Gauss-point coefficients (the
+// Galerkin product without the 125 x 27 contraction). One warp per element, lanes =
+// Gauss points for the coefficients, then lane a sums row a of the element matrix
+// (and lanes 0..7 the trilinear rows) and adds it to the stencil rows of its node.
+// Elements run in 8 colours (index parity per axis): elements of one colour share no
+// node, so the read-modify-writes of a launch never collide, and the colours run in
+// a fixed order (deterministic). Arithmetic of the sums in the stencil precision T.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Q2HFillArgs {
+  DevMesh m;   // the Q2 mesh
+  DevPhys P;
+  Q2Tab Tb;
+  const double* U;
+  const double* Un;
+  T* st;       // lattice stencils [2][125][nn], zeroed before the first colour
+  T* stv;      // vertex-grid stencils [2][27][nv], zeroed, or null
+  int nvx, nvy;  // vertex grid nodes per axis (nx + 1, ny + 1)
+  i64 nv;
+  int color;
+  int ncx, ncy;  // elements of this colour per axis (x, y)
+  int ncol;      // elements of this colour
+};
+
+template <int MODEL, typename T>
+__global__ void __launch_bounds__(128) k_q2h_stencil_fill(const Q2HFillArgs<T> A) {
+  constexpr int W = 4;  // warps (elements) per CTA
+  __shared__ Q2HTab sT;
+  __shared__ T sN[27][27], sGx[27][27], sGy[27][27], sGz[27][27];  // [g][b] Q2 basis, physical gradient
+  __shared__ T sN1[27][8], sG1x[27][8], sG1y[27][8], sG1z[27][8];  // trilinear basis of the vertices
+  __shared__ double sNod[W][3][27];                                 // phi, u, phi^n of the element nodes
+  __shared__ T sC[W][4][27];                                         // weighted coefficients per Gauss point
+  const DevMesh& m = A.m;
+  const DevPhys& P = A.P;
+  for (int t = threadIdx.x; t < 27 * 27; t += blockDim.x) {
+    const int g = t / 27, b = t % 27;
+    const int gx = g % 3, gy = (g / 3) % 3, gz = g / 9, bx = b % 3, by = (b / 3) % 3, bz = b / 9;
+    const Q2Tab& Q = A.Tb;
+    sN[g][b] = T(Q.B[gx][bx] * Q.B[gy][by] * Q.B[gz][bz]);
+    sGx[g][b] = T(Q.G[gx][bx] * Q.B[gy][by] * Q.B[gz][bz]);
+    sGy[g][b] = T(Q.B[gx][bx] * Q.G[gy][by] * Q.B[gz][bz]);
+    sGz[g][b] = T(Q.B[gx][bx] * Q.B[gy][by] * Q.G[gz][bz]);
+    if (b < 8) {
+      const int vx = b & 1, vy = (b >> 1) & 1, vz = b >> 2;
+      const double xs[3] = {Q.xg[gx], Q.xg[gy], Q.xg[gz]};
+      const int v[3] = {vx, vy, vz};
+      double l[3], dl[3];
+      for (int d = 0; d < 3; ++d) {
+        l[d] = v[d] ? xs[d] : 1.0 - xs[d];
+        dl[d] = (v[d] ? 1.0 : -1.0) / m.h;
+      }
+      sN1[g][b] = T(l[0] * l[1] * l[2]);
+      sG1x[g][b] = T(dl[0] * l[1] * l[2]);
+      sG1y[g][b] = T(l[0] * dl[1] * l[2]);
+      sG1z[g][b] = T(l[0] * l[1] * dl[2]);
+    }
+  }
+  if (threadIdx.x < 9) {
+    const int g = threadIdx.x / 3, a = threadIdx.x % 3;
+    sT.B[g][a] = A.Tb.B[g][a];
+    sT.G[g][a] = A.Tb.G[g][a];
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int l = lane < 27 ? lane : 26;
+  const int i0 = l % 3, i1 = (l / 3) % 3, i2 = l / 9;
+  const int eid = blockIdx.x * W + w;
+  const bool valid = eid < A.ncol;  // uniform across the warp
+  const int ci = valid ? eid % A.ncx : 0, cj = valid ? (eid / A.ncx) % A.ncy : 0,
+            ck = valid ? eid / (A.ncx * A.ncy) : 0;
+  const int ex = 2 * ci + (A.color & 1), ey = 2 * cj + ((A.color >> 1) & 1), ez = 2 * ck + ((A.color >> 2) & 1);
+  const i64 node = (2 * ex + i0) + (i64)m.nnx * ((2 * ey + i1) + (i64)m.nny * (2 * ez + i2));
+  if (valid && lane < 27) {
+    sNod[w][0][lane] = A.U[node];
+    sNod[w][1][lane] = A.U[m.nn + node];
+    sNod[w][2][lane] = A.Un[node];
+  }
+  __syncthreads();
+  if (!valid) return;
+  // Gauss-point coefficients (lane = Gauss point), weights included
+  {
+    double phi, u, phin, p[3], gu[3];
+    q2h_interp<true, 3, 9>(sT, &sNod[w][0][0], 0, i0, i1, i2, phi, p);
+    q2h_interp<false, 3, 9>(sT, &sNod[w][1][0], 0, i0, i1, i2, u, gu);
+    q2h_interp<false, 3, 9>(sT, &sNod[w][2][0], 0, i0, i1, i2, phin, nullptr);
+    Aniso<3> An;
+    An.eval(p, P.eps4);
+    const double a2 = An.a * An.a;
+    const double B = fma(1.0 - P.k, u, 1.0);
+    const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - (1.0 - P.k) * phin);
+    const double q = MODEL == 0 ? 1.0 : 0.5 * (1.0 - phi);
+    const double wg = (5.0 + 3.0 * (i0 == 1)) * (5.0 + 3.0 * (i1 == 1)) * (5.0 + 3.0 * (i2 == 1)) / 5832.0 *
+                      m.h * m.h * m.h;  // (5/18 or 8/18)^3 h^3
+    if (lane < 27) {
+      sC[w][0][lane] = T(wg * P.tau0 * B * a2 * P.idt);
+      sC[w][1][lane] = T(wg * P.thW2 * a2);
+      sC[w][2][lane] = T(wg * Acoef * P.idt);
+      sC[w][3][lane] = T(wg * P.thD * q);
+    }
+  }
+  __syncwarp();
+  // row a = lane of the triquadratic element matrices of both blocks
+  if (lane < 27) {
+    const int a = lane;
+    T acc0[27], acc1[27];
+#pragma unroll
+    for (int b = 0; b < 27; ++b) acc0[b] = acc1[b] = T(0);
+#pragma unroll 1
+    for (int g = 0; g < 27; ++g) {
+      const T na = sN[g][a], xa = sGx[g][a], ya = sGy[g][a], za = sGz[g][a];
+      const T m0 = sC[w][0][g] * na, k0 = sC[w][1][g], m1 = sC[w][2][g] * na, k1 = sC[w][3][g];
+      const T k0x = k0 * xa, k0y = k0 * ya, k0z = k0 * za, k1x = k1 * xa, k1y = k1 * ya, k1z = k1 * za;
+#pragma unroll
+      for (int b = 0; b < 27; ++b) {
+        const T nb = sN[g][b], xb = sGx[g][b], yb = sGy[g][b], zb = sGz[g][b];
+        acc0[b] += m0 * nb + k0x * xb + k0y * yb + k0z * zb;
+        acc1[b] += m1 * nb + k1x * xb + k1y * yb + k1z * zb;
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < 27; ++b) {
+      const int o = (b % 3 - i0 + 2) + 5 * ((b / 3) % 3 - i1 + 2) + 25 * (b / 9 - i2 + 2);
+      A.st[(i64)o * m.nn + node] += acc0[b];
+      A.st[(i64)(125 + o) * m.nn + node] += acc1[b];
+    }
+  }
+  // vertex rows of the trilinear element matrices (lanes 0..7)
+  if (A.stv && lane < 8) {
+    const int vx = lane & 1, vy = (lane >> 1) & 1, vz = lane >> 2;
+    T acc0[8], acc1[8];
+#pragma unroll
+    for (int b = 0; b < 8; ++b) acc0[b] = acc1[b] = T(0);
+#pragma unroll 1
+    for (int g = 0; g < 27; ++g) {
+      const T na = sN1[g][lane], xa = sG1x[g][lane], ya = sG1y[g][lane], za = sG1z[g][lane];
+      const T m0 = sC[w][0][g] * na, k0 = sC[w][1][g], m1 = sC[w][2][g] * na, k1 = sC[w][3][g];
+#pragma unroll
+      for (int b = 0; b < 8; ++b) {
+        const T gd = xa * sG1x[g][b] + ya * sG1y[g][b] + za * sG1z[g][b];
+        acc0[b] += m0 * sN1[g][b] + k0 * gd;
+        acc1[b] += m1 * sN1[g][b] + k1 * gd;
+      }
+    }
+    const i64 vnode = (ex + vx) + (i64)A.nvx * ((ey + vy) + (i64)A.nvy * (ez + vz));
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const int o = ((b & 1) - vx + 1) + 3 * (((b >> 1) & 1) - vy + 1) + 9 * ((b >> 2) - vz + 1);
+      A.stv[(i64)o * A.nv + vnode] += acc0[b];
+      A.stv[(i64)(27 + o) * A.nv + vnode] += acc1[b];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t q2h_stencil_fill(const ElemCtx& c, const double* U, const double* Un, T* st, T* stv, cudaStream_t s) {
+  const DevMesh& m = c.m;
+  if (m.dim != 3 || m.order != 2) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(st, 0, sizeof(T) * 2 * 125 * (size_t)m.nn, s);
+  if (e != cudaSuccess) return e;
+  Q2HFillArgs<T> a;
+  a.m = m;
+  a.P = c.P;
+  a.Tb = c.q2;
+  a.U = U;
+  a.Un = Un;
+  a.st = st;
+  a.stv = stv;
+  a.nvx = m.nx + 1;
+  a.nvy = m.ny + 1;
+  a.nv = (i64)(m.nx + 1) * (m.ny + 1) * (m.nz + 1);
+  if (stv) {
+    e = cudaMemsetAsync(stv, 0, sizeof(T) * 2 * 27 * (size_t)a.nv, s);
+    if (e != cudaSuccess) return e;
+  }
+  for (int col = 0; col < 8; ++col) {
+    const int cx = col & 1, cy = (col >> 1) & 1, cz = (col >> 2) & 1;
+    a.color = col;
+    a.ncx = (m.nx - cx + 1) / 2;
+    a.ncy = (m.ny - cy + 1) / 2;
+    const int ncz = (m.nz - cz + 1) / 2;
+    a.ncol = a.ncx * a.ncy * ncz;
+    if (a.ncol <= 0) continue;
+    const int blocks = (a.ncol + 3) / 4;
+    if (c.P.model == 0)
+      k_q2h_stencil_fill<0, T><<<blocks, 128, 0, s>>>(a);
+    else
+      k_q2h_stencil_fill<1, T><<<blocks, 128, 0, s>>>(a);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+template cudaError_t q2h_stencil_fill<float>(const ElemCtx&, const double*, const double*, float*, float*,
+                                             cudaStream_t);
+template cudaError_t q2h_stencil_fill<double>(const ElemCtx&, const double*, const double*, double*, double*,
+                                              cudaStream_t);
 
 }  // namespace tusas

@@ -65,7 +65,7 @@ def test_invalid_arguments_fail_without_gpu_work():
 
 
 def test_mesh_validation_rejects_bad_orders_before_gpu_work():
-    """order must be 0/1 (Q1) or 2 (Q2); no multigrid for triquadratic hexes; precond in 0..2."""
+    """order must be 0/1 (Q1) or 2 (Q2); precond in 0..2."""
     import ctypes
 
     import paper_2006_16764_b300 as pkg
@@ -73,7 +73,7 @@ def test_mesh_validation_rejects_bad_orders_before_gpu_work():
 
     lib = pkg.lib()
     h = ctypes.c_void_p()
-    for mesh, prm in [(Mesh(3, 4, 4, 4, 1.0, order=2), Params(precond=2)),
+    for mesh, prm in [(Mesh(3, 4, 4, 4, 1.0, order=3), Params(precond=1)),
                       (Mesh(2, 4, 4, 0, 1.0, order=3), Params(precond=1)),
                       (Mesh(2, 4, 4, 0, 1.0, order=2), Params(precond=3))]:
         cm, cp = pkg.make_mesh(mesh), pkg.make_params(prm)

@@ -2,7 +2,8 @@
 
 Same bars as the Q1 and 2D Q2 parity tests: residual, tangent, adjoint,
 (dF/dU^n)^T w and dF/d eps4 within 1e-12 normwise relative; point Jacobi within
-1e-13 (FP64) or 1e-7 (FP32 reciprocal); converged time steps within 1e-8.
+1e-13 (FP64) or 1e-7 (FP32 reciprocal); multigrid within 1e-10 (FP64) or 2e-4
+(FP32); converged time steps within 1e-8.
 Meshes are ragged against the 4 x 2 x 2 element tile and include a single
 element.
 """
@@ -106,6 +107,28 @@ def test_q2_hex_jacobi_matches_oracle(prm, fp32, tol):
     assert rel(host(z), want) <= tol
 
 
+@pytest.mark.parametrize("prm", [PURE, ALLOY], ids=["pure", "alloy"])
+@pytest.mark.parametrize("fp32,tol", [(0, 1e-10), (1, 2e-4)])
+@pytest.mark.parametrize("dims", [(6, 4, 4), (3, 5, 1), (1, 1, 1)], ids=["6x4x4", "3x5x1", "1x1x1"])
+def test_q2_hex_multigrid_matches_oracle(prm, fp32, tol, dims):
+    """Block Jacobi + multigrid for triquadratic hexes: 125-point stencils on the h/2 node
+    lattice, the element-vertex level (the Galerkin product, filled directly from the same
+    Gauss-point coefficients) and the trilinear levels below."""
+    mesh = Mesh(3, dims[0], dims[1], dims[2], 0.8, order=2)
+    prm = dataclasses.replace(prm, precond=2, smoother_fp32=fp32, mg_levels=4, cheb_degree=3)
+    U, Un = synth.random_fields(mesh, 21)
+    Un = 0.5 * Un
+    U = 0.5 * U
+    h = handle(mesh, prm)
+    h.set_state(dev(Un), 0.0, 0.3)
+    h.precond_setup(dev(U))
+    r = synth.random_vector(mesh, 11)
+    z = dev(np.zeros_like(r))
+    h.precond_apply(dev(r), z)
+    want = OP.Preconditioner(mesh, prm, U, Un, 0.3).apply(r)
+    assert rel(host(z), want) <= tol
+
+
 def test_q2_hex_residual_and_tangent_are_bitwise_deterministic():
     mesh = Mesh(3, 13, 7, 6, 0.8, order=2)
     U, Un = synth.random_fields(mesh, 3)
@@ -127,6 +150,7 @@ HEX_STEPS = [
     ("pure-exact", PURE, dict(jvp_mode=1)),
     ("pure-fd", PURE, dict(jvp_mode=0)),
     ("alloy-exact-fp32", ALLOY, dict(jvp_mode=1, smoother_fp32=1)),
+    ("pure-exact-gmg-fp32", PURE, dict(jvp_mode=1, precond=2, smoother_fp32=1, cheb_degree=3, gmres_maxit=30)),
 ]
 
 

@@ -230,3 +230,32 @@ def test_q2_hex_sampled_node_residual_matches_full_residual():
     rp, ru = R.residual_at_nodes(mesh, prm, U, Un, 0.4, 0.3, nodes)
     assert np.abs(rp - F[nodes]).max() <= 1e-13 * np.abs(F).max()
     assert np.abs(ru - F[n + nodes]).max() <= 1e-13 * np.abs(F).max()
+
+
+def test_q2_hex_multigrid_hierarchy():
+    """Triquadratic blocks on the h/2 node lattice: the first Galerkin product is the trilinear
+    operator of the element vertices (exact embedding of Q1 in Q2; for the pure metal M22 is
+    (1/dt) M + theta D K, so the product equals the textbook Q1 matrices), and the V-cycle
+    contracts as a stationary iteration."""
+    from oracle import precond as P
+
+    mesh = Mesh(3, 4, 2, 4, 0.7, order=2)
+    prm = Params(model=0, eps4=0.05, lam=3.19, D=2.0, precond=2)
+    U, Un = synth.random_fields(mesh, 5)
+    U, Un = 0.3 * U, 0.3 * Un
+    M11, M22 = P.blocks(mesh, prm, U, Un, 0.4)
+    lat = P.q2_lattice(mesh)
+    assert lat.n_nodes == mesh.n_nodes
+    Pm = P.prolongation(lat)
+    q1 = Mesh(3, 4, 2, 4, 0.7)
+    Mc = (Pm.T @ M22 @ Pm).tocsr()
+    Kq1 = tb.mass(q1) / 0.4 + prm.theta * prm.D * tb.stiffness(q1)
+    assert abs(Mc - Kq1).max() <= 1e-13 * abs(Kq1).max()
+    rng = np.random.default_rng(0)
+    b = rng.standard_normal(mesh.n_nodes)
+    r0 = np.linalg.norm(b)
+    H = P.Hierarchy(lat, M11, 3, cheb_degree=3)
+    x = np.zeros_like(b)
+    for _ in range(10):
+        x = x + H.vcycle(b - M11 @ x)
+    assert np.linalg.norm(b - M11 @ x) < 1e-4 * r0
