@@ -430,14 +430,19 @@ def run_report(name):
             dl = 0.45 + 0.30 * r[2 * i + 1]
             te = torch.tensor(e4, dtype=torch.float64, requires_grad=True)
             td = torch.tensor(dl, dtype=torch.float64, requires_grad=True)
+            h.timers(True)
             t0 = time.perf_counter()
             S = SolidFraction.apply(te, td, pb)
             t1 = time.perf_counter()
             ge, gd = torch.autograd.grad(S, (te, td))
             t2 = time.perf_counter()
+            tm = h.get_timers()
+            h.timers(False)
             samples.append({"eps4": e4, "Delta": dl, "S": float(S), "dS_deps4": float(ge), "dS_dDelta": float(gd),
                             "forward_s": t1 - t0, "adjoint_s": t2 - t1,
-                            "forward_gmres": pb.last_forward["gmres_its"], "adjoint_gmres": pb.last_adjoint["gmres_its"]})
+                            "forward_gmres": pb.last_forward["gmres_its"], "adjoint_gmres": pb.last_adjoint["gmres_its"],
+                            # device time of the operator classes (CUDA events around each application)
+                            "operator_device_s": sum(v[0] for v in tm.values()) / 1e3})
         out["samples"] = samples
         # the same 8 samples at once: 8 handles on 8 streams, one host thread each
         from paper_2006_16764_b300.adjoint import solid_fraction_batch
@@ -450,9 +455,12 @@ def run_report(name):
                 w.steps, 10, 1e-12, stream=s_))
         sam = [(x["eps4"], x["Delta"]) for x in samples]
         solid_fraction_batch(probs[:1], sam[:1])  # allocate the first handle's checkpoints outside the timing
+        util = UtilSampler(0)
+        util.start()
         t0 = time.perf_counter()
         res = solid_fraction_batch(probs, sam)
         t1 = time.perf_counter()
+        out["batch_gpu_utilization"] = util.stop()
         out["batch_of_8"] = {
             "seconds": t1 - t0,
             "sequential_seconds": sum(x["forward_s"] + x["adjoint_s"] for x in samples),
@@ -570,6 +578,39 @@ class OraclePool:
     def close(self):
         self.pool.close()
         self.pool.join()
+
+
+class UtilSampler:
+    """nvidia-smi utilization.gpu (percent of the sample period with a kernel running) every 100 ms."""
+
+    def __init__(self, index):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=utilization.gpu",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=lambda: self.rows.extend(line.strip() for line in self.proc.stdout),
+                                       daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=2)
+        v = [float(r) for r in self.rows if r.replace(".", "").isdigit()]
+        return {"samples": len(v), "mean_pct": statistics.mean(v) if v else None,
+                "median_pct": statistics.median(v) if v else None}
 
 
 class ClockSampler:
