@@ -45,6 +45,10 @@ CPU_SAMPLE = (48, 48, 32)
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over the 8
 # colour launches of one pass on the 256x192x64 alloy box / its elements).
 FP64_FLOPS_PER_ELEM = {"residual": 1127.3, "residual_lin": 1910.3, "jv": 802.7}
+# FP64 instructions per element (DADD + DMUL + DFMA, same counts): each occupies the FP64
+# pipe for one issue slot, so against the FMA issue rate (peak FLOP/s / 2) they give the
+# pipe's issue fraction; the FLOP fraction is lower where DADD / DMUL carry one flop.
+FP64_INSTR_PER_ELEM = {"residual": 812.1, "residual_lin": 1423.1, "jv": 496.3}
 # Algorithmic HBM bytes per node of the method's operators: F reads U, U^n and
 # writes F (6 doubles); J v also reads v (8 doubles). Coordinates are implicit.
 ALG_BYTES_PER_NODE = {"residual": 48.0, "residual_lin": 48.0, "jv": 64.0}
@@ -864,7 +868,8 @@ def run_ours(args, ws, rank, local):
         "kernel": "res3_kernel<1,0> (3D alloy residual), one evaluation = 8 colour launches",
         "fp64": {"achieved_tflops": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / 1e12,
                  "peak_tflops": fp64_peak / 1e12,
-                 "frac": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / fp64_peak},
+                 "frac": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / fp64_peak,
+                 "issue_frac": FP64_INSTR_PER_ELEM["residual"] * ne / (res_per * 1e-3) / (fp64_peak / 2)},
         "hbm": {"algorithmic_bytes": ALG_BYTES_PER_NODE["residual"] * nn,
                 "achieved_gbs": ALG_BYTES_PER_NODE["residual"] * nn / (res_per * 1e-3) / 1e9,
                 "peak_gbs": hbm_peak, "peak_kind": hbm_kind},
@@ -884,6 +889,7 @@ def run_ours(args, ws, rank, local):
             + ", one operator application = 8 colour launches",
             "launch_ms": per_launch, "launches": d_cnt,
             "peak_kind": "FP64 FMA-chain throughput measured in this run (tusas_fma_peak)",
+            "fp64_issue_frac": FP64_INSTR_PER_ELEM[dom] * ne / (per_launch * 1e-3) / (fp64_peak / 2),
             "hbm": {"algorithmic_bytes": alg_bytes, "achieved_gbs": alg_bytes / (per_launch * 1e-3) / 1e9,
                     "peak_gbs": hbm_peak, "peak_kind": hbm_kind,
                     "basis": "nodal vectors only (48 B/node for F, 64 B/node for J v)"},
@@ -925,22 +931,45 @@ def run_ours(args, ws, rank, local):
     # ---- end to end through the C-ABI with pinned host buffers ----
     e2e = None
     if args.e2e_steps > 0:
-        # the headline metric: H2D of U, residual, D2H of F per evaluation
-        Uh = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        Fh = torch.empty(N, dtype=torch.float64, pin_memory=True)
-        Uh.copy_(Ut.cpu())
-        Ud = torch.empty_like(U0)
+        # the headline metric: per evaluation, H2D of its U from pinned host memory, the
+        # residual, D2H of its F to pinned host memory. Double-buffered on three streams
+        # (copy in, compute on the handle's stream, copy out): evaluation i computes while
+        # the input of i + 1 and the output of i - 1 move, as a stream of evaluations would.
+        Uh = [torch.empty(N, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        Fh = [torch.empty(N, dtype=torch.float64, pin_memory=True) for _ in range(2)]
+        for b in range(2):
+            Uh[b].copy_(Ut.cpu())
+        Ud = [torch.empty_like(U0) for _ in range(2)]
+        Fd = [torch.empty_like(U0) for _ in range(2)]
+        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+        ev_in = [torch.cuda.Event() for _ in range(args.steps)]
+        ev_c = [torch.cuda.Event() for _ in range(args.steps)]
+        ev_out = [torch.cuda.Event() for _ in range(args.steps)]
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.steps):
-            Ud.copy_(Uh, non_blocking=True)
-            h.residual(Ud, F)
-            Fh.copy_(F, non_blocking=True)
-            torch.cuda.synchronize(dev)
+        for i in range(args.steps):
+            b = i % 2
+            if i >= 2:
+                s_in.wait_event(ev_c[i - 2])  # Ud[b] is free once evaluation i - 2 is done
+            with torch.cuda.stream(s_in):
+                Ud[b].copy_(Uh[b], non_blocking=True)
+            ev_in[i].record(s_in)
+            stream.wait_event(ev_in[i])
+            if i >= 2:
+                stream.wait_event(ev_out[i - 2])  # Fd[b] is free once copied out
+            h.residual(Ud[b], Fd[b])
+            ev_c[i].record(stream)
+            s_out.wait_event(ev_c[i])
+            with torch.cuda.stream(s_out):
+                Fh[b].copy_(Fd[b], non_blocking=True)
+            ev_out[i].record(s_out)
+        torch.cuda.synchronize(dev)
         el = time.perf_counter() - t0
+        ok = bool(torch.equal(Fh[(args.steps - 1) % 2], F.cpu()))  # same state, bitwise the same F
         e2e = {"value": args.steps * N / el / 1e6, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
-               "d2h_bytes_per_step": 8 * N, "steps": args.steps,
-               "what": "tusas_residual from pinned host U to pinned host F, host clock"}
+               "d2h_bytes_per_step": 8 * N, "steps": args.steps, "output_matches_device_run": ok,
+               "what": "tusas_residual from pinned host U to pinned host F, host clock, copies of "
+                       "neighbouring evaluations overlapped with compute (double-buffered, 3 streams)"}
         # the time step end to end: state in, step, state out
         Sh = torch.empty(N, dtype=torch.float64, pin_memory=True)
         Sh.copy_(Ustart.cpu())

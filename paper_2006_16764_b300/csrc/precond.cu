@@ -274,6 +274,35 @@ __device__ __forceinline__ bool node3b(const DevMesh& m, int& ix, int& iy, int& 
   return true;
 }
 
+// 27-point sum of a 3D radius-1 stencil with 32-bit offsets from the node (for levels whose
+// 27 x nn coefficient index fits an int). Used for every node whose y and z neighbours exist
+// (fast27), including the first and last node of an x-row: there the x-neighbour index wraps
+// to the adjacent row, a valid address whose coefficient is exactly zero (the fine fill and
+// the Galerkin products give zero entries towards nodes outside the box), so the product adds
+// +0 and the sum is that of the generic loop. Only rows on a y or z face take the loop with
+// bounds tests, so warps along x no longer run both paths.
+// Whether every neighbour index node + ox + sy oy + sz oz (|o| <= 1) lies in [0, nn): y and z
+// neighbours exist, and the two extreme offsets stay inside the array (they fail only at the
+// first and last node of the box's second / second-to-last row and layer).
+__device__ __forceinline__ bool fast27(const DevMesh& m, int iy, int iz, i64 node, i64 sy, i64 sz) {
+  return iy >= 1 && iy < m.nny - 1 && iz >= 1 && iz < m.nnz - 1 && node - 1 - sy - sz >= 0 &&
+         node + 1 + sy + sz < m.nn && m.nn * 27 < (i64)0x7fffffff;
+}
+
+template <typename T, typename V>
+__device__ __forceinline__ T stencil27_i32(const T* __restrict__ st, int nn, int node, int sy, int sz, V val) {
+  const T* sp = st + node;
+  T s = T(0);
+#pragma unroll
+  for (int o = 0; o < 27; ++o) {
+    const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = o / 9 - 1;
+    const int off = ox + sy * oy + sz * oz;
+    const T a = o < 13 ? __ldg(sp + ((26 - o) * nn + off)) : __ldg(sp + o * nn);
+    s += a * val(off);
+  }
+  return s;
+}
+
 // sum_o A[o] x[node + o] in offset order; interior nodes skip the bounds tests
 template <int DIM, typename T, int R = 1>
 __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __restrict__ x, const DevMesh& m, i64 node,
@@ -283,6 +312,10 @@ __device__ __forceinline__ T stencil_apply(const T* __restrict__ st, const T* __
   T s = T(0);
   const bool interior = ix >= R && ix < m.nnx - R && iy >= R && iy < m.nny - R &&
                         (DIM == 2 || (iz >= R && iz < m.nnz - R));
+  if (DIM == 3 && R == 1 && fast27(m, iy, iz, node, sy, sz)) {
+    const T* xp = x + node;
+    return stencil27_i32<T>(st, (int)m.nn, (int)node, (int)sy, (int)sz, [&](int off) { return __ldg(xp + off); });
+  }
   if (interior) {
 #pragma unroll
     for (int o = 0; o < NS; ++o) {
@@ -317,6 +350,8 @@ __device__ __forceinline__ T stencil_apply_f(const T* __restrict__ st, const Dev
   T s = T(0);
   const bool interior = ix >= R && ix < m.nnx - R && iy >= R && iy < m.nny - R &&
                         (DIM == 2 || (iz >= R && iz < m.nnz - R));
+  if (DIM == 3 && R == 1 && fast27(m, iy, iz, node, sy, sz))
+    return stencil27_i32<T>(st, (int)m.nn, (int)node, (int)sy, (int)sz, [&](int off) { return val(node + off); });
   if (interior) {
 #pragma unroll
     for (int o = 0; o < NS; ++o) {
