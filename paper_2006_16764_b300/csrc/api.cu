@@ -33,6 +33,7 @@ struct tusas_handle {
   int m = 0;  // restart length the basis was allocated for
   double* partials = nullptr;
   double* sc = nullptr;  // device scalars: [0..63] h1, [64..127] h2, [128..191] y, [192..] misc
+  double* hess = nullptr;  // GMRES Hessenberg H [(m+1) x m], Givens cs, sn [m], g [m+1], status [4]
   tusas::Precond pc;
   bool pc_ready = false;
   std::string err;
@@ -318,7 +319,8 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
       tusas::dev_malloc(&h->Z, sizeof(double) * h->N * h->m) != cudaSuccess ||
       tusas::dev_malloc(&h->partials, sizeof(double) * std::max(tusas::reduce_blocks(), tusas::gs_blocks()) * 32) !=
           cudaSuccess ||
-      tusas::dev_malloc(&h->sc, sizeof(double) * 256) != cudaSuccess) {
+      tusas::dev_malloc(&h->sc, sizeof(double) * 256) != cudaSuccess ||
+      tusas::dev_malloc(&h->hess, sizeof(double) * ((h->m + 1) * h->m + 3 * h->m + 8)) != cudaSuccess) {
     tusas_destroy(h);
     return TUSAS_ENOMEM;
   }
@@ -339,7 +341,7 @@ void tusas_destroy(tusas_handle* h) {
   if (h->st) cudaStreamSynchronize(h->st);
   cudaDeviceSynchronize();
   double* vecs[] = {h->Un, h->U, h->F, h->Ft, h->dU, h->Ut, h->tmp, h->tmp2, h->lin, h->lin_t, h->V, h->Z,
-                    h->partials, h->sc, h->Unm1, h->Fold, h->phold};
+                    h->partials, h->sc, h->hess, h->Unm1, h->Fold, h->phold};
   for (double* v : vecs) tusas::dev_free(v);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (double* p : h->ckpt) tusas::dev_free(p);
@@ -583,6 +585,42 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
   return TUSAS_OK;
 }
 
+// New column j of the Arnoldi relation and its Givens rotation, on the device (one
+// thread): H[i][j] = h1[i] + h2[i] (the two Gram-Schmidt passes), H[j+1][j] = ||w||,
+// the earlier rotations applied to the column, the new rotation from its last two
+// entries, g updated. st[0] = |g[j+1]| (the residual estimate), st[1] = ||w||,
+// st[2] = 1/||w|| (0 if ||w|| = 0), st[3] = the new diagonal entry. The host reads st
+// (one 32-byte copy per iteration) and the triangle once per cycle.
+__global__ void k_arnoldi_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
+                                 const double* __restrict__ norm2, double* __restrict__ H, double* __restrict__ cs,
+                                 double* __restrict__ sn, double* __restrict__ g, double* __restrict__ st) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double hn = sqrt(*norm2);
+  for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
+  H[(j + 1) * m + j] = hn;
+  for (int i = 0; i < j; ++i) {
+    const double a = H[i * m + j], bb = H[(i + 1) * m + j];
+    H[i * m + j] = cs[i] * a + sn[i] * bb;
+    H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+  }
+  const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
+  cs[j] = H[j * m + j] / den;
+  sn[j] = H[(j + 1) * m + j] / den;
+  H[j * m + j] = den;
+  H[(j + 1) * m + j] = 0.0;
+  g[j + 1] = -sn[j] * g[j];
+  g[j] = cs[j] * g[j];
+  st[0] = fabs(g[j + 1]);
+  st[1] = hn;
+  st[2] = hn > 0.0 ? 1.0 / hn : 0.0;
+  st[3] = den;
+}
+
+// g = (beta, 0, ..., 0) at the start of a cycle
+__global__ void k_givens_start(int m, double beta, double* __restrict__ g) {
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) g[i] = i == 0 ? beta : 0.0;
+}
+
 // Flexible right-preconditioned restarted GMRES with classical Gram-Schmidt
 // applied twice, x0 = 0; solves J x = b (b = -F) to ||b - J x|| <= tol_abs.
 // resid_out: the final residual norm (the Givens estimate, or the true norm after a restart).
@@ -590,7 +628,14 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
                  tusas_stats* stats, bool* converged = nullptr, int maxit = -1, double* resid_out = nullptr) {
   const int m = h->prm.gmres_restart;
   const i64 N = h->N;
-  std::vector<double> H((m + 1) * m), cs(m), sn(m), g(m + 1), y(m), col(64);
+  // device Hessenberg, rotations, g and status (k_arnoldi_givens), sized for the allocated restart
+  double* dH = h->hess;
+  double* dcs = dH + (h->m + 1) * h->m;
+  double* dsn = dcs + h->m;
+  double* dg = dsn + h->m;
+  double* dst = dg + h->m + 1;
+  std::vector<double> H((m + 1) * m), g(m + 1), y(m);
+  double stat[4];
   TCK(cudaMemsetAsync(x, 0, sizeof(double) * N, h->st));
   int its = 0;
   // r = b
@@ -604,9 +649,8 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
   while (beta > tol_abs && its < maxit) {
     if (!isfinite(beta)) return fail(h, TUSAS_ENONFINITE, "non-finite GMRES residual");
     TCK(tusas::vscal(N, 1.0 / beta, r, h->st));  // V_0 = r / beta
-    std::fill(g.begin(), g.end(), 0.0);
-    std::fill(H.begin(), H.end(), 0.0);
-    g[0] = beta;
+    k_givens_start<<<1, 32, 0, h->st>>>(m, beta, dg);
+    tusas::count_launches(1);
     int mu = 0;
     for (int j = 0; j < m; ++j) {
       double* Vj = h->V + (i64)j * N;
@@ -626,33 +670,22 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       TCK(tusas::gs_pass(0, N, j + 1, h->V, N, nullptr, w, h->partials, h->sc, h->st));
       TCK(tusas::gs_pass(1, N, j + 1, h->V, N, h->sc, w, h->partials, h->sc + 64, h->st));
       TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, w, h->partials, h->sc + 63, h->st));
-      std::vector<double> col2(64);
-      TCK(cudaMemcpyAsync(col.data(), h->sc, sizeof(double) * 64, cudaMemcpyDeviceToHost, h->st));
-      TCK(cudaMemcpyAsync(col2.data(), h->sc + 64, sizeof(double) * (j + 1), cudaMemcpyDeviceToHost, h->st));
+      // column j of H and its Givens rotation on the device; w scaled by 1/||w|| from there
+      k_arnoldi_givens<<<1, 32, 0, h->st>>>(j, m, h->sc, h->sc + 64, h->sc + 63, dH, dcs, dsn, dg, dst);
+      tusas::count_launches(1);
+      TCK(tusas::vscal_dev(N, dst + 2, w, h->st));
+      TCK(cudaMemcpyAsync(stat, dst, sizeof(stat), cudaMemcpyDeviceToHost, h->st));
       TCK(cudaStreamSynchronize(h->st));
-      for (int i = 0; i <= j; ++i) col[i] += col2[i];
-      const double hn = sqrt(col[63]);
       tend(h, TUSAS_T_ORTHO, to);
-      if (!isfinite(hn)) return fail(h, TUSAS_ENONFINITE, "non-finite Krylov vector");
-      for (int i = 0; i <= j; ++i) H[i * m + j] = col[i];
-      H[(j + 1) * m + j] = hn;
-      if (hn > 0.0) TCK(tusas::vscal(N, 1.0 / hn, w, h->st));
-      for (int i = 0; i < j; ++i) {
-        const double a = H[i * m + j], bb = H[(i + 1) * m + j];
-        H[i * m + j] = cs[i] * a + sn[i] * bb;
-        H[(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
-      }
-      const double den = hypot(H[j * m + j], H[(j + 1) * m + j]);
-      cs[j] = H[j * m + j] / den;
-      sn[j] = H[(j + 1) * m + j] / den;
-      H[j * m + j] = den;
-      H[(j + 1) * m + j] = 0.0;
-      g[j + 1] = -sn[j] * g[j];
-      g[j] = cs[j] * g[j];
-      resid = fabs(g[j + 1]);
+      if (!isfinite(stat[1]) || !isfinite(stat[0])) return fail(h, TUSAS_ENONFINITE, "non-finite Krylov vector");
+      resid = stat[0];
       mu = j + 1;
-      if (resid <= tol_abs || its >= maxit || den == 0.0) break;
+      if (resid <= tol_abs || its >= maxit || stat[3] == 0.0) break;
     }
+    // the triangle R = H[0..mu-1][0..mu-1] and g once per cycle
+    TCK(cudaMemcpyAsync(H.data(), dH, sizeof(double) * mu * m, cudaMemcpyDeviceToHost, h->st));
+    TCK(cudaMemcpyAsync(g.data(), dg, sizeof(double) * (mu + 1), cudaMemcpyDeviceToHost, h->st));
+    TCK(cudaStreamSynchronize(h->st));
     for (int i = mu - 1; i >= 0; --i) {
       double s = g[i];
       for (int k = i + 1; k < mu; ++k) s -= H[i * m + k] * y[k];

@@ -80,8 +80,9 @@ cudaError_t vfdq(i64 n, const double* x, double* y, const double* ainv, cudaStre
 // y = x * (*s) (s on device, optionally inverted)
 cudaError_t vscale_dev(i64 n, const double* x, double* y, const double* s, int invert, cudaStream_t st);
 cudaError_t vcopy(i64 n, const double* x, double* y, cudaStream_t st);
-// y *= a
+// y *= a (a a host value, or *a in device memory)
 cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st);
+cudaError_t vscal_dev(i64 n, const double* a, double* y, cudaStream_t st);
 cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st);
 
 // out[j] = sum_i X_j[i] * y[i] for j < k, X_j = X + j*ld; partials has

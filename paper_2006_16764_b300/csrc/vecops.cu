@@ -42,6 +42,10 @@ __global__ void k_scale_dev(i64 n, const double* __restrict__ x, double* __restr
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = x[i] * f;
 }
+__global__ void k_scal_dev(i64 n, const double* __restrict__ a, double* __restrict__ y) {
+  const double f = *a;
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) y[i] *= f;
+}
 __global__ void k_scal(i64 n, double a, double* __restrict__ y) {
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) y[i] *= a;
 }
@@ -85,6 +89,11 @@ cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st) {
     k_scal<<<grid_for(n), VT, 0, st>>>(n, a, y);
     count_launches(1);
   }
+  return cudaGetLastError();
+}
+cudaError_t vscal_dev(i64 n, const double* a, double* y, cudaStream_t st) {
+  k_scal_dev<<<grid_for(n), VT, 0, st>>>(n, a, y);
+  count_launches(1);
   return cudaGetLastError();
 }
 cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st) {
