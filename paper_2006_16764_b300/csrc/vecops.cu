@@ -465,19 +465,60 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_norm(i64 nv, int k, const do
   gs_block_sum<1>(acc, 1, partials);
 }
 
+// pass 3: w -= sum_j c_j X_j (no reduction; the first half of pass 1 for long cycles)
+template <int KM, int VEC, bool EXACT>
+__global__ void __launch_bounds__(GS_T) k_gs_update(i64 nv, int k, const double* __restrict__ X, i64 ldv,
+                                                    const double* __restrict__ c, double* __restrict__ w) {
+  typedef typename Vec<VEC>::T T;
+  constexpr int UNR = GsUnroll<KM>::V;
+  if (EXACT) k = KM;
+  const T* Xv = reinterpret_cast<const T*>(X);
+  T* wv = reinterpret_cast<T*>(w);
+  double cc[KM];
+#pragma unroll
+  for (int j = 0; j < KM; ++j) cc[j] = (EXACT || j < k) ? -c[j] : 0.0;
+  const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
+  const i64 lo = blockIdx.x * chunk;
+  const i64 hi = lo + chunk < nv ? lo + chunk : nv;
+  for (i64 i = lo + threadIdx.x; i < hi; i += (i64)GS_T * UNR) {
+    T wi[UNR], x[KM][UNR];
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+      const i64 e = i + (i64)u * GS_T;
+      wi[u] = e < hi ? wv[e] : gs_zero<VEC>();
+#pragma unroll
+      for (int j = 0; j < KM; ++j) x[j][u] = ((EXACT || j < k) && e < hi) ? Xv[j * ldv + e] : gs_zero<VEC>();
+    }
+#pragma unroll
+    for (int u = 0; u < UNR; ++u) {
+#pragma unroll
+      for (int j = 0; j < KM; ++j)
+        if (EXACT || j < k) wi[u] = Vec<VEC>::axpy(cc[j], x[j][u], wi[u]);
+      const i64 e = i + (i64)u * GS_T;
+      if (e < hi) wv[e] = wi[u];
+    }
+  }
+}
+
+// the fused update + dots of pass 1 keeps the KM loaded basis values in registers: up to 16
+static const int GS_FUSED_MAX = 16;
+
 template <int KM, int VEC, bool EXACT>
 static void gs_kernel(int pass, i64 nv, int k, const double* X, i64 ldv, const double* c, double* w,
                       double* partials, cudaStream_t st) {
-  if (pass == 0)
+  if (pass == 0) {
     k_gs_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);
-  else if (pass == 1)
-    k_gs_update_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
-  else
+  } else if (pass == 1) {
+    if constexpr (KM <= GS_FUSED_MAX) k_gs_update_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
+  } else if (pass == 2) {
     k_gs_update_norm<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
+  } else {
+    k_gs_update<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w);
+  }
 }
 
-// 16-byte loads: one instantiation per vector count up to 16; rounded counts above (GMRES
-// cycles longer than 16 vectors) and for the scalar-load fallback.
+// 16-byte loads: one instantiation per vector count up to 30 (the longest GMRES cycle); the
+// scalar-load fallback takes rounded counts.
 static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
                                   double* partials, cudaStream_t st) {
   const i64 nv = n / 2, ldv = ld / 2;
@@ -488,13 +529,12 @@ static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 l
     break;
     TUSAS_GS_K(1) TUSAS_GS_K(2) TUSAS_GS_K(3) TUSAS_GS_K(4) TUSAS_GS_K(5) TUSAS_GS_K(6) TUSAS_GS_K(7)
     TUSAS_GS_K(8) TUSAS_GS_K(9) TUSAS_GS_K(10) TUSAS_GS_K(11) TUSAS_GS_K(12) TUSAS_GS_K(13) TUSAS_GS_K(14)
-    TUSAS_GS_K(15) TUSAS_GS_K(16)
+    TUSAS_GS_K(15) TUSAS_GS_K(16) TUSAS_GS_K(17) TUSAS_GS_K(18) TUSAS_GS_K(19) TUSAS_GS_K(20) TUSAS_GS_K(21)
+    TUSAS_GS_K(22) TUSAS_GS_K(23) TUSAS_GS_K(24) TUSAS_GS_K(25) TUSAS_GS_K(26) TUSAS_GS_K(27) TUSAS_GS_K(28)
+    TUSAS_GS_K(29) TUSAS_GS_K(30)
 #undef TUSAS_GS_K
     default:
-      if (k <= 24)
-        gs_kernel<24, 2, false>(pass, nv, k, X, ldv, c, w, partials, st);
-      else
-        gs_kernel<32, 2, false>(pass, nv, k, X, ldv, c, w, partials, st);
+      gs_kernel<32, 2, false>(pass, nv, k, X, ldv, c, w, partials, st);
   }
   count_launches(1);
   return cudaGetLastError();
@@ -520,9 +560,10 @@ cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const doubl
                     double* out, cudaStream_t st) {
   if (k < 1 || k > 32) return cudaErrorInvalidValue;
   const bool vec = n % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)w % 16) == 0;
-  if (pass == 1 && k > 16) {
-    // the fused update + dots would spill with 32 vectors in registers: update, then dots
-    cudaError_t e = multi_axpy_sign(n, k, X, ld, c, -1.0, w, st);
+  if (pass == 1 && k > GS_FUSED_MAX) {
+    // the fused update + dots would spill with this many vectors in registers: update, then dots
+    cudaError_t e = vec ? gs_launch_vec2(3, n, k, X, ld, c, w, partials, st)
+                        : gs_launch_scalar(3, n, k, X, ld, c, w, partials, st);
     if (e != cudaSuccess) return e;
     pass = 0;
   }
