@@ -284,10 +284,12 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
     const long long base = (long long)sizeof(double) * 2 * nn * (11 + 2 * params->gmres_restart + 1);
     if (!tusas::dev_bytes_admit(base)) return TUSAS_ENOMEM;
   }
+  int device = 0;
+  if (cudaGetDevice(&device) != cudaSuccess) return TUSAS_ECUDA;
   tusas_handle* h = new tusas_handle();
   h->mesh = *mesh;
   h->prm = *params;
-  TCK(cudaGetDevice(&h->device));
+  h->device = device;
   tusas::DevMesh& d = h->dm;
   d.dim = mesh->dim;
   d.order = mesh->order == 2 ? 2 : 1;
@@ -594,7 +596,6 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
 __global__ void k_arnoldi_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
                                  const double* __restrict__ norm2, double* __restrict__ H, double* __restrict__ cs,
                                  double* __restrict__ sn, double* __restrict__ g, double* __restrict__ st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
   const double hn = sqrt(*norm2);
   for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
   H[(j + 1) * m + j] = hn;
@@ -671,7 +672,7 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       TCK(tusas::gs_pass(1, N, j + 1, h->V, N, h->sc, w, h->partials, h->sc + 64, h->st));
       TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, w, h->partials, h->sc + 63, h->st));
       // column j of H and its Givens rotation on the device; w scaled by 1/||w|| from there
-      k_arnoldi_givens<<<1, 32, 0, h->st>>>(j, m, h->sc, h->sc + 64, h->sc + 63, dH, dcs, dsn, dg, dst);
+      k_arnoldi_givens<<<1, 1, 0, h->st>>>(j, m, h->sc, h->sc + 64, h->sc + 63, dH, dcs, dsn, dg, dst);
       tusas::count_launches(1);
       TCK(tusas::vscal_dev(N, dst + 2, w, h->st));
       TCK(cudaMemcpyAsync(stat, dst, sizeof(stat), cudaMemcpyDeviceToHost, h->st));
