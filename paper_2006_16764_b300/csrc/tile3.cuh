@@ -109,16 +109,12 @@ __device__ __forceinline__ void t3_z(const double* Y, int tid, double* val, doub
 }
 
 // ---- transposed stages ----------------------------------------------------------------
-// Transposed z-stage of one element and field (integrands sv at the Gauss points, fluxes
-// fl[d][g]): contributions to the face below (lo) and above (hi) in the face layout.
-__device__ __forceinline__ void t3_zt(const double* sv, double (*fl)[8], double* lo, double* hi) {
+// Transposed z-stage of one element and field from the integrands sv at the Gauss points and
+// the flux pair sums F[d][j] = f_d at the two Gauss points along d (accumulated while the
+// Gauss points are evaluated, which keeps 12 instead of 24 flux values live per field):
+// contributions to the face below (lo) and above (hi) in the face layout.
+__device__ __forceinline__ void t3_zt_sums(const double* sv, double (*F)[4], double* lo, double* hi) {
   const double t = TUSAS_GP_T;
-  double F[3][4];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int j = 0; j < 4; ++j) F[d][j] = fl[d][insert_bit(j, d, 0)] + fl[d][insert_bit(j, d, 1)];
-  }
 #pragma unroll
   for (int k = 0; k < 4; ++k) {  // values with the z-differences
     const double yL = sv[k], yR = sv[k + 4];
@@ -139,6 +135,17 @@ __device__ __forceinline__ void t3_zt(const double* sv, double (*fl)[8], double*
     const double dd = yL - yR;
     lo[4 + xb] = fma(-t, dd, yL);
     hi[4 + xb] = fma(t, dd, yR);
+  }
+}
+
+// flux of Gauss point g into the pair sums: F[d][j] = f_d(g with bit d clear) + f_d(g with bit d set)
+__device__ __forceinline__ void t3_flux_sum(double (*F)[4], const double* f, int g) {
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    if ((g >> d) & 1)
+      F[d][remove_bit(g, d)] += f[d];
+    else
+      F[d][remove_bit(g, d)] = f[d];
   }
 }
 
@@ -277,8 +284,11 @@ struct Tan3 {
 };
 static_assert(Tan3::BYTES <= 48 * 1024, "tan3_kernel launches without the large-shared-memory opt-in");
 
+// 4 CTAs per SM (128 registers): with the flux pair sums accumulated per Gauss point the
+// tangent fits with at most 56 bytes of spills (8.05 -> 8.01 ms per application on the alloy
+// box against 3 CTAs; 2 CTAs per SM cost 13 %)
 template <int MODEL, bool TRANS>
-__global__ void __launch_bounds__(T3::NE, 3) tan3_kernel(const ElemArgs A) {
+__global__ void __launch_bounds__(T3::NE, 4) tan3_kernel(const ElemArgs A) {
   constexpr int NE = T3::NE;
   constexpr int NC = NLin<3, MODEL>::VALUE;
   extern __shared__ double sm[];
@@ -308,7 +318,7 @@ __global__ void __launch_bounds__(T3::NE, 3) tan3_kernel(const ElemArgs A) {
     t3_z<true>(sY + T3::YG, tid, val[1], grd[1]);
     const i64 tile_id = T.tx + (i64)A.ntx * (T.ty + (i64)A.nty * T.tz);
     const double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
-    double s0[8], s1[8], f0[3][8], f1[3][8];
+    double s0[8], s1[8], F0[3][4], F1[3][4];
     GPOut<3> o;
 #pragma unroll
     for (int g = 0; g < 8; ++g) {
@@ -324,14 +334,11 @@ __global__ void __launch_bounds__(T3::NE, 3) tan3_kernel(const ElemArgs A) {
       lin_apply<3, MODEL, TRANS, true>(A.P, L, val[0][g], val[1][g], xp, xg, o, A.K);
       s0[g] = o.sphi;
       s1[g] = o.su;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        f0[d][g] = o.fphi[d];
-        f1[d][g] = o.fu[d];
-      }
+      t3_flux_sum(F0, o.fphi, g);
+      t3_flux_sum(F1, o.fu, g);
     }
-    t3_zt(s0, f0, zlo[0], zhi[0]);
-    t3_zt(s1, f1, zlo[1], zhi[1]);
+    t3_zt_sums(s0, F0, zlo[0], zhi[0]);
+    t3_zt_sums(s1, F1, zlo[1], zhi[1]);
   } else {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
@@ -363,6 +370,7 @@ struct Res3 {
   static const size_t BYTES = sizeof(double) * DOUBLES;
 };
 
+// 2 CTAs per SM (the residual at 3, 168 registers with 72 bytes of spills, was 1 % slower)
 template <int MODEL, bool LIN>
 __global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
   constexpr int NE = T3::NE, NT = T3::NT;
@@ -421,7 +429,7 @@ __global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
     }
     const i64 tile_id = T.tx + (i64)A.ntx * (T.ty + (i64)A.nty * T.tz);
     double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
-    double s0[8], s1[8], f0[3][8], f1[3][8];
+    double s0[8], s1[8], F0[3][4], F1[3][4];
     GPOut<3> o;
     // frozen gradient at the two Gauss-point levels of the element (z = z0 + h (ez + t), h (ez + 1 - t))
     double G4z[2] = {0.0, 0.0};
@@ -448,14 +456,11 @@ __global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
       // true-unit integrands: values times h here, the node sums times w / h
       s0[g] = o.sphi * A.h;
       s1[g] = o.su * A.h;
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        f0[d][g] = o.fphi[d];
-        f1[d][g] = o.fu[d];
-      }
+      t3_flux_sum(F0, o.fphi, g);
+      t3_flux_sum(F1, o.fu, g);
     }
-    t3_zt(s0, f0, zlo[0], zhi[0]);
-    t3_zt(s1, f1, zlo[1], zhi[1]);
+    t3_zt_sums(s0, F0, zlo[0], zhi[0]);
+    t3_zt_sums(s1, F1, zlo[1], zhi[1]);
   } else {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
