@@ -34,6 +34,9 @@ struct tusas_handle {
   double* partials = nullptr;
   double* sc = nullptr;  // device scalars: [0..63] h1, [64..127] h2, [128..191] y, [192..] misc
   double* hess = nullptr;  // GMRES Hessenberg H [(m+1) x m], Givens cs, sn [m], g [m+1], status [4]
+  double* st_host = nullptr;      // mapped pinned copy of the GMRES status, written by k_arnoldi_givens
+  double* st_host_dev = nullptr;  // its device address
+  cudaEvent_t ev_st = nullptr;    // recorded after k_arnoldi_givens
   tusas::Precond pc;
   bool pc_ready = false;
   std::string err;
@@ -326,6 +329,17 @@ int tusas_create(const tusas_mesh* mesh, const tusas_params* params, tusas_handl
     tusas_destroy(h);
     return TUSAS_ENOMEM;
   }
+  if (cudaHostAlloc(&h->st_host, sizeof(double) * 4, cudaHostAllocMapped) != cudaSuccess) {
+    h->st_host = nullptr;
+    tusas_destroy(h);
+    return TUSAS_ENOMEM;
+  }
+  if (cudaHostGetDevicePointer(&h->st_host_dev, h->st_host, 0) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_st, cudaEventDisableTiming) != cudaSuccess) {
+    h->ev_st = nullptr;
+    tusas_destroy(h);
+    return TUSAS_ECUDA;
+  }
   if (params->precond > 0) {
     cudaError_t e = h->pc.create(h->dm, params->precond, params->smoother_fp32, params->mg_levels,
                                  params->cheb_degree, params->coarse_degree);
@@ -352,6 +366,8 @@ void tusas_destroy(tusas_handle* h) {
   tusas::dev_free(h->lam_rhs);
   tusas::dev_free(h->Ufinal);
   tusas::dev_free(h->sfw);
+  if (h->st_host) cudaFreeHost(h->st_host);
+  if (h->ev_st) cudaEventDestroy(h->ev_st);
   h->pc.destroy();
   delete h;
 }
@@ -587,17 +603,43 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
   return TUSAS_OK;
 }
 
-// New column j of the Arnoldi relation and its Givens rotation, on the device (one
-// thread): H[i][j] = h1[i] + h2[i] (the two Gram-Schmidt passes), H[j+1][j] = ||w||,
-// the earlier rotations applied to the column, the new rotation from its last two
-// entries, g updated. st[0] = |g[j+1]| (the residual estimate), st[1] = ||w||,
-// st[2] = 1/||w|| (0 if ||w|| = 0), st[3] = the new diagonal entry. The host reads st
-// (one 32-byte copy per iteration) and the triangle once per cycle.
-__global__ void k_arnoldi_givens(int j, int m, const double* __restrict__ h1, const double* __restrict__ h2,
-                                 const double* __restrict__ norm2, double* __restrict__ H, double* __restrict__ cs,
-                                 double* __restrict__ sn, double* __restrict__ g, double* __restrict__ st) {
-  const double hn = sqrt(*norm2);
-  for (int i = 0; i <= j; ++i) H[i * m + j] = h1[i] + h2[i];
+// New column j of the Arnoldi relation and its Givens rotation, on the device. One block
+// of 32 (j + 2) threads: warp c reduces column c of the second Gram-Schmidt pass's block
+// partial sums (c <= j: h2[c] = V_c . w1, c = j + 1: ||w1||^2), in the order of the
+// deterministic reductions; then one thread forms H[i][j] = h1[i] + h2[i] and
+// H[j+1][j] = ||w2||, w2 = w1 - V h2, from the Pythagorean identity
+// ||w2||^2 = ||w1||^2 - ||h2||^2 (exact for an orthonormal V; the classical Gram-Schmidt
+// variant with the Pythagorean norm, Smoktunowicz, Barlow and Langou, Numer. Math. 105
+// (2006)); h2 is the reorthogonalisation correction, of the order of the rounding of the
+// first pass, so the difference loses no digits unless w lies in span(V) to machine
+// precision, where H[j+1][j] and the GMRES residual vanish to rounding and the cycle ends.
+// The earlier rotations are applied to the column, the new one formed from its last two
+// entries, g updated. st[0] = |g[j+1]| (the residual estimate), st[1] = ||w2||,
+// st[2] = 1/||w2|| (0 if ||w2|| = 0; the last pass scales w2 by it), st[3] = the new
+// diagonal entry, copied to st_host (mapped pinned memory) as well.
+__global__ void k_arnoldi_givens(int j, int m, int nb, const double* __restrict__ partials,
+                                 const double* __restrict__ h1, double* __restrict__ h2, double* __restrict__ H,
+                                 double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                                 double* __restrict__ st, double* __restrict__ st_host) {
+  __shared__ double red[32];
+  const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (c <= j + 1) {
+    double s = 0.0;
+    for (int b = lane; b < nb; b += 32) s += partials[b * (i64)32 + c];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+    if (lane == 0) red[c] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  double q = red[j + 1];
+  for (int i = 0; i <= j; ++i) {
+    const double c2 = red[i];
+    h2[i] = c2;
+    q = fma(-c2, c2, q);
+    H[i * m + j] = h1[i] + c2;
+  }
+  const double hn = sqrt(q > 0.0 ? q : 0.0);
   H[(j + 1) * m + j] = hn;
   for (int i = 0; i < j; ++i) {
     const double a = H[i * m + j], bb = H[(i + 1) * m + j];
@@ -611,10 +653,8 @@ __global__ void k_arnoldi_givens(int j, int m, const double* __restrict__ h1, co
   H[(j + 1) * m + j] = 0.0;
   g[j + 1] = -sn[j] * g[j];
   g[j] = cs[j] * g[j];
-  st[0] = fabs(g[j + 1]);
-  st[1] = hn;
-  st[2] = hn > 0.0 ? 1.0 / hn : 0.0;
-  st[3] = den;
+  const double o[4] = {fabs(g[j + 1]), hn, hn > 0.0 ? 1.0 / hn : 0.0, den};
+  for (int i = 0; i < 4; ++i) st[i] = st_host[i] = o[i];
 }
 
 // g = (beta, 0, ..., 0) at the start of a cycle
@@ -663,21 +703,22 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       if (rc) return rc;
       if (stats) stats->jv_evals++;
       ++its;
-      // classical Gram-Schmidt applied twice (CGS2): h = V^T w; w -= V h; h2 = V^T w;
-      // w -= V h2 fused with ||w||^2; h += h2
+      // classical Gram-Schmidt applied twice (CGS2) in three passes over the basis: h = V^T w;
+      // w -= V h fused with h2 = V^T w and ||w||^2; w = (w - V h2) / ||w - V h2|| with the norm
+      // from the Pythagorean identity (k_arnoldi_givens, between the last two passes)
       const size_t to = tbeg(h);
-      // three passes over the basis: h = V^T w; w -= V h fused with h2 = V^T w; w -= V h2 fused
-      // with ||w||^2
-      TCK(tusas::gs_pass(0, N, j + 1, h->V, N, nullptr, w, h->partials, h->sc, h->st));
-      TCK(tusas::gs_pass(1, N, j + 1, h->V, N, h->sc, w, h->partials, h->sc + 64, h->st));
-      TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, w, h->partials, h->sc + 63, h->st));
-      // column j of H and its Givens rotation on the device; w scaled by 1/||w|| from there
-      k_arnoldi_givens<<<1, 1, 0, h->st>>>(j, m, h->sc, h->sc + 64, h->sc + 63, dH, dcs, dsn, dg, dst);
+      TCK(tusas::gs_pass(0, N, j + 1, h->V, N, nullptr, nullptr, w, h->partials, h->sc, h->st));
+      TCK(tusas::gs_pass(1, N, j + 1, h->V, N, h->sc, nullptr, w, h->partials, nullptr, h->st));
+      k_arnoldi_givens<<<1, 32 * (j + 2), 0, h->st>>>(j, m, tusas::gs_blocks(), h->partials, h->sc, h->sc + 64, dH,
+                                                        dcs, dsn, dg, dst, h->st_host_dev);
       tusas::count_launches(1);
-      TCK(tusas::vscal_dev(N, dst + 2, w, h->st));
-      TCK(cudaMemcpyAsync(stat, dst, sizeof(stat), cudaMemcpyDeviceToHost, h->st));
-      TCK(cudaStreamSynchronize(h->st));
+      TCK(cudaGetLastError());
+      TCK(cudaEventRecord(h->ev_st, h->st));
+      TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, dst + 2, w, h->partials, nullptr, h->st));
       tend(h, TUSAS_T_ORTHO, to);
+      // the status is read while the last pass runs
+      TCK(cudaEventSynchronize(h->ev_st));
+      for (int i = 0; i < 4; ++i) stat[i] = ((volatile double*)h->st_host)[i];
       if (!isfinite(stat[1]) || !isfinite(stat[0])) return fail(h, TUSAS_ENONFINITE, "non-finite Krylov vector");
       resid = stat[0];
       mu = j + 1;

@@ -80,9 +80,8 @@ cudaError_t vfdq(i64 n, const double* x, double* y, const double* ainv, cudaStre
 // y = x * (*s) (s on device, optionally inverted)
 cudaError_t vscale_dev(i64 n, const double* x, double* y, const double* s, int invert, cudaStream_t st);
 cudaError_t vcopy(i64 n, const double* x, double* y, cudaStream_t st);
-// y *= a (a a host value, or *a in device memory)
+// y *= a
 cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st);
-cudaError_t vscal_dev(i64 n, const double* a, double* y, cudaStream_t st);
 cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st);
 
 // out[j] = sum_i X_j[i] * y[i] for j < k, X_j = X + j*ld; partials has
@@ -97,14 +96,15 @@ cudaError_t multi_axpy(i64 n, int k, const double* X, i64 ld, const double* c, d
 // y -= sum_j c[j] X_j fused with the deterministic norm: *out_norm2 = ||y||^2
 cudaError_t multi_axpy_norm(i64 n, int k, const double* X, i64 ld, const double* c, double* y, double* partials,
                             double* out_norm2, cudaStream_t st);
-// Gram-Schmidt passes of the GMRES orthogonalisation over X_0..X_{k-1} (k <= 32) and w,
-// deterministic; partials holds gs_blocks() x 32 doubles; c and out are device arrays:
-//   pass 0: out[j] = X_j . w
-//   pass 1: w -= sum_j c[j] X_j, then out[j] = X_j . w
-//   pass 2: w -= sum_j c[j] X_j, then out[0] = ||w||^2
+// Gram-Schmidt passes of the GMRES orthogonalisation over X_0..X_{k-1} (k <= 31) and w,
+// deterministic; partials holds gs_blocks() x 32 doubles; c, s and out are device arrays:
+//   pass 0: out[j] = X_j . w (reduced)
+//   pass 1: w -= sum_j c[j] X_j, then the per-block partial sums of X_j . w in partials[b][j]
+//           and of ||w||^2 in partials[b][k], left for the caller to reduce (b < gs_blocks())
+//   pass 2: w = (w - sum_j c[j] X_j) s[0]
 int gs_blocks();
-cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w, double* partials,
-                    double* out, cudaStream_t st);
+cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, const double* s, double* w,
+                    double* partials, double* out, cudaStream_t st);
 // x = sum_j c[j] X_j + x (c on host memory passed by value through a device array)
 cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st);
 

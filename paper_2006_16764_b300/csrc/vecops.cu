@@ -42,10 +42,6 @@ __global__ void k_scale_dev(i64 n, const double* __restrict__ x, double* __restr
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
     y[i] = x[i] * f;
 }
-__global__ void k_scal_dev(i64 n, const double* __restrict__ a, double* __restrict__ y) {
-  const double f = *a;
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) y[i] *= f;
-}
 __global__ void k_scal(i64 n, double a, double* __restrict__ y) {
   for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) y[i] *= a;
 }
@@ -89,11 +85,6 @@ cudaError_t vscal(i64 n, double a, double* y, cudaStream_t st) {
     k_scal<<<grid_for(n), VT, 0, st>>>(n, a, y);
     count_launches(1);
   }
-  return cudaGetLastError();
-}
-cudaError_t vscal_dev(i64 n, const double* a, double* y, cudaStream_t st) {
-  k_scal_dev<<<grid_for(n), VT, 0, st>>>(n, a, y);
-  count_launches(1);
   return cudaGetLastError();
 }
 cudaError_t vfill(i64 n, double v, double* y, cudaStream_t st) {
@@ -304,11 +295,13 @@ template <> struct Vec<1> {
   typedef double T;
   static __device__ __forceinline__ double dot(T a, T b, double acc) { return fma(a, b, acc); }
   static __device__ __forceinline__ T axpy(double c, T x, T y) { return fma(c, x, y); }
+  static __device__ __forceinline__ T scale(double c, T x) { return c * x; }
 };
 template <> struct Vec<2> {
   typedef double2 T;
   static __device__ __forceinline__ double dot(T a, T b, double acc) { return fma(a.y, b.y, fma(a.x, b.x, acc)); }
   static __device__ __forceinline__ T axpy(double c, T x, T y) { return make_double2(fma(c, x.x, y.x), fma(c, x.y, y.y)); }
+  static __device__ __forceinline__ T scale(double c, T x) { return make_double2(c * x.x, c * x.y); }
 };
 
 // Sum of KM per-thread accumulators over the block into partials[blockIdx.x * 32 + j], j < k.
@@ -342,6 +335,16 @@ __device__ __forceinline__ void gs_block_sum(const double* acc, int k, double* _
 // else an upper bound with k the runtime count.
 template <int KM> struct GsUnroll { static const int V = KM <= 4 ? 4 : (KM <= 8 ? 2 : 1); };
 
+// With NORM the ||w||^2 accumulator (kept in acc[KM]) moves to slot k, the column after the dots.
+template <int KM, bool NORM>
+__device__ __forceinline__ void gs_norm_slot(double* acc, int k) {
+  if (NORM && k < KM) {
+#pragma unroll
+    for (int j = 0; j < KM; ++j)
+      if (j == k) acc[j] = acc[KM];
+  }
+}
+
 template <int VEC>
 __device__ __forceinline__ typename Vec<VEC>::T gs_zero();
 template <>
@@ -349,8 +352,8 @@ __device__ __forceinline__ double gs_zero<1>() { return 0.0; }
 template <>
 __device__ __forceinline__ double2 gs_zero<2>() { return make_double2(0.0, 0.0); }
 
-// pass 0: partials[b][j] of X_j . w
-template <int KM, int VEC, bool EXACT>
+// pass 0: partials[b][j] of X_j . w (j < k), and with NORM partials[b][k] of ||w||^2
+template <int KM, int VEC, bool EXACT, bool NORM>
 __global__ void __launch_bounds__(GS_T) k_gs_dots(i64 nv, int k, const double* __restrict__ X, i64 ldv,
                                                   const double* __restrict__ w, double* __restrict__ partials) {
   typedef typename Vec<VEC>::T T;
@@ -358,9 +361,9 @@ __global__ void __launch_bounds__(GS_T) k_gs_dots(i64 nv, int k, const double* _
   if (EXACT) k = KM;
   const T* Xv = reinterpret_cast<const T*>(X);
   const T* wv = reinterpret_cast<const T*>(w);
-  double acc[KM];
+  double acc[KM + 1];
 #pragma unroll
-  for (int j = 0; j < KM; ++j) acc[j] = 0.0;
+  for (int j = 0; j <= KM; ++j) acc[j] = 0.0;
   const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < nv ? lo + chunk : nv;
@@ -378,12 +381,15 @@ __global__ void __launch_bounds__(GS_T) k_gs_dots(i64 nv, int k, const double* _
 #pragma unroll
       for (int j = 0; j < KM; ++j)
         if (EXACT || j < k) acc[j] = Vec<VEC>::dot(x[j][u], wi[u], acc[j]);
+      if (NORM) acc[KM] = Vec<VEC>::dot(wi[u], wi[u], acc[KM]);
     }
   }
-  gs_block_sum<KM>(acc, k, partials);
+  gs_norm_slot<KM, NORM>(acc, k);
+  gs_block_sum<NORM ? KM + 1 : KM>(acc, NORM ? k + 1 : k, partials);
 }
 
-// pass 1: w -= sum_j c_j X_j, then partials[b][j] of X_j . w (the updated w)
+// pass 1: w -= sum_j c_j X_j, then partials[b][j] of X_j . w (the updated w) and partials[b][k]
+// of ||w||^2
 template <int KM, int VEC, bool EXACT>
 __global__ void __launch_bounds__(GS_T) k_gs_update_dots(i64 nv, int k, const double* __restrict__ X, i64 ldv,
                                                          const double* __restrict__ c, double* __restrict__ w,
@@ -393,12 +399,13 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_dots(i64 nv, int k, const do
   if (EXACT) k = KM;
   const T* Xv = reinterpret_cast<const T*>(X);
   T* wv = reinterpret_cast<T*>(w);
-  double cc[KM], acc[KM];
+  double cc[KM], acc[KM + 1];
 #pragma unroll
   for (int j = 0; j < KM; ++j) {
     cc[j] = (EXACT || j < k) ? -c[j] : 0.0;
     acc[j] = 0.0;
   }
+  acc[KM] = 0.0;
   const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < nv ? lo + chunk : nv;
@@ -421,16 +428,18 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_dots(i64 nv, int k, const do
 #pragma unroll
       for (int j = 0; j < KM; ++j)
         if (EXACT || j < k) acc[j] = Vec<VEC>::dot(x[j][u], wi[u], acc[j]);
+      acc[KM] = Vec<VEC>::dot(wi[u], wi[u], acc[KM]);
     }
   }
-  gs_block_sum<KM>(acc, k, partials);
+  gs_norm_slot<KM, true>(acc, k);
+  gs_block_sum<KM + 1>(acc, k + 1, partials);
 }
 
-// pass 2: w -= sum_j c_j X_j, then partials[b][0] of ||w||^2
+// pass 2: w = (w - sum_j c_j X_j) s[0]
 template <int KM, int VEC, bool EXACT>
-__global__ void __launch_bounds__(GS_T) k_gs_update_norm(i64 nv, int k, const double* __restrict__ X, i64 ldv,
-                                                         const double* __restrict__ c, double* __restrict__ w,
-                                                         double* __restrict__ partials) {
+__global__ void __launch_bounds__(GS_T) k_gs_update_scale(i64 nv, int k, const double* __restrict__ X, i64 ldv,
+                                                          const double* __restrict__ c, const double* __restrict__ s,
+                                                          double* __restrict__ w) {
   typedef typename Vec<VEC>::T T;
   constexpr int UNR = GsUnroll<KM>::V;
   if (EXACT) k = KM;
@@ -439,7 +448,7 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_norm(i64 nv, int k, const do
   double cc[KM];
 #pragma unroll
   for (int j = 0; j < KM; ++j) cc[j] = (EXACT || j < k) ? -c[j] : 0.0;
-  double acc[1] = {0.0};
+  const double sc = s[0];
   const i64 chunk = (nv + gridDim.x - 1) / gridDim.x;
   const i64 lo = blockIdx.x * chunk;
   const i64 hi = lo + chunk < nv ? lo + chunk : nv;
@@ -458,11 +467,9 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_norm(i64 nv, int k, const do
       for (int j = 0; j < KM; ++j)
         if (EXACT || j < k) wi[u] = Vec<VEC>::axpy(cc[j], x[j][u], wi[u]);
       const i64 e = i + (i64)u * GS_T;
-      if (e < hi) wv[e] = wi[u];
-      acc[0] = Vec<VEC>::dot(wi[u], wi[u], acc[0]);
+      if (e < hi) wv[e] = Vec<VEC>::scale(sc, wi[u]);
     }
   }
-  gs_block_sum<1>(acc, 1, partials);
 }
 
 // pass 3: w -= sum_j c_j X_j (no reduction; the first half of pass 1 for long cycles)
@@ -503,29 +510,33 @@ __global__ void __launch_bounds__(GS_T) k_gs_update(i64 nv, int k, const double*
 // the fused update + dots of pass 1 keeps the KM loaded basis values in registers: up to 16
 static const int GS_FUSED_MAX = 16;
 
+// pass 0: dots; 1: update + dots + norm (fused up to GS_FUSED_MAX vectors); 2: update + scale;
+// 3: update alone; 4: dots + norm (3 then 4 is pass 1 for long cycles)
 template <int KM, int VEC, bool EXACT>
-static void gs_kernel(int pass, i64 nv, int k, const double* X, i64 ldv, const double* c, double* w,
+static void gs_kernel(int pass, i64 nv, int k, const double* X, i64 ldv, const double* c, const double* s, double* w,
                       double* partials, cudaStream_t st) {
   if (pass == 0) {
-    k_gs_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);
+    k_gs_dots<KM, VEC, EXACT, false><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);
   } else if (pass == 1) {
     if constexpr (KM <= GS_FUSED_MAX) k_gs_update_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
   } else if (pass == 2) {
-    k_gs_update_norm<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
-  } else {
+    k_gs_update_scale<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, s, w);
+  } else if (pass == 3) {
     k_gs_update<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w);
+  } else {
+    k_gs_dots<KM, VEC, EXACT, true><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);
   }
 }
 
 // 16-byte loads: one instantiation per vector count up to 30 (the longest GMRES cycle); the
 // scalar-load fallback takes rounded counts.
-static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
-                                  double* partials, cudaStream_t st) {
+static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 ld, const double* c,
+                                  const double* s, double* w, double* partials, cudaStream_t st) {
   const i64 nv = n / 2, ldv = ld / 2;
   switch (k) {
 #define TUSAS_GS_K(K) \
   case K:             \
-    gs_kernel<K, 2, true>(pass, nv, k, X, ldv, c, w, partials, st); \
+    gs_kernel<K, 2, true>(pass, nv, k, X, ldv, c, s, w, partials, st); \
     break;
     TUSAS_GS_K(1) TUSAS_GS_K(2) TUSAS_GS_K(3) TUSAS_GS_K(4) TUSAS_GS_K(5) TUSAS_GS_K(6) TUSAS_GS_K(7)
     TUSAS_GS_K(8) TUSAS_GS_K(9) TUSAS_GS_K(10) TUSAS_GS_K(11) TUSAS_GS_K(12) TUSAS_GS_K(13) TUSAS_GS_K(14)
@@ -534,44 +545,45 @@ static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 l
     TUSAS_GS_K(29) TUSAS_GS_K(30)
 #undef TUSAS_GS_K
     default:
-      gs_kernel<32, 2, false>(pass, nv, k, X, ldv, c, w, partials, st);
+      gs_kernel<31, 2, false>(pass, nv, k, X, ldv, c, s, w, partials, st);
   }
   count_launches(1);
   return cudaGetLastError();
 }
 
-static cudaError_t gs_launch_scalar(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w,
-                                    double* partials, cudaStream_t st) {
+static cudaError_t gs_launch_scalar(int pass, i64 n, int k, const double* X, i64 ld, const double* c,
+                                    const double* s, double* w, double* partials, cudaStream_t st) {
   if (k <= 4)
-    gs_kernel<4, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+    gs_kernel<4, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
   else if (k <= 8)
-    gs_kernel<8, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+    gs_kernel<8, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
   else if (k <= 16)
-    gs_kernel<16, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+    gs_kernel<16, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
   else
-    gs_kernel<32, 1, false>(pass, n, k, X, ld, c, w, partials, st);
+    gs_kernel<31, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
   count_launches(1);
   return cudaGetLastError();
 }
 
 int gs_blocks() { return GS_BLOCKS; }
 
-cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, double* w, double* partials,
-                    double* out, cudaStream_t st) {
-  if (k < 1 || k > 32) return cudaErrorInvalidValue;
+cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, const double* s, double* w,
+                    double* partials, double* out, cudaStream_t st) {
+  if (k < 1 || k > 31 || pass < 0 || pass > 2) return cudaErrorInvalidValue;
   const bool vec = n % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)w % 16) == 0;
   if (pass == 1 && k > GS_FUSED_MAX) {
-    // the fused update + dots would spill with this many vectors in registers: update, then dots
-    cudaError_t e = vec ? gs_launch_vec2(3, n, k, X, ld, c, w, partials, st)
-                        : gs_launch_scalar(3, n, k, X, ld, c, w, partials, st);
+    // the fused update + dots would spill with this many vectors in registers: update, then
+    // dots + norm
+    cudaError_t e = vec ? gs_launch_vec2(3, n, k, X, ld, c, s, w, partials, st)
+                        : gs_launch_scalar(3, n, k, X, ld, c, s, w, partials, st);
     if (e != cudaSuccess) return e;
-    pass = 0;
+    return vec ? gs_launch_vec2(4, n, k, X, ld, c, s, w, partials, st)
+               : gs_launch_scalar(4, n, k, X, ld, c, s, w, partials, st);
   }
-  cudaError_t e = vec ? gs_launch_vec2(pass, n, k, X, ld, c, w, partials, st)
-                      : gs_launch_scalar(pass, n, k, X, ld, c, w, partials, st);
-  if (e != cudaSuccess) return e;
-  const int kout = pass == 2 ? 1 : k;
-  k_reduce_partials<<<1, 32 * kout, 0, st>>>(GS_BLOCKS, kout, 32, partials, out);
+  cudaError_t e = vec ? gs_launch_vec2(pass, n, k, X, ld, c, s, w, partials, st)
+                      : gs_launch_scalar(pass, n, k, X, ld, c, s, w, partials, st);
+  if (e != cudaSuccess || pass != 0) return e;
+  k_reduce_partials<<<1, 32 * k, 0, st>>>(GS_BLOCKS, k, 32, partials, out);
   count_launches(1);
   return cudaGetLastError();
 }
