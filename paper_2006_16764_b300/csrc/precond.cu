@@ -519,6 +519,15 @@ template <int DIM, int R>
 struct SmoothMinB {
   static const int V = (DIM == 3 && R == 2) ? 4 : TUSAS_SMOOTH_MINB;
 };
+// Coarse levels whose grid fits one wave at 2 blocks per SM take a variant compiled for 2
+// blocks per SM (128 registers): there the launch is bound by the latency of each thread's 54
+// stencil loads, which the larger budget keeps in flight at once instead of in several
+// dependent rounds (7.2 instead of 8.7 us per launch on a 33 x 25 x 9 level; a 702-block
+// level ran 2 us slower with it than with all its blocks resident at 32 registers).
+static const int SMOOTH_LAT_MINB = 2;
+static bool smooth_latency_grid(dim3 g) {
+  return (long long)g.x * g.y * g.z <= 148LL * SMOOTH_LAT_MINB;  // one wave of the variant
+}
 
 template <typename T>
 struct Coef2 {
@@ -526,8 +535,8 @@ struct Coef2 {
 };
 
 // r = D^-1 (b - A x) (or D^-1 b if x == nullptr, and then x = 0); d = r * it
-template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB) k_cheb_init(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                             T* __restrict__ x, int zero_x, T* __restrict__ r, T* __restrict__ d, Coef2<T> it) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -546,8 +555,8 @@ __global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_cheb_init(DevM
 }
 
 // x += d; if !last: r -= D^-1 A d; dout = c1 d + c2 r
-template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB) k_cheb_step(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, T* __restrict__ x,
                             T* __restrict__ r, const T* __restrict__ d, T* __restrict__ dout, Coef2<T> c, int last) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -566,8 +575,30 @@ __global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_cheb_step(DevM
   }
 }
 
-template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
+// The last Chebyshev step with a stencil product of the post-smoothing on the finest level,
+// with the deferred step and the widening to FP64 folded in: z = x + d + dout, where
+// x + d and dout = c1 d + c2 (r - D^-1 A d) are what k_cheb_step would store (the same
+// rounding) and the final x += dout was left to the reader of x.
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB) k_cheb_step_out(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv,
+                                                           const T* __restrict__ x, const T* __restrict__ r,
+                                                           const T* __restrict__ d, Coef2<T> c,
+                                                           double* __restrict__ z) {
+  constexpr int NS = Sten<DIM, R>::V;
+  int ix, iy, iz, blk;
+  i64 i;
+  if (!node3b(m, ix, iy, iz, i, blk)) return;
+  const i64 k = blk * m.nn + i;
+  const T dk = d[k];
+  const T xk = x[k] + dk;
+  const T ad = stencil_apply<DIM, T, R>(st + blk * NS * m.nn, d + blk * m.nn, m, i, ix, iy, iz);
+  const T rr = r[k] - dinv[k] * ad;
+  const T dn = (blk ? c.a[1] : c.a[0]) * dk + (blk ? c.b[1] : c.b[0]) * rr;
+  z[k] = (double)(xk + dn);
+}
+
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
   constexpr int NS = Sten<DIM, R>::V;
   {
@@ -582,8 +613,8 @@ __global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V)) k_resid(DevMesh 
 // Fused first Chebyshev step from x = 0 (the zero-x k_cheb_init followed by the first
 // k_cheb_step, same arithmetic): r0 = D^-1 b, d0 = a0 r0, x = d0, r = r0 - D^-1 A d0,
 // dout = c1 d0 + c2 r (requires degree >= 2, so the first step is not the last).
-template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V))
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB)
     k_cheb_first(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
                  T* __restrict__ x, T* __restrict__ r, T* __restrict__ dout, Coef2<T> it, Coef2<T> c) {
   constexpr int NS = Sten<DIM, R>::V;
@@ -606,8 +637,8 @@ __global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V))
 
 // Residual with the last Chebyshev update folded in: x' = x + p (p the pending
 // direction), res = b - A x', x' written to xout (a buffer other than x and p).
-template <int DIM, typename T, int R = 1>
-__global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V))
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB)
     k_resid_p(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
               const T* __restrict__ p, T* __restrict__ xout, T* __restrict__ res) {
   constexpr int NS = Sten<DIM, R>::V;
@@ -622,7 +653,30 @@ __global__ void __launch_bounds__(256, (SmoothMinB<DIM, R>::V))
                                                 [&](i64 j) { return __ldg(xv + j) + __ldg(pv + j); });
 }
 
-// b_c(I) = sum_i P(i, I) res(i) over the fine nodes within distance 1 of 2I
+// One smoother-type launch on level LV (both blocks): the kernel instance for the level's
+// dimension and stencil radius, and for radius-1 levels that do not fill the GPU the
+// latency variant (SMOOTH_LAT_MINB). T and st come from the caller.
+#define TUSAS_SMOOTH_LAUNCH(KERN, LV, ...)                                                       \
+  do {                                                                                          \
+    const dim3 g_ = grid3b((LV).m), b_ = block3((LV).m);                                        \
+    const bool lat_ = smooth_latency_grid(g_);                                                  \
+    if ((LV).m.dim == 3 && (LV).r == 2)                                                         \
+      KERN<3, T, 2><<<g_, b_, 0, st>>>(__VA_ARGS__);                                            \
+    else if ((LV).m.dim == 3 && lat_)                                                           \
+      KERN<3, T, 1, SMOOTH_LAT_MINB><<<g_, b_, 0, st>>>(__VA_ARGS__);                           \
+    else if ((LV).m.dim == 3)                                                                   \
+      KERN<3, T><<<g_, b_, 0, st>>>(__VA_ARGS__);                                               \
+    else if ((LV).r == 2)                                                                       \
+      KERN<2, T, 2><<<g_, b_, 0, st>>>(__VA_ARGS__);                                            \
+    else if (lat_)                                                                              \
+      KERN<2, T, 1, SMOOTH_LAT_MINB><<<g_, b_, 0, st>>>(__VA_ARGS__);                           \
+    else                                                                                        \
+      KERN<2, T><<<g_, b_, 0, st>>>(__VA_ARGS__);                                               \
+    count_launches(1);                                                                          \
+  } while (0)
+
+// b_c(I) = sum_i P(i, I) res(i) over the fine nodes within distance 1 of 2I (interior coarse
+// nodes, whose 3^dim fine neighbours all exist, skip the bounds tests; same order of the sum)
 template <int DIM, typename T>
 __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T* __restrict__ bc) {
   constexpr int NS = Pow3<DIM>::V;
@@ -630,6 +684,25 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
     int cx, cy, cz;
     i64 I;
     if (!node3(mc, cx, cy, cz, I)) return;
+    const bool interior = cx >= 1 && cx < mc.nnx - 1 && cy >= 1 && cy < mc.nny - 1 &&
+                          (DIM == 2 || (cz >= 1 && cz < mc.nnz - 1));
+    if (interior) {
+      const i64 fsy = mf.nnx, fsz = (i64)mf.nnx * mf.nny;
+      const i64 fc = 2 * (i64)cx + fsy * (2 * (i64)cy) + fsz * (2 * (i64)cz);
+#pragma unroll
+      for (int blk = 0; blk < 2; ++blk) {
+        const T* r = res + blk * mf.nn + fc;
+        T s = T(0);
+#pragma unroll
+        for (int o = 0; o < NS; ++o) {
+          const int ox = o % 3 - 1, oy = (o / 3) % 3 - 1, oz = DIM == 3 ? o / 9 - 1 : 0;
+          const T w = (ox ? T(0.5) : T(1)) * (oy ? T(0.5) : T(1)) * (oz ? T(0.5) : T(1));
+          s += w * r[ox + fsy * oy + fsz * oz];
+        }
+        bc[blk * mc.nn + I] = s;
+      }
+      return;
+    }
 #pragma unroll
     for (int blk = 0; blk < 2; ++blk) {
       T s = T(0);
@@ -647,40 +720,32 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
 }
 
 // x_f(i) += sum_J P(i, J) (x_c(J) + p_c(J)); p_c: the coarse level's pending Chebyshev
-// direction, or null
+// direction, or null. Fine node i = 2J + a (a_d in {0, 1}) interpolates between the coarse
+// nodes J and J + a, axis by axis (x first) as the mean of the two values: where a_d = 0 both
+// are the same node and the mean is exact, so every node takes the same branch-free path.
 template <int DIM, typename T>
 __global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, const T* __restrict__ pc,
                           T* __restrict__ xf) {
-  {
-    int fx, fy, fz;
-    i64 i;
-    if (!node3(mf, fx, fy, fz, i)) return;
-    const int f[3] = {fx, fy, fz};
+  int fx, fy, fz;
+  i64 i;
+  if (!node3(mf, fx, fy, fz, i)) return;
+  const i64 sy = mc.nnx, sz = (i64)mc.nnx * mc.nny;
+  const i64 J0 = (fx >> 1) + sy * (fy >> 1) + sz * (fz >> 1);
+  const i64 dx = fx & 1, dy = (fy & 1) ? sy : 0, dz = (DIM == 3 && (fz & 1)) ? sz : 0;
+  const T half = T(0.5);
 #pragma unroll
-    for (int blk = 0; blk < 2; ++blk) {
-      T s = T(0);
-#pragma unroll
-      for (int c = 0; c < (1 << DIM); ++c) {
-        int J[3] = {0, 0, 0};
-        T w = T(1);
-        bool ok = true;
-#pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          const int hi = (c >> d) & 1;
-          if ((f[d] & 1) == 0) {
-            if (hi) ok = false;
-            J[d] = f[d] / 2;
-          } else {
-            J[d] = f[d] / 2 + hi;
-            w *= T(0.5);
-          }
-        }
-        if (!ok) continue;
-        const i64 Jn = blk * mc.nn + J[0] + (i64)mc.nnx * (J[1] + (i64)mc.nny * J[2]);
-        s += w * (pc ? xc[Jn] + pc[Jn] : xc[Jn]);
-      }
-      xf[blk * mf.nn + i] += s;
-    }
+  for (int blk = 0; blk < 2; ++blk) {
+    const T* xb = xc + blk * mc.nn;
+    const T* pb = pc ? pc + blk * mc.nn : nullptr;
+    auto cv = [&](i64 J) { return pb ? xb[J] + pb[J] : xb[J]; };
+    auto plane = [&](i64 J) {
+      const T e0 = half * (cv(J) + cv(J + dx));
+      const T e1 = half * (cv(J + dy) + cv(J + dy + dx));
+      return half * (e0 + e1);
+    };
+    T v = plane(J0);
+    if (DIM == 3) v = half * (v + plane(J0 + dz));
+    xf[blk * mf.nn + i] += v;
   }
 }
 
@@ -915,7 +980,7 @@ cudaError_t Precond::setup(const ElemCtx& c, double theta, const double* U, cons
 }
 
 template <typename T>
-cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
+cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout, bool* zdone) {
   PrecondLevel& L = lv[l];
   Coef2<T> it, cc;
   double theta[2], delta[2], sigma[2], rho[2];
@@ -936,8 +1001,6 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
       rho[b] = rn;
     }
   };
-  const bool d3 = L.m.dim == 3;
-  const dim3 g = grid3b(L.m), bl = block3(L.m);
   const T *S = (const T*)L.st, *Di = (const T*)L.dinv, *B = (const T*)L.b;
   T *X = (T*)L.x, *Rr = (T*)L.r_;
   T* dcur = (T*)L.d;
@@ -949,27 +1012,11 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
   int k0 = 0;
   if (fuse && zero_x && degree >= 2) {  // zero start: initialisation and first step in one pass
     next_coef();
-    if (d3 && L.r == 2)
-      k_cheb_first<3, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
-    else if (d3)
-      k_cheb_first<3, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
-    else if (L.r == 2)
-      k_cheb_first<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
-    else
-      k_cheb_first<2, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, Rr, dnext, it, cc);
-    count_launches(1);
+    TUSAS_SMOOTH_LAUNCH(k_cheb_first, L, L.m, S, Di, B, X, Rr, dnext, it, cc);
     std::swap(dcur, dnext);
     k0 = 1;
   } else {
-    if (d3 && L.r == 2)
-      k_cheb_init<3, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
-    else if (d3)
-      k_cheb_init<3, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
-    else if (L.r == 2)
-      k_cheb_init<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
-    else
-      k_cheb_init<2, T><<<g, bl, 0, st>>>(L.m, S, Di, B, X, zero_x, Rr, dcur, it);
-    count_launches(1);
+    TUSAS_SMOOTH_LAUNCH(k_cheb_init, L, L.m, S, Di, B, X, zero_x, Rr, dcur, it);
   }
   for (int kk = k0; kk < degree; ++kk) {
     const int last = kk == degree - 1;
@@ -978,22 +1025,20 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st) {
       break;
     }
     next_coef();
-    if (d3 && L.r == 2)
-      k_cheb_step<3, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
-    else if (d3)
-      k_cheb_step<3, T><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
-    else if (L.r == 2)
-      k_cheb_step<2, T, 2><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
-    else
-      k_cheb_step<2, T><<<g, bl, 0, st>>>(L.m, S, Di, X, Rr, dcur, dnext, cc, last);
-    count_launches(1);
+    if (fuse && zout && kk == degree - 2) {  // the result goes straight to z (FP64)
+      TUSAS_SMOOTH_LAUNCH(k_cheb_step_out, L, L.m, S, Di, X, Rr, dcur, cc, zout);
+      *zdone = true;
+      L.pend = nullptr;
+      return cudaGetLastError();
+    }
+    TUSAS_SMOOTH_LAUNCH(k_cheb_step, L, L.m, S, Di, X, Rr, dcur, dnext, cc, last);
     std::swap(dcur, dnext);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t Precond::vcycle(int l, cudaStream_t st) {
+cudaError_t Precond::vcycle(int l, cudaStream_t st, double* zout, bool* zdone) {
   const int last = (int)lv.size() - 1;
   if (l == last) return cheb<T>(l, true, coarse_degree, st);
   cudaError_t e = cheb<T>(l, true, cheb_degree, st);
@@ -1001,32 +1046,16 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
   PrecondLevel& F = lv[l];
   PrecondLevel& C = lv[l + 1];
   const bool d3 = F.m.dim == 3;
-  const dim3 g = grid3b(F.m), bl = block3(F.m);
   const T *S = (const T*)F.st, *B = (const T*)F.b;
   if (F.pend) {  // residual of x + pending direction; the updated x goes to the free direction buffer
     void** xo = F.pend == F.d ? &F.d2 : &F.d;
     const T *X = (const T*)F.x, *P = (const T*)F.pend;
-    if (d3 && F.r == 2)
-      k_resid_p<3, T, 2><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
-    else if (d3)
-      k_resid_p<3, T><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
-    else if (F.r == 2)
-      k_resid_p<2, T, 2><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
-    else
-      k_resid_p<2, T><<<g, bl, 0, st>>>(F.m, S, B, X, P, (T*)*xo, (T*)F.res);
+    TUSAS_SMOOTH_LAUNCH(k_resid_p, F, F.m, S, B, X, P, (T*)*xo, (T*)F.res);
     std::swap(F.x, *xo);
     F.pend = nullptr;
   } else {
-    if (d3 && F.r == 2)
-      k_resid<3, T, 2><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
-    else if (d3)
-      k_resid<3, T><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
-    else if (F.r == 2)
-      k_resid<2, T, 2><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
-    else
-      k_resid<2, T><<<g, bl, 0, st>>>(F.m, S, B, (const T*)F.x, (T*)F.res);
+    TUSAS_SMOOTH_LAUNCH(k_resid, F, F.m, S, B, (const T*)F.x, (T*)F.res);
   }
-  count_launches(1);
   if (d3)
     k_restrict<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
   else
@@ -1040,7 +1069,7 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st) {
     k_prolong<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend, (T*)F.x);
   count_launches(1);
   C.pend = nullptr;
-  return cheb<T>(l, false, cheb_degree, st);
+  return cheb<T>(l, false, cheb_degree, st, zout, zdone);
 }
 
 template <typename T>
@@ -1058,9 +1087,10 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
     k_to_t<T><<<grid_nodes(n), 256, 0, st>>>(n, r, (T*)L0.b);
     count_launches(1);
   }
-  cudaError_t e = vcycle<T>(0, st);
+  bool zdone = false;
+  cudaError_t e = vcycle<T>(0, st, z, &zdone);
   if (e != cudaSuccess) return e;
-  {
+  if (!zdone) {
     k_from_t<T><<<grid_nodes(n), 256, 0, st>>>(n, (const T*)L0.x, (const T*)L0.pend, z);
     count_launches(1);
   }

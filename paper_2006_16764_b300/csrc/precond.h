@@ -53,12 +53,14 @@ class Precond {
   cudaError_t apply_t(const double* r, double* z, cudaStream_t st);
   template <typename T>
   cudaError_t galerkin_and_bounds(cudaStream_t st);
+  // zout: the finest level's post-smoothing writes its result there in FP64 (and sets
+  // *zdone) when its last stencil step can take the widening
   template <typename T>
-  cudaError_t vcycle(int l, cudaStream_t st);
+  cudaError_t vcycle(int l, cudaStream_t st, double* zout = nullptr, bool* zdone = nullptr);
   // Chebyshev smoothing of level l; the last step's x += d is left to the next reader of
   // x (residual, prolongation or the FP64 output), which adds lv[l].pend
   template <typename T>
-  cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st);
+  cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout = nullptr, bool* zdone = nullptr);
 };
 
 }  // namespace tusas
