@@ -160,6 +160,38 @@ def test_converged_steps_match_oracle(name, dims, opts, nsteps):
     assert abs(h.time - t) < 1e-12
 
 
+SMALL_SYSTEMS = [
+    ("2d-2x2-alloy", Mesh(2, 2, 2, 0, 0.7), ALLOY),
+    ("3d-1x1x1-pure", Mesh(3, 1, 1, 1, 0.6), PURE),
+]
+
+
+@pytest.mark.parametrize("precond", [0, 1])
+@pytest.mark.parametrize("jvp_mode", [1, 0])
+@pytest.mark.parametrize("name,mesh,prm", SMALL_SYSTEMS, ids=[c[0] for c in SMALL_SYSTEMS])
+def test_gmres_past_the_system_dimension(name, mesh, prm, jvp_mode, precond):
+    """Systems of 16-18 unknowns with the 30-vector restart: the Krylov space fills the whole
+    space within a cycle, where the new Arnoldi vector is rounding noise and ||w||^2 from the
+    Pythagorean identity cancels to nothing (the residual estimate then ends the cycle). The
+    steps must still converge to the direct-solve Newton solution (GMRES, Sec. 2.2)."""
+    p = dataclasses.replace(prm, precond=precond, jvp_mode=jvp_mode, gmres_restart=30, gmres_maxit=300,
+                            newton_rtol=1e-10)
+    n = mesh.n_dofs
+    Un = synth.seed_state(mesh, p, radius=0.5)
+    Un = Un + 0.2 * synth.uniform_pm1(17, n)
+    h = handle(mesh, p)
+    dt = 0.1
+    h.set_state(dev(Un), 0.0, dt)
+    Uo, t, out = Un.copy(), 0.0, dev(np.zeros_like(Un))
+    for _ in range(2):
+        st = h.step()
+        assert st["converged"] and st["fnorm"] < p.newton_rtol * st["fnorm0"], st
+        Uo, ratio = OS.newton_direct(mesh, p, Uo, t, dt)
+        assert ratio < 1e-12
+        t += dt
+        assert rel(host(h.get_state(out)), Uo) <= 1e-8
+
+
 @pytest.mark.parametrize("name", ["alloy3d_256x256x128", "dendrite3d_192", "dendrite2d_1024"])
 def test_full_size_residual_on_sampled_nodes(name):
     """At the full workload size the oracle evaluates sampled nodes one by one (Sec. 4.3 sizes)."""
