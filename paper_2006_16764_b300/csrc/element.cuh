@@ -324,6 +324,8 @@ struct PwConst {
   double e32g, e256g;  // K.thW2_gf 32 eps, K.thW2_gf 256 eps^2 (flux Hessian)
   double thW2gf;    // K.thW2_gf
   double ilT, g4off;   // G4 = z / lT - (zT + Vp t^{n+1}) / lT
+  double tauidt;    // tau0 / dt
+  double a_idt, ma_idt;  // A(phi^n) / dt = a_idt + ma_idt phi^n: (1 + k) / (2 dt), -(1 - k) / (2 dt)
 };
 
 inline PwConst pw_consts(const DevPhys& P, const LinScale& K, double gsc) {
@@ -343,6 +345,9 @@ inline PwConst pw_consts(const DevPhys& P, const LinScale& K, double gsc) {
   c.thW2gf = K.thW2_gf;
   c.ilT = P.has_g4 ? 1.0 / P.lT : 0.0;
   c.g4off = P.has_g4 ? -(P.zT + P.Vp * P.t_new) / P.lT : 0.0;
+  c.tauidt = P.tau0 * P.idt;
+  c.a_idt = 0.5 * (1.0 + P.k) * P.idt;
+  c.ma_idt = -0.5 * (1.0 - P.k) * P.idt;
   return c;
 }
 
@@ -370,28 +375,33 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, do
   A.eval(p, P.eps4, C.guard_q);
   const double eps = P.eps4;
   const double c16 = 16.0 * eps;
-  double m[DIM];  // n_i^2 - sum n^4
-#pragma unroll
-  for (int d = 0; d < DIM; ++d) m[d] = A.n2[d] - A.sn;
-  // anisotropic flux f = theta W0^2 a p_i (a + 16 eps (n_i^2 - sn))
+  // anisotropic flux f = theta W0^2 a p_i (a + 16 eps (n_i^2 - sn)), the last factor as
+  // 16 eps n_i^2 + (a - 16 eps sn)
   const double W2a = C.thW2g * A.a;
+  const double aa = fma(-c16, A.sn, A.a);
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, m[d], A.a);
-  const double dphidt = dphi * P.idt;  // time term
-  const double phihat = P.phihat_old ? fma(P.theta, dphidt, (1.0 - P.theta) * phold) : dphidt;  // source, j
+  for (int d = 0; d < DIM; ++d) o.fphi[d] = W2a * p[d] * fma(c16, A.n2[d], aa);
   const double omk = 1.0 - P.k;
   const double B = MODEL == 0 ? 1.0 : fma(omk, u, 1.0);
+  const double Bd = MODEL == 0 ? dphi : B * dphi;  // B (phi - phi^n)
+  const double Bt = Bd * P.idt;                     // B (phi - phi^n) / dt
+  // phihat of the u source and of j: (phi - phi^n)/dt, or the Eq. (theta) estimate; Bp = B phihat
+  double Bp = Bt, phihat = 0.0;
+  if (P.phihat_old) {
+    phihat = fma(P.theta, dphi * P.idt, (1.0 - P.theta) * phold);
+    Bp = MODEL == 0 ? phihat : B * phihat;
+  } else if (LIN) {
+    phihat = dphi * P.idt;
+  }
   const double a2 = A.a * A.a;
-  const double phi2 = phi * phi;
-  const double om = 1.0 - phi2;
+  const double om = fma(-phi, phi, 1.0);  // 1 - phi^2
   const double ug = u + G4;
   const double phom = phi * om;
   const double om2 = om * om;
-  const double Bt = MODEL == 0 ? dphidt : B * dphidt;
   const double phin = phi - dphi;
   double time;
   if (P.time_form == 0) {
-    time = P.tau0 * a2 * Bt;
+    time = (a2 * C.tauidt) * Bd;  // tau0 a^2 B (phi - phi^n) / dt
   } else {
     Aniso<DIM> An;
     An.eval(pn, eps, C.guard_q);
@@ -399,15 +409,14 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, do
     time = P.tau0 * (B * a2 * phi - Bn * (An.a * An.a) * phin) * P.idt;
   }
   o.sphi = fma(-P.theta, fma(-P.lam * om2, ug, phom), time);
-  const double Acoef = MODEL == 0 ? 1.0 : 0.5 * ((1.0 + P.k) - omk * phin);
-  const double Bp = MODEL == 0 ? phihat : B * phihat;
-  o.su = fma(-0.5, Bp, Acoef * du * P.idt);
+  const double Ai = MODEL == 0 ? P.idt : fma(C.ma_idt, phin, C.a_idt);  // A(phi^n) / dt
+  o.su = fma(-0.5, Bp, Ai * du);
   double Bpr = 0.0;
   if (MODEL == 0) {
 #pragma unroll
     for (int d = 0; d < DIM; ++d) o.fu[d] = C.thDg * g[d];
   } else {
-    const double Dq = C.halfthDg * (1.0 - phi);
+    const double Dq = fma(-C.halfthDg, phi, C.halfthDg);  // theta D (1 - phi) / 2
     Bpr = Bp * A.r;
     const double jn = P.jat_norm ? C.cw * Bpr : C.cwg * Bp;
 #pragma unroll
@@ -416,12 +425,16 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, do
   if constexpr (LIN) {
     // ---- pointwise Jacobian -------------------------------------------------
     // m_i = n_i^2 - sn, R_i = n_i m_i: da/dp_i = 16 eps R_i / |p|
-    double R[DIM];
+    double m[DIM], R[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) R[d] = A.n[d] * m[d];
+    for (int d = 0; d < DIM; ++d) {
+      m[d] = A.n2[d] - A.sn;
+      R[d] = A.n[d] * m[d];
+    }
+    const double phi2 = phi * phi;
     const double dbulk = fma(4.0 * P.lam * phom, ug, fma(-3.0, phi2, 1.0));
     // with the literal time term the coefficients of d(B a^2) multiply phi/dt instead of phihat
-    const double tfac = P.time_form == 0 ? dphidt : phi * P.idt;
+    const double tfac = P.time_form == 0 ? dphi * P.idt : phi * P.idt;
     const double Btf = P.time_form == 0 ? Bt : (MODEL == 0 ? tfac : B * tfac);
     L[0] = fma(K.m_th_vv, dbulk, K.tau_idt_vv * B * a2);  // alpha_phi
     L[1] = MODEL == 0 ? K.thlam_vv * om2 : fma(K.thlam_vv, om2, K.tau_vv * omk * a2 * tfac);  // alpha_u
@@ -451,8 +464,8 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, do
     }
     if (MODEL == 1) {
       constexpr int o0 = NLin<DIM, 1>::PHI;
-      L[o0 + 0] = K.mdphat * B;                                // beta_phi
-      L[o0 + 1] = fma(Acoef, K.idt, -K.half_omk_vv * phihat);  // beta_u
+      L[o0 + 0] = K.mdphat * B;                            // beta_phi
+      L[o0 + 1] = fma(Ai, K.vv, -K.half_omk_vv * phihat);  // beta_u = (A(phi^n)/dt - (1-k) phihat / 2) vv
       // direction of the antitrapping current (true units) and its derivative factors
       double nv[DIM];
 #pragma unroll
@@ -462,7 +475,7 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, do
 #pragma unroll
       for (int d = 0; d < DIM; ++d) L[o0 + 2 + d] = fma(C.mhthDg, g[d], cgp * nv[d]);  // gamma_phi
       L[o0 + 2 + DIM] = K.cw_omk_vf * phihat;                                           // c_u
-      L[o0 + 3 + DIM] = K.half_thD_gf * (1.0 - phi);                                    // gamma_g
+      L[o0 + 3 + DIM] = fma(-K.half_thD_gf, phi, K.half_thD_gf);                        // gamma_g
       L[o0 + 4 + DIM] = kap;                                                            // kappa1
       L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                         // kappa2
 #pragma unroll
