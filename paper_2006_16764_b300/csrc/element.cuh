@@ -295,7 +295,9 @@ template <int DIM, int MODEL>
 struct NLin {
   static const int SYM = DIM * (DIM + 1) / 2;
   static const int PHI = 2 + DIM + SYM;              // alpha_phi, alpha_u, alpha_p, H
-  static const int VALUE = MODEL == 0 ? PHI : PHI + 2 + DIM + 4 + DIM;
+  // alloy: beta_phi, beta_u, gamma_phi, c_u, gamma_g, kappa1, nvec (the second antitrapping
+  // factor kappa2 is kappa1 for the normalised current and 0 for the printed one: not stored)
+  static const int VALUE = MODEL == 0 ? PHI : PHI + 2 + DIM + 3 + DIM;
 };
 
 // unit factors: stored coefficients in true units (host)
@@ -477,9 +479,8 @@ __device__ __forceinline__ void pointwise(const DevPhys& P, const PwConst& C, do
       L[o0 + 2 + DIM] = K.cw_omk_vf * phihat;                                           // c_u
       L[o0 + 3 + DIM] = fma(-K.half_thD_gf, phi, K.half_thD_gf);                        // gamma_g
       L[o0 + 4 + DIM] = kap;                                                            // kappa1
-      L[o0 + 5 + DIM] = P.jat_norm ? kap : 0.0;                                         // kappa2
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) L[o0 + 6 + DIM + d] = nv[d];  // nvec
+      for (int d = 0; d < DIM; ++d) L[o0 + 5 + DIM + d] = nv[d];  // nvec
     }
   }
 }
@@ -664,11 +665,12 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
     } else {
       constexpr int o0 = NLin<DIM, 1>::PHI;
       o.su = fma(L[o0], x0, L[o0 + 1] * x1);
-      const double* nv = L + o0 + 6 + DIM;
+      const double* nv = L + o0 + 5 + DIM;
       double ndp = 0.0;
 #pragma unroll
       for (int d = 0; d < DIM; ++d) ndp = fma(nv[d], xp[d], ndp);
-      const double cu = L[o0 + 2 + DIM] * x1 - L[o0 + 5 + DIM] * ndp;
+      const double k2 = P.jat_norm ? L[o0 + 4 + DIM] : 0.0;  // kappa2
+      const double cu = L[o0 + 2 + DIM] * x1 - k2 * ndp;
 #pragma unroll
       for (int d = 0; d < DIM; ++d)
         o.fu[d] = fma(L[o0 + 2 + d], x0, fma(L[o0 + 3 + DIM], xg[d], fma(L[o0 + 4 + DIM], xp[d], cu * nv[d])));
@@ -685,7 +687,7 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
       for (int d = 0; d < DIM; ++d) o.fu[d] = thD * xg[d];
     } else {
       constexpr int o0 = NLin<DIM, 1>::PHI;
-      const double* nv = L + o0 + 6 + DIM;
+      const double* nv = L + o0 + 5 + DIM;
       s0 = fma(L[o0], x1, s0);
       s1 = fma(L[o0 + 1], x1, s1);
       double nfu = 0.0, gs = 0.0;
@@ -696,7 +698,7 @@ __device__ __forceinline__ void lin_apply(const DevPhys& P, const double* L, dou
       }
       s0 += gs;
       s1 = fma(L[o0 + 2 + DIM], nfu, s1);
-      const double k2 = L[o0 + 5 + DIM] * nfu;
+      const double k2 = (P.jat_norm ? L[o0 + 4 + DIM] : 0.0) * nfu;  // kappa2 (n . f_u)
 #pragma unroll
       for (int d = 0; d < DIM; ++d) {
         o.fphi[d] = fma(L[o0 + 4 + DIM], xg[d], fma(-k2, nv[d], o.fphi[d]));
