@@ -12,6 +12,8 @@ the GPU's hand-written tangent and adjoint against the plain definition.
 * ``jtvp``              F'(U)^T w via the element Jacobians
 * ``dF_deps4``          dF/d eps4
 * ``dF_dUn_T``          (dF/dU^n)^T w, the coupling of consecutive time steps
+* ``jvp_at_nodes``, ``jtvp_at_nodes``  the same products at listed nodes only,
+  from the elements adjacent to them (for meshes too large to evaluate whole)
 
 Parity: pinned against brute-force central differences (tests/test_oracle_jacobian.py).
 """
@@ -23,7 +25,7 @@ import numpy as np
 import scipy.sparse as sp
 
 from . import fem
-from .residual import element_residual, gather, residual
+from .residual import element_residual, gather, residual, residual_at_nodes
 
 H_CS = 1e-30
 
@@ -92,3 +94,30 @@ def jtvp(mesh, prm, U, Un, t_n, dt, w, wrt_prev=False, Unm1=None):
 
 def dF_dUn_T(mesh, prm, U, Un, t_n, dt, w):
     return jtvp(mesh, prm, U, Un, t_n, dt, w, wrt_prev=True)
+
+
+def jvp_at_nodes(mesh, prm, U, Un, t_n, dt, v, nodes):
+    """(F'(U) v) at the listed nodes: the complex step of residual_at_nodes, (rows phi, rows u)."""
+    rp, ru = residual_at_nodes(mesh, prm, U + 1j * H_CS * v, Un, t_n, dt, nodes)
+    return rp.imag / H_CS, ru.imag / H_CS
+
+
+def jtvp_at_nodes(mesh, prm, U, Un, t_n, dt, w, nodes):
+    """(F'(U)^T w) at the listed nodes: column j of F' meets w only on the elements adjacent to
+    node j, so their element Jacobians give the entries exactly; (entries phi, entries u)."""
+    n = mesh.n_nodes
+    nodes = np.asarray(nodes, dtype=np.int64)
+    elems = fem.elements_of_nodes(mesh, nodes)
+    Je, conn = element_jacobians(mesh, prm, U, Un, t_n, dt, elems=elems)
+    we = np.stack([w[:n][conn], w[n:][conn]], axis=1)  # (E, 2, nl)
+    contrib = np.einsum("eiajb,eia->ejb", Je, we)
+    pos = {int(v): i for i, v in enumerate(nodes)}
+    out_p = np.zeros(len(nodes))
+    out_u = np.zeros(len(nodes))
+    for e in range(conn.shape[0]):
+        for b in range(conn.shape[1]):
+            i = pos.get(int(conn[e, b]))
+            if i is not None:
+                out_p[i] += contrib[e, 0, b]
+                out_u[i] += contrib[e, 1, b]
+    return out_p, out_u

@@ -211,6 +211,35 @@ def test_full_size_residual_on_sampled_nodes(name):
     assert np.abs(F[n + nodes] - ru).max() <= 1e-12 * scale
 
 
+@pytest.mark.parametrize("name", ["alloy3d_256x256x128", "dendrite3d_192", "dendrite2d_1024"])
+def test_full_size_tangent_and_adjoint_on_sampled_nodes(name):
+    """Exact J v (linearisation pass + tangent kernels, the launches of the timed step) and
+    J^T w at the full workload size, against the oracle's complex-step products at sampled
+    nodes (the directional derivative of Eqs. pf2/conc2, Sec. 2.2)."""
+    w = synth.workload(name)
+    U0 = synth.initial_state(w)
+    U = U0 + 0.05 * synth.uniform_pm1(77, w.mesh.n_dofs)
+    v = synth.uniform_pm1(78, w.mesh.n_dofs)
+    wv = synth.uniform_pm1(79, w.mesh.n_dofs)
+    prm = dataclasses.replace(w.params, precond=0, jvp_mode=1)
+    h = handle(w.mesh, prm)
+    h.set_state(dev(U0), 1.0, w.dt)
+    tU, out = dev(U), dev(np.zeros_like(U))
+    JV = host(h.jvp(tU, dev(v), out))
+    JTW = host(h.jtvp(tU, dev(wv), out))
+    n = w.mesh.n_nodes
+    rng_nodes = (synth.splitmix64(6, 40) % np.uint64(n)).astype(np.int64)
+    nodes = np.unique(np.concatenate([rng_nodes, [0, n - 1, w.mesh.nx, n // 2]]))
+    jp, ju = OJ.jvp_at_nodes(w.mesh, prm, U, U0, 1.0, w.dt, v, nodes)
+    scale = max(np.abs(jp).max(), np.abs(ju).max())
+    assert np.abs(JV[nodes] - jp).max() <= 1e-12 * scale
+    assert np.abs(JV[n + nodes] - ju).max() <= 1e-12 * scale
+    tp, tu = OJ.jtvp_at_nodes(w.mesh, prm, U, U0, 1.0, w.dt, wv, nodes)
+    scale = max(np.abs(tp).max(), np.abs(tu).max())
+    assert np.abs(JTW[nodes] - tp).max() <= 1e-12 * scale
+    assert np.abs(JTW[n + nodes] - tu).max() <= 1e-12 * scale
+
+
 def test_error_codes():
     import paper_2006_16764_b300 as pkg
 

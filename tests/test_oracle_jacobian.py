@@ -74,3 +74,23 @@ def test_dense_jacobian_columns_brute_force():
         e[j] = 1.0
         col = _fd(lambda X: R.residual(mesh, prm, X, Un, 0.0, 0.5), U, e, 1e-5)
         assert np.abs(Jd[:, j] - col).max() <= 1e-7 * max(1.0, np.abs(col).max())
+
+
+@pytest.mark.parametrize("mesh,prm", CASES, ids=IDS)
+def test_products_at_listed_nodes_match_the_whole_mesh(mesh, prm):
+    """J v and J^T w at a few nodes (corners, faces, interior) from their adjacent
+    elements only: the entries of the whole-mesh products, which the tests above pin."""
+    U, Un = synth.random_fields(mesh, 11)
+    v = synth.random_vector(mesh, 12)
+    w = synth.random_vector(mesh, 13)
+    dt, tn = 0.3, 0.2
+    n = mesh.n_nodes
+    nodes = np.array([0, n - 1, 1, mesh.shape_nodes[0], n // 2, n // 3, n - 2])
+    jv = J.jvp(mesh, prm, U, Un, tn, dt, v)
+    jp, ju = J.jvp_at_nodes(mesh, prm, U, Un, tn, dt, v, nodes)
+    assert np.abs(jp - jv[nodes]).max() <= 1e-13 * np.abs(jv).max()
+    assert np.abs(ju - jv[n + nodes]).max() <= 1e-13 * np.abs(jv).max()
+    jtw = J.jtvp(mesh, prm, U, Un, tn, dt, w)
+    tp, tu = J.jtvp_at_nodes(mesh, prm, U, Un, tn, dt, w, nodes)
+    assert np.abs(tp - jtw[nodes]).max() <= 1e-13 * np.abs(jtw).max()
+    assert np.abs(tu - jtw[n + nodes]).max() <= 1e-13 * np.abs(jtw).max()
