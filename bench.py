@@ -716,7 +716,8 @@ def bench_config(w, ws):
                        f"{'FP32' if prm.smoother_fp32 else 'FP64'}",
             "newton_rtol": prm.newton_rtol, "gmres_restart": prm.gmres_restart,
             "gmres_maxit_per_newton": prm.gmres_maxit,
-            "l2": "inputs larger than L2 (state 136 MB per vector, linearisation 12.3 GB), no flush",
+            "l2": f"inputs larger than L2 (state {8 * mesh.n_dofs / 1e6:.0f} MB per vector, linearisation "
+                  f"{LIN_BYTES_PER_ELEM * mesh.n_elems / 1e9:.1f} GB), no flush",
             "parallelism": f"{ws} independent replica(s)"}
 
 
