@@ -47,4 +47,26 @@ struct Q2HexTile { static const int X = 4, Y = 2, Z = 2; };
 
 __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
 
+// Narrowing of FP64 inputs to the fill / smoother precision. To FP32 it runs on the integer
+// pipe instead of the FP64 unit (B300 converts 64-bit floats at the FP64 rate, 2 per clock per
+// SM): the binary32 result takes the sign, the exponent re-biased from 1023 to 127 and the top
+// 23 of the 52 mantissa bits (rounding toward zero, relative error below 2^-23). Magnitudes
+// below the binary32 normal range give a signed zero, above it (or NaN) an infinity; the
+// states and residuals narrowed here are finite and of order one or zero.
+__device__ __forceinline__ float f32_from_f64_rz(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned sign = (unsigned)(b >> 32) & 0x80000000u;
+  const int e = (int)((b >> 52) & 0x7ff) - 1023 + 127;
+  const unsigned mant = (unsigned)(b >> 29) & 0x7fffffu;
+  const unsigned r = e <= 0 ? sign : (e >= 255 ? (sign | 0x7f800000u) : (sign | ((unsigned)e << 23) | mant));
+  return __uint_as_float(r);
+}
+template <typename T>
+__device__ __forceinline__ T narrow(double x);
+template <>
+__device__ __forceinline__ double narrow<double>(double x) { return x; }
+template <>
+__device__ __forceinline__ float narrow<float>(double x) { return f32_from_f64_rz(x); }
+
+
 }  // namespace tusas

@@ -51,6 +51,11 @@ struct FillArgs {
   T theta;
   T w;          // Gauss weight (h/2)^dim
   T ih2;        // 1/h^2
+  // Gauss-point constants in the fill precision (host-computed, so that an FP32 fill does no
+  // FP64 arithmetic per Gauss point): small-gradient guard, 1 - 3 eps4, 4 eps4, 1 - k,
+  // (1 + k)/2, (1 - k)/2, and the weights of the four coefficients w tau0/dt, w theta W0^2,
+  // w/dt, w theta D
+  T guard, one_m3e, four_e, omk, half_opk, half_omk, wm1, wk1, wm2, wk2;
   const double* U;
   const double* Un;
   T* st;        // [2][NS][nn]
@@ -119,38 +124,39 @@ __device__ __forceinline__ void elem_pair_values(const FillArgs<T>& A, int ex, i
 #pragma unroll
   for (int a = 0; a < NN; ++a) {
     const i64 node = (ex + (a & 1)) + (i64)m.nnx * ((ey + ((a >> 1) & 1)) + (i64)m.nny * (ez + ((a >> 2) & 1)));
-    nphi[a] = (T)__ldg(A.U + node);
-    nu[a] = (T)__ldg(A.U + m.nn + node);
-    npn[a] = (T)__ldg(A.Un + node);
+    nphi[a] = narrow<T>(__ldg(A.U + node));
+    nu[a] = narrow<T>(__ldg(A.U + m.nn + node));
+    npn[a] = narrow<T>(__ldg(A.Un + node));
   }
   T phi[NN], u[NN], phin[NN], gp[DIM][NH];
   interp<DIM, true, T>(nphi, phi, gp, A.S);
   interp<DIM, false, T>(nu, u, nullptr, A.S);
   interp<DIM, false, T>(npn, phin, nullptr, A.S);
   T cm1[NN], ck1[NN], cm2[NN], ck2[NN];
-  const T eps = (T)A.P.eps4, k = (T)A.P.k;
 #pragma unroll
   for (int g = 0; g < NN; ++g) {
     T q = 0, s4 = 0;
 #pragma unroll
     for (int d = 0; d < DIM; ++d) {
       const T pd = gp[d][remove_bit(g, d)];
-      q += pd * pd;
-      s4 += pd * pd * pd * pd;
+      const T pd2 = pd * pd;
+      q += pd2;
+      s4 += pd2 * pd2;
     }
     T a = 1;
-    if ((double)q >= TUSAS_GUARD_Q) {
-      const T iq = t_rsqrt<T>(q) * t_rsqrt<T>(q);
-      a = (T)(1.0 - 3.0 * A.P.eps4) + T(4) * eps * s4 * iq * iq;
+    if (q >= A.guard) {
+      const T r = t_rsqrt<T>(q);
+      const T iq = r * r;
+      a = A.one_m3e + A.four_e * s4 * iq * iq;
     }
     const T a2 = a * a;
-    const T B = T(1) + (T(1) - k) * u[g];
-    const T Ac = MODEL == 0 ? T(1) : T(0.5) * ((T(1) + k) - (T(1) - k) * phin[g]);
+    const T B = T(1) + A.omk * u[g];
+    const T Ac = MODEL == 0 ? T(1) : A.half_opk - A.half_omk * phin[g];
     const T mob = MODEL == 0 ? T(1) : T(0.5) * (T(1) - phi[g]);
-    cm1[g] = A.w * (T)A.P.tau0 * B * a2 * (T)A.P.idt;
-    ck1[g] = A.w * A.theta * (T)(A.P.W0 * A.P.W0) * a2;
-    cm2[g] = A.w * Ac * (T)A.P.idt;
-    ck2[g] = A.w * A.theta * (T)A.P.D * mob;
+    cm1[g] = A.wm1 * B * a2;
+    ck1[g] = A.wk1 * a2;
+    cm2[g] = A.wm2 * Ac;
+    ck2[g] = A.wk2 * mob;
   }
   // 1D tables: mass [p][g] (p: 0 = (0,0), 1 = (0,1), 2 = (1,1)); stiffness +-1/h^2
   const T sq = (T)0.57735026918962576;
@@ -751,7 +757,8 @@ __global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, cons
 
 template <typename T>
 __global__ void k_to_t(i64 n, const double* __restrict__ r, T* __restrict__ b) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) b[i] = (T)r[i];
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
+    b[i] = narrow<T>(r[i]);
 }
 // z = x (+ p, the pending Chebyshev direction, if not null), widened to FP64
 template <typename T>
@@ -894,8 +901,20 @@ cudaError_t Precond::setup_t(const ElemCtx& c, double theta, const double* U, co
     A.S.gsw[k] = (T)c.S.gsw[k];
   }
   A.theta = (T)theta;
-  A.w = (T)(m.dim == 3 ? pow(m.h / 2, 3) : pow(m.h / 2, 2));
+  const double wg = m.dim == 3 ? pow(m.h / 2, 3) : pow(m.h / 2, 2);
+  A.w = (T)wg;
   A.ih2 = (T)(1.0 / (m.h * m.h));
+  const DevPhys& P = c.P;
+  A.guard = (T)TUSAS_GUARD_Q;
+  A.one_m3e = (T)(1.0 - 3.0 * P.eps4);
+  A.four_e = (T)(4.0 * P.eps4);
+  A.omk = (T)(1.0 - P.k);
+  A.half_opk = (T)(0.5 * (1.0 + P.k));
+  A.half_omk = (T)(0.5 * (1.0 - P.k));
+  A.wm1 = (T)(wg * P.tau0 * P.idt);
+  A.wk1 = (T)(wg * theta * P.W0 * P.W0);
+  A.wm2 = (T)(wg * P.idt);
+  A.wk2 = (T)(wg * theta * P.D);
   A.U = U;
   A.Un = Un;
   A.st = (T*)L0.st;

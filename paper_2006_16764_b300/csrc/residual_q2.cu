@@ -447,9 +447,9 @@ __global__ void __launch_bounds__(256) k_q2_stencil_fill(const Q2FillArgs<T> A) 
 #pragma unroll
       for (int b = 0; b < 9; ++b) {
         const i64 nb = (2 * ex + b % 3) + (i64)m.nnx * (2 * ey + b / 3);
-        nphi[b] = (T)__ldg(A.U + nb);
-        nu[b] = (T)__ldg(A.U + m.nn + nb);
-        npn[b] = (T)__ldg(A.Un + nb);
+        nphi[b] = narrow<T>(__ldg(A.U + nb));
+        nu[b] = narrow<T>(__ldg(A.U + m.nn + nb));
+        npn[b] = narrow<T>(__ldg(A.Un + nb));
       }
 #pragma unroll 1
       for (int g = 0; g < 9; ++g) {
@@ -466,7 +466,7 @@ __global__ void __launch_bounds__(256) k_q2_stencil_fill(const Q2FillArgs<T> A) 
         // Gauss-point coefficients of the two blocks (as the Q1 fill)
         const T q = px * px + py * py;
         T an = T(1);
-        if ((double)q >= TUSAS_GUARD_Q) {
+        if (q >= T(TUSAS_GUARD_Q)) {
           const T iq = T(1) / q;
           an = a0 + T(4) * eps * (px * px * px * px + py * py * py * py) * iq * iq;
         }
