@@ -44,11 +44,11 @@ CPU_SAMPLE = (48, 48, 32)
 # from the compiled kernels (DADD + DMUL + 2 DFMA per element: ncu
 # smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on.sum over the 8
 # colour launches of one pass on the 256x192x64 alloy box / its elements).
-FP64_FLOPS_PER_ELEM = {"residual": 1110.3, "residual_lin": 1917.3, "jv": 802.7}
+FP64_FLOPS_PER_ELEM = {"residual": 1128.3, "residual_lin": 1894.3, "jv": 802.7}
 # FP64 instructions per element (DADD + DMUL + DFMA, same counts): each occupies the FP64
 # pipe for one issue slot, so against the FMA issue rate (peak FLOP/s / 2) they give the
 # pipe's issue fraction; the FLOP fraction is lower where DADD / DMUL carry one flop.
-FP64_INSTR_PER_ELEM = {"residual": 779.2, "residual_lin": 1399.2, "jv": 496.3}
+FP64_INSTR_PER_ELEM = {"residual": 795.2, "residual_lin": 1376.2, "jv": 496.3}
 # Algorithmic HBM bytes per node of the method's operators: F reads U, U^n and
 # writes F (6 doubles); J v also reads v (8 doubles). Coordinates are implicit.
 ALG_BYTES_PER_NODE = {"residual": 48.0, "residual_lin": 48.0, "jv": 64.0}
@@ -59,7 +59,7 @@ LIN_BYTES_PER_ELEM = 22 * 8 * 8.0
 # DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
 # with the elements processed (same tiles, same per-element streams).
-NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1447.3, "jv": 1604.5}
+NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1447.6, "jv": 1605.1}
 
 
 def parse():

@@ -108,6 +108,39 @@ __device__ __forceinline__ void t3_z(const double* Y, int tid, double* val, doub
   }
 }
 
+// The z-stage split by Gauss-point column, the same operations as t3_z: gx[y + 2 z] and
+// gy[x + 2 z] are the x- and y-differences interpolated along z (grd[0], grd[1] of t3_z) ...
+__device__ __forceinline__ void t3_zxy(const double* Y, int tid, double* gx, double* gy) {
+  constexpr int UY = T3::UY;
+  const double t = TUSAS_GP_T;
+  const int u0 = tid, u1 = tid + T3::TX * T3::TY;
+#pragma unroll
+  for (int yb = 0; yb < 2; ++yb) {
+    const double x0 = Y[(6 + yb) * UY + u0], x1 = Y[(6 + yb) * UY + u1];
+    const double bb = x1 - x0;
+    gx[yb] = fma(t, bb, x0);
+    gx[yb + 2] = fma(-t, bb, x1);
+  }
+#pragma unroll
+  for (int xb = 0; xb < 2; ++xb) {
+    const double x0 = Y[(4 + xb) * UY + u0], x1 = Y[(4 + xb) * UY + u1];
+    const double bb = x1 - x0;
+    gy[xb] = fma(t, bb, x0);
+    gy[xb + 2] = fma(-t, bb, x1);
+  }
+}
+// ... and v0, v1 the values at the Gauss points (k, z = 0) and (k, z = 1) of column
+// k = x + 2 y, dz their z-difference (val[k], val[k + 4], grd[2][k] of t3_z).
+__device__ __forceinline__ void t3_zcol(const double* Y, int tid, int k, double& v0, double& v1, double& dz) {
+  constexpr int UY = T3::UY;
+  const double t = TUSAS_GP_T;
+  const double x0 = Y[k * UY + tid], x1 = Y[k * UY + tid + T3::TX * T3::TY];
+  const double bb = x1 - x0;
+  dz = bb;
+  v0 = fma(t, bb, x0);
+  v1 = fma(-t, bb, x1);
+}
+
 // ---- transposed stages ----------------------------------------------------------------
 // Transposed z-stage of one element and field from the integrands sv at the Gauss points and
 // the flux pair sums F[d][j] = f_d at the two Gauss points along d (accumulated while the
@@ -370,9 +403,11 @@ struct Res3 {
   static const size_t BYTES = sizeof(double) * DOUBLES;
 };
 
-// 2 CTAs per SM (the residual at 3, 168 registers with 72 bytes of spills, was 1 % slower)
+// The residual runs 3 CTAs per SM: with the Gauss points taken by column it needs 156
+// registers (all eight points' interpolated inputs at once needed 206, and forcing 3 CTAs
+// then spilled); the linearisation pass, 200 registers, runs 2.
 template <int MODEL, bool LIN>
-__global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
+__global__ void __launch_bounds__(T3::NE, (LIN ? 2 : 3)) res3_kernel(const ElemArgs A) {
   constexpr int NE = T3::NE, NT = T3::NT;
   constexpr int NC = NLin<3, MODEL>::VALUE;
   extern __shared__ double sm[];
@@ -412,24 +447,19 @@ __global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
   const bool valid = T.ex0 + lx < m.nx && T.ey0 + ly < m.ny && ez < m.nz;
   double zlo[2][8], zhi[2][8];
   if (valid) {
-    double phi[8], u[8], dphi[8], du[8], pho[8], gp[3][4], gu[3][4], gpn[3][4];
-    t3_z<true>(sY + Res3::Y_PHI, tid, phi, gp);
-    t3_z<true>(sY + Res3::Y_U, tid, u, gu);
-    t3_z<false>(sY + Res3::Y_DP, tid, dphi, nullptr);
-    t3_z<false>(sY + Res3::Y_DU, tid, du, nullptr);
-    if (tf1) {
-      double vpn[8];
-      t3_z<true>(sY + Res3::Y_PN, tid, vpn, gpn);
-    }
-    if (pho_on) {
-      t3_z<false>(sY + Res3::Y_PO, tid, pho, nullptr);
-    } else {
-#pragma unroll
-      for (int g = 0; g < 8; ++g) pho[g] = 0.0;
-    }
+    // Gauss points by column k = x + 2 y, the pair (k, z = 0), (k, z = 1) at a time: the values
+    // and z-differences of a column come from the faces when it is reached and its
+    // transposed z-stage follows its integrands, so only the x- and y-differences and the
+    // flux pair sums live across the loop. Operations and summation order are those of
+    // t3_z, t3_flux_sum and t3_zt_sums over the Gauss points in order.
+    double gpx[4], gpy[4], gux[4], guy[4], gnx[4] = {0, 0, 0, 0}, gny[4] = {0, 0, 0, 0};
+    t3_zxy(sY + Res3::Y_PHI, tid, gpx, gpy);
+    t3_zxy(sY + Res3::Y_U, tid, gux, guy);
+    if (tf1) t3_zxy(sY + Res3::Y_PN, tid, gnx, gny);
     const i64 tile_id = T.tx + (i64)A.ntx * (T.ty + (i64)A.nty * T.tz);
     double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
-    double s0[8], s1[8], F0[3][4], F1[3][4];
+    // flux pair sums: x-fluxes summed over x at (y, z), y-fluxes over y at (x, z)
+    double Fx0[4], Fy0[4], Fx1[4], Fy1[4];
     GPOut<3> o;
     // frozen gradient at the two Gauss-point levels of the element (z = z0 + h (ez + t), h (ez + 1 - t))
     double G4z[2] = {0.0, 0.0};
@@ -437,30 +467,85 @@ __global__ void __launch_bounds__(T3::NE, 2) res3_kernel(const ElemArgs A) {
       G4z[0] = fma(fma(m.h, ez + TUSAS_GP_T, m.z0), A.C.ilT, A.C.g4off);
       G4z[1] = fma(fma(m.h, ez + (1.0 - TUSAS_GP_T), m.z0), A.C.ilT, A.C.g4off);
     }
+    const double t = TUSAS_GP_T;
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      // gradients stay in the staged units (h times the gradient): A.C carries the factors
-      double p[3], gg[3], pn[3];
-#pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        p[d] = gp[d][remove_bit(g, d)];
-        gg[d] = gu[d][remove_bit(g, d)];
-        pn[d] = tf1 ? gpn[d][remove_bit(g, d)] : 0.0;
+    for (int k = 0; k < 4; ++k) {
+      const int x = k & 1, y = k >> 1;
+      double ph[2], uu[2], dph[2], duu[2], po[2] = {0.0, 0.0}, pz, uz, pnz = 0.0, dummy;
+      t3_zcol(sY + Res3::Y_PHI, tid, k, ph[0], ph[1], pz);
+      t3_zcol(sY + Res3::Y_U, tid, k, uu[0], uu[1], uz);
+      t3_zcol(sY + Res3::Y_DP, tid, k, dph[0], dph[1], dummy);
+      t3_zcol(sY + Res3::Y_DU, tid, k, duu[0], duu[1], dummy);
+      if (tf1) {
+        double a0, a1;
+        t3_zcol(sY + Res3::Y_PN, tid, k, a0, a1, pnz);
       }
-      double L[LIN ? NC : 1];
-      pointwise<3, MODEL, LIN>(A.P, A.C, phi[g], u[g], dphi[g], du[g], pho[g], p, gg, pn, G4z[g >> 2], o, L, A.K);
-      if (LIN) {
+      if (pho_on) t3_zcol(sY + Res3::Y_PO, tid, k, po[0], po[1], dummy);
+      double sv0[2], sv1[2], fz0[2], fz1[2];
 #pragma unroll
-        for (int c = 0; c < NC; ++c) linp[(c * 8 + g) * NE] = L[c];
+      for (int zb = 0; zb < 2; ++zb) {
+        const int g = k + 4 * zb;
+        // gradients stay in the staged units (h times the gradient): A.C carries the factors
+        const double p[3] = {gpx[y + 2 * zb], gpy[x + 2 * zb], pz};
+        const double gg[3] = {gux[y + 2 * zb], guy[x + 2 * zb], uz};
+        const double pn[3] = {gnx[y + 2 * zb], gny[x + 2 * zb], pnz};
+        double L[LIN ? NC : 1];
+        pointwise<3, MODEL, LIN>(A.P, A.C, ph[zb], uu[zb], dph[zb], duu[zb], po[zb], p, gg, pn, G4z[zb], o, L, A.K);
+        if (LIN) {
+#pragma unroll
+          for (int c = 0; c < NC; ++c) linp[(c * 8 + g) * NE] = L[c];
+        }
+        // true-unit integrands: values times h here, the node sums times w / h
+        sv0[zb] = o.sphi * A.h;
+        sv1[zb] = o.su * A.h;
+        fz0[zb] = o.fphi[2];
+        fz1[zb] = o.fu[2];
+        if (x == 0) {
+          Fx0[y + 2 * zb] = o.fphi[0];
+          Fx1[y + 2 * zb] = o.fu[0];
+        } else {
+          Fx0[y + 2 * zb] += o.fphi[0];
+          Fx1[y + 2 * zb] += o.fu[0];
+        }
+        if (y == 0) {
+          Fy0[x + 2 * zb] = o.fphi[1];
+          Fy1[x + 2 * zb] = o.fu[1];
+        } else {
+          Fy0[x + 2 * zb] += o.fphi[1];
+          Fy1[x + 2 * zb] += o.fu[1];
+        }
       }
-      // true-unit integrands: values times h here, the node sums times w / h
-      s0[g] = o.sphi * A.h;
-      s1[g] = o.su * A.h;
-      t3_flux_sum(F0, o.fphi, g);
-      t3_flux_sum(F1, o.fu, g);
+      // transposed z-stage of the values of column k (the z-flux pair sum as in t3_flux_sum)
+      double F2 = fz0[0];
+      F2 += fz0[1];
+      double q = fma(t, sv0[0] - sv0[1], F2);
+      zlo[0][k] = sv0[0] - q;
+      zhi[0][k] = sv0[1] + q;
+      F2 = fz1[0];
+      F2 += fz1[1];
+      q = fma(t, sv1[0] - sv1[1], F2);
+      zlo[1][k] = sv1[0] - q;
+      zhi[1][k] = sv1[1] + q;
     }
-    t3_zt_sums(s0, F0, zlo[0], zhi[0]);
-    t3_zt_sums(s1, F1, zlo[1], zhi[1]);
+    // x- and y-differences transposed along z (the tail of t3_zt_sums)
+#pragma unroll
+    for (int yb = 0; yb < 2; ++yb) {
+      double dd = Fx0[yb] - Fx0[yb + 2];
+      zlo[0][6 + yb] = fma(-t, dd, Fx0[yb]);
+      zhi[0][6 + yb] = fma(t, dd, Fx0[yb + 2]);
+      dd = Fx1[yb] - Fx1[yb + 2];
+      zlo[1][6 + yb] = fma(-t, dd, Fx1[yb]);
+      zhi[1][6 + yb] = fma(t, dd, Fx1[yb + 2]);
+    }
+#pragma unroll
+    for (int xb = 0; xb < 2; ++xb) {
+      double dd = Fy0[xb] - Fy0[xb + 2];
+      zlo[0][4 + xb] = fma(-t, dd, Fy0[xb]);
+      zhi[0][4 + xb] = fma(t, dd, Fy0[xb + 2]);
+      dd = Fy1[xb] - Fy1[xb + 2];
+      zlo[1][4 + xb] = fma(-t, dd, Fy1[xb]);
+      zhi[1][4 + xb] = fma(t, dd, Fy1[xb + 2]);
+    }
   } else {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
