@@ -59,7 +59,7 @@ LIN_BYTES_PER_ELEM = 22 * 8 * 8.0
 # DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
 # with the elements processed (same tiles, same per-element streams).
-NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1447.6, "jv": 1605.1}
+NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1447.6, "jv": 1544.8}
 
 
 def parse():

@@ -346,32 +346,79 @@ __global__ void __launch_bounds__(T3::NE, 4) tan3_kernel(const ElemArgs A) {
   const bool valid = T.ex0 + lx < m.nx && T.ey0 + ly < m.ny && T.ez0 + lz < m.nz;
   double zlo[2][8], zhi[2][8];
   if (valid) {
-    double val[2][8], grd[2][3][4];
-    t3_z<true>(sY, tid, val[0], grd[0]);
-    t3_z<true>(sY + T3::YG, tid, val[1], grd[1]);
+    // Gauss points by column k = x + 2 y, as in res3_kernel (same operations and order)
+    double g0x[4], g0y[4], g1x[4], g1y[4];
+    t3_zxy(sY, tid, g0x, g0y);
+    t3_zxy(sY + T3::YG, tid, g1x, g1y);
     const i64 tile_id = T.tx + (i64)A.ntx * (T.ty + (i64)A.nty * T.tz);
     const double* linp = A.lin + tile_id * (i64)(NC * 8 * NE) + tid;  // [c][g][t] within the tile
-    double s0[8], s1[8], F0[3][4], F1[3][4];
+    double Fx0[4], Fy0[4], Fx1[4], Fy1[4];
     GPOut<3> o;
+    const double t = TUSAS_GP_T;
 #pragma unroll
-    for (int g = 0; g < 8; ++g) {
-      double L[NC];
+    for (int k = 0; k < 4; ++k) {
+      const int x = k & 1, y = k >> 1;
+      double v0[2], v1[2], z0, z1;
+      t3_zcol(sY, tid, k, v0[0], v0[1], z0);
+      t3_zcol(sY + T3::YG, tid, k, v1[0], v1[1], z1);
+      double sv0[2], sv1[2], fz0[2], fz1[2];
 #pragma unroll
-      for (int c = 0; c < NC; ++c) L[c] = __ldg(linp + (c * 8 + g) * NE);
-      double xp[3], xg[3];
+      for (int zb = 0; zb < 2; ++zb) {
+        const int g = k + 4 * zb;
+        double L[NC];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        xp[d] = grd[0][d][remove_bit(g, d)];
-        xg[d] = grd[1][d][remove_bit(g, d)];
+        for (int c = 0; c < NC; ++c) L[c] = __ldg(linp + (c * 8 + g) * NE);
+        const double xp[3] = {g0x[y + 2 * zb], g0y[x + 2 * zb], z0};
+        const double xg[3] = {g1x[y + 2 * zb], g1y[x + 2 * zb], z1};
+        lin_apply<3, MODEL, TRANS, true>(A.P, L, v0[zb], v1[zb], xp, xg, o, A.K);
+        sv0[zb] = o.sphi;
+        sv1[zb] = o.su;
+        fz0[zb] = o.fphi[2];
+        fz1[zb] = o.fu[2];
+        if (x == 0) {
+          Fx0[y + 2 * zb] = o.fphi[0];
+          Fx1[y + 2 * zb] = o.fu[0];
+        } else {
+          Fx0[y + 2 * zb] += o.fphi[0];
+          Fx1[y + 2 * zb] += o.fu[0];
+        }
+        if (y == 0) {
+          Fy0[x + 2 * zb] = o.fphi[1];
+          Fy1[x + 2 * zb] = o.fu[1];
+        } else {
+          Fy0[x + 2 * zb] += o.fphi[1];
+          Fy1[x + 2 * zb] += o.fu[1];
+        }
       }
-      lin_apply<3, MODEL, TRANS, true>(A.P, L, val[0][g], val[1][g], xp, xg, o, A.K);
-      s0[g] = o.sphi;
-      s1[g] = o.su;
-      t3_flux_sum(F0, o.fphi, g);
-      t3_flux_sum(F1, o.fu, g);
+      double F2 = fz0[0];
+      F2 += fz0[1];
+      double q = fma(t, sv0[0] - sv0[1], F2);
+      zlo[0][k] = sv0[0] - q;
+      zhi[0][k] = sv0[1] + q;
+      F2 = fz1[0];
+      F2 += fz1[1];
+      q = fma(t, sv1[0] - sv1[1], F2);
+      zlo[1][k] = sv1[0] - q;
+      zhi[1][k] = sv1[1] + q;
     }
-    t3_zt_sums(s0, F0, zlo[0], zhi[0]);
-    t3_zt_sums(s1, F1, zlo[1], zhi[1]);
+#pragma unroll
+    for (int yb = 0; yb < 2; ++yb) {
+      double dd = Fx0[yb] - Fx0[yb + 2];
+      zlo[0][6 + yb] = fma(-t, dd, Fx0[yb]);
+      zhi[0][6 + yb] = fma(t, dd, Fx0[yb + 2]);
+      dd = Fx1[yb] - Fx1[yb + 2];
+      zlo[1][6 + yb] = fma(-t, dd, Fx1[yb]);
+      zhi[1][6 + yb] = fma(t, dd, Fx1[yb + 2]);
+    }
+#pragma unroll
+    for (int xb = 0; xb < 2; ++xb) {
+      double dd = Fy0[xb] - Fy0[xb + 2];
+      zlo[0][4 + xb] = fma(-t, dd, Fy0[xb]);
+      zhi[0][4 + xb] = fma(t, dd, Fy0[xb + 2]);
+      dd = Fy1[xb] - Fy1[xb + 2];
+      zlo[1][4 + xb] = fma(-t, dd, Fy1[xb]);
+      zhi[1][4 + xb] = fma(t, dd, Fy1[xb + 2]);
+    }
   } else {
 #pragma unroll
     for (int f = 0; f < 2; ++f) {
