@@ -256,7 +256,11 @@ __device__ __forceinline__ void t3_tile_t(double* sm, const double (*zlo)[8], co
   }
   __syncthreads();
 
-  // node sums in fixed order, read-modify-write
+  // node sums in fixed order, read-modify-write. The previous tile colour writes the same
+  // boundary nodes: a colour launched as a programmatic dependent of the previous one waits
+  // here, and only here, for that grid to complete and its writes to be visible (a no-op
+  // after an ordinary launch); the reads bypass L1, which may hold lines of an earlier colour.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int s = tid; s < NT; s += NE) {
     const int nx_ = s % NX, r = s / NX;
     const int ny_ = r % NY, nz_ = r / NY;
@@ -273,8 +277,8 @@ __device__ __forceinline__ void t3_tile_t(double* sm, const double (*zlo)[8], co
       if (SCALE) acc[f] *= scale;
     }
     const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
-    out[node] += acc[0];
-    out[m.nn + node] += acc[1];
+    out[node] = __ldcg(out + node) + acc[0];
+    out[m.nn + node] = __ldcg(out + m.nn + node) + acc[1];
   }
 }
 
@@ -331,6 +335,9 @@ __global__ void __launch_bounds__(T3::NE, 4) tan3_kernel(const ElemArgs A) {
   double* sN = sm;
   double* sX = sm + Tan3::OFF_X;
   double* sY = sm + Tan3::OFF_Y;
+  // the next tile colour may start on free SMs now: it touches nothing this grid writes
+  // before its own wait at the node sums
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   t3_stage(sN, m, T, tid, [&](i64 n) { return A.V[n]; });
   t3_stage(sN + T3::NT, m, T, tid, [&](i64 n) { return A.V[m.nn + n]; });
@@ -463,6 +470,8 @@ __global__ void __launch_bounds__(T3::NE, (LIN ? 2 : 3)) res3_kernel(const ElemA
   const int tid = threadIdx.x;
   const bool tf1 = A.P.time_form != 0;
   const bool pho_on = A.P.phihat_old && A.phold;
+  // the next tile colour may start on free SMs now (it waits at the node sums)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   double* sN = sm + Res3::OFF_N;
   double* sX = sm + Res3::OFF_X;
   double* sY = sm + Res3::OFF_Y;
