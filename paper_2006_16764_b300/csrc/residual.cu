@@ -69,6 +69,8 @@ elem_kernel(const ElemArgs A) {
   __shared__ double sV[NVF][NT];
   __shared__ double sC[2 * NN][NE];
 
+  // the next tile colour may start on free SMs now (it waits at the node sums)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   const DevMesh& m = A.m;
   int b = blockIdx.x;
   const int ix = b % A.ctx;
@@ -271,6 +273,9 @@ elem_kernel(const ElemArgs A) {
   __syncthreads();
 
   // ---- 3. node sums in fixed order, read-modify-write ---------------------------
+  // a colour launched as a programmatic dependent of the previous one waits here for that
+  // grid's node sums (a no-op after an ordinary launch); the reads bypass L1
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int s = threadIdx.x; s < NT; s += NE) {
     const int nx_ = s % NX, ny_ = (s / NX) % NY, nz_ = s / (NX * NY);
     const int gx = ex0 + nx_, gy = ey0 + ny_, gz = ez0 + nz_;
@@ -290,8 +295,8 @@ elem_kernel(const ElemArgs A) {
       acc1 *= A.wh;
     }
     const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
-    A.out[node] += acc0;
-    A.out[m.nn + node] += acc1;
+    A.out[node] = __ldcg(A.out + node) + acc0;
+    A.out[m.nn + node] = __ldcg(A.out + m.nn + node) + acc1;
   }
 }
 
@@ -391,7 +396,17 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
         e = cudaLaunchKernelEx(&cfg, res3_kernel<MODEL, MODE == M_RES_LIN>, a);
       if (e != cudaSuccess) return e;
     } else {
-      elem_kernel<DIM, MODEL, MODE><<<(unsigned)blocks, NE, 0, st>>>(a);
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3((unsigned)blocks);
+      cfg.blockDim = dim3(NE);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      attr[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = col > 0 ? 1 : 0;
+      const cudaError_t e = cudaLaunchKernelEx(&cfg, elem_kernel<DIM, MODEL, MODE>, a);
+      if (e != cudaSuccess) return e;
     }
     count_launches(1);
   }
