@@ -1,5 +1,6 @@
 // Host-side launch interface of the tusas-b300 kernels (internal to the library).
 #pragma once
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "common.cuh"
@@ -45,6 +46,26 @@ struct ElemCtx {
   int ntx, nty, ntz;  // tiles per axis
   int nlin;           // linearisation coefficients per Gauss point
 };
+
+// One tile-colour launch of an element pass. Colours after the first are programmatic
+// dependents of the previous colour: their CTAs may start on the SMs its last wave frees,
+// because the kernels touch nothing the previous colour writes until their node sums, where
+// they wait for it (griddepcontrol.wait) and read the sums past L1.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_colour(void (*kernel)(KArgs...), unsigned blocks, unsigned threads, size_t smem,
+                                 cudaStream_t st, bool dependent, Args&&... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = dependent ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 void elem_ctx_init(ElemCtx& c, const DevMesh& m, const DevPhys& P);
 // Doubles of the linearisation store for this mesh / model.

@@ -375,39 +375,14 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
     a.ctz = DIM == 3 ? (c.ntz - cz + 1) / 2 : 1;
     const long long blocks = (long long)a.ctx * a.cty * a.ctz;
     if (blocks <= 0) continue;
-    if constexpr (tan3 || res3) {
-      // colours after the first are programmatic dependents of the previous colour: their CTAs
-      // start on SMs the previous colour's last wave leaves free and wait only before the node
-      // sums they share with it (griddepcontrol in the kernels)
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)blocks);
-      cfg.blockDim = dim3(T3::NE);
-      cfg.dynamicSmemBytes = tan3 ? Tan3::BYTES : Res3::BYTES;
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      attr[0].val.programmaticStreamSerializationAllowed = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = col > 0 ? 1 : 0;
-      cudaError_t e;
-      if constexpr (tan3)
-        e = cudaLaunchKernelEx(&cfg, tan3_kernel<MODEL, MODE == M_JTV>, a);
-      else
-        e = cudaLaunchKernelEx(&cfg, res3_kernel<MODEL, MODE == M_RES_LIN>, a);
-      if (e != cudaSuccess) return e;
-    } else {
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3((unsigned)blocks);
-      cfg.blockDim = dim3(NE);
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-      attr[0].val.programmaticStreamSerializationAllowed = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = col > 0 ? 1 : 0;
-      const cudaError_t e = cudaLaunchKernelEx(&cfg, elem_kernel<DIM, MODEL, MODE>, a);
-      if (e != cudaSuccess) return e;
-    }
+    cudaError_t e;
+    if constexpr (tan3)
+      e = launch_colour(tan3_kernel<MODEL, MODE == M_JTV>, (unsigned)blocks, T3::NE, Tan3::BYTES, st, col > 0, a);
+    else if constexpr (res3)
+      e = launch_colour(res3_kernel<MODEL, MODE == M_RES_LIN>, (unsigned)blocks, T3::NE, Res3::BYTES, st, col > 0, a);
+    else
+      e = launch_colour(elem_kernel<DIM, MODEL, MODE>, (unsigned)blocks, NE, 0, st, col > 0, a);
+    if (e != cudaSuccess) return e;
     count_launches(1);
   }
   return cudaGetLastError();

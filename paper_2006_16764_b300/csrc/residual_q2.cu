@@ -138,6 +138,8 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
   constexpr int NUF = needU ? 6 : 0;
   constexpr int NVF = needV ? 2 : 0;
   constexpr int NSTAGE = (NUF + NVF) * NT;
+  // the next tile colour may start on free SMs now (it waits at the node sums)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   constexpr int NACC = 2 * NL * NE;
   // staging: [NUF][NT] fields phi, u, phi - phi^n, u - u^n, phi^n, phihat_old, then [NVF][NT];
   // after the element arithmetic the same memory holds the contributions [2 NL][NE]
@@ -339,6 +341,9 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
   __syncthreads();
 
   // ---- 3. node sums in fixed order, read-modify-write ---------------------------
+  // a colour launched as a programmatic dependent of the previous one waits here for that
+  // grid's node sums (a no-op after an ordinary launch); the reads bypass L1
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int s = threadIdx.x; s < NT; s += NE) {
     const int nxl = s % NX, nyl = s / NX;
     const int gx = nx0 + nxl, gy = ny0 + nyl;
@@ -363,8 +368,8 @@ __global__ void __launch_bounds__(Tile<2>::X * Tile<2>::Y, Q2MinBlocks<MODE>::V)
       }
     }
     const i64 node = gx + (i64)m.nnx * gy;
-    A.out[node] += acc0;
-    A.out[m.nn + node] += acc1;
+    A.out[node] = __ldcg(A.out + node) + acc0;
+    A.out[m.nn + node] = __ldcg(A.out + m.nn + node) + acc1;
   }
 }
 
@@ -530,7 +535,8 @@ static cudaError_t q2_colours(const ElemCtx& c, Q2Args a, cudaStream_t st) {
     a.cty = (c.nty - cy + 1) / 2;
     const long long blocks = (long long)a.ctx * a.cty;
     if (blocks <= 0) continue;
-    q2_kernel<MODEL, MODE><<<(unsigned)blocks, NE, 0, st>>>(a);
+    const cudaError_t e = launch_colour(q2_kernel<MODEL, MODE>, (unsigned)blocks, NE, 0, st, col > 0, a);
+    if (e != cudaSuccess) return e;
     count_launches(1);
   }
   return cudaGetLastError();

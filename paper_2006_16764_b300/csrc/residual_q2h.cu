@@ -154,6 +154,8 @@ __global__ void __launch_bounds__(HTHREADS, 1) q2h_kernel(const Q2HArgs A) {
   __shared__ double sV[NVF * HNT];
   __shared__ double sC[2 * 27 * HNE];
   __shared__ Q2HTab sT;
+  // the next tile colour may start on free SMs now (it waits at the node sums)
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   const DevMesh& m = A.m;
   const DevPhys& P = A.P;
@@ -296,6 +298,9 @@ __global__ void __launch_bounds__(HTHREADS, 1) q2h_kernel(const Q2HArgs A) {
   __syncthreads();
 
   // ---- 4. node sums in fixed order, read-modify-write ---------------------------------------
+  // a colour launched as a programmatic dependent of the previous one waits here for that
+  // grid's node sums (a no-op after an ordinary launch); the reads bypass L1
+  asm volatile("griddepcontrol.wait;" ::: "memory");
   for (int s = threadIdx.x; s < HNT; s += HTHREADS) {
     const int nxl = s % HNX, nyl = (s / HNX) % HNY, nzl = s / (HNX * HNY);
     const int gx = nx0 + nxl, gy = ny0 + nyl, gz = nz0 + nzl;
@@ -325,8 +330,8 @@ __global__ void __launch_bounds__(HTHREADS, 1) q2h_kernel(const Q2HArgs A) {
       }
     }
     const i64 node = gx + (i64)m.nnx * (gy + (i64)m.nny * gz);
-    A.out[node] += acc0;
-    A.out[m.nn + node] += acc1;
+    A.out[node] = __ldcg(A.out + node) + acc0;
+    A.out[m.nn + node] = __ldcg(A.out + m.nn + node) + acc1;
   }
 }
 
@@ -340,7 +345,8 @@ static cudaError_t q2h_colours(const ElemCtx& c, Q2HArgs a, cudaStream_t st) {
     a.ctz = (c.ntz - cz + 1) / 2;
     const long long blocks = (long long)a.ctx * a.cty * a.ctz;
     if (blocks <= 0) continue;
-    q2h_kernel<MODEL, MODE><<<(unsigned)blocks, HTHREADS, 0, st>>>(a);
+    const cudaError_t e = launch_colour(q2h_kernel<MODEL, MODE>, (unsigned)blocks, HTHREADS, 0, st, col > 0, a);
+    if (e != cudaSuccess) return e;
     count_launches(1);
   }
   return cudaGetLastError();
