@@ -618,10 +618,12 @@ __global__ void __launch_bounds__(256, MB) k_resid(DevMesh m, const T* __restric
 
 // Fused first Chebyshev step from x = 0 (the zero-x k_cheb_init followed by the first
 // k_cheb_step, same arithmetic): r0 = D^-1 b, d0 = a0 r0, x = d0, r = r0 - D^-1 A d0,
-// dout = c1 d0 + c2 r (requires degree >= 2, so the first step is not the last).
+// dout = c1 d0 + c2 r (requires degree >= 2, so the first step is not the last). db = D^-1 b,
+// formed by the kernel that produced b (k_to_t, k_restrict), so the stencil reads one array at
+// the 27 neighbours instead of two.
 template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
 __global__ void __launch_bounds__(256, MB)
-    k_cheb_first(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ bvec,
+    k_cheb_first(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv, const T* __restrict__ db,
                  T* __restrict__ x, T* __restrict__ r, T* __restrict__ dout, Coef2<T> it, Coef2<T> c) {
   constexpr int NS = Sten<DIM, R>::V;
   int ix, iy, iz, blk;
@@ -629,13 +631,12 @@ __global__ void __launch_bounds__(256, MB)
   if (!node3b(m, ix, iy, iz, i, blk)) return;
   const i64 k = blk * m.nn + i;
   const T a0 = blk ? it.a[1] : it.a[0];
-  const T* dv = dinv + blk * m.nn;
-  const T* bv = bvec + blk * m.nn;
-  const T r0 = dinv[k] * bvec[k];
+  const T* dbv = db + blk * m.nn;
+  const T r0 = db[k];
   const T dk = r0 * a0;
   x[k] = dk;
   const T ad = stencil_apply_f<DIM, T, R>(st + blk * NS * m.nn, m, i, ix, iy, iz,
-                                          [&](i64 j) { return (__ldg(dv + j) * __ldg(bv + j)) * a0; });
+                                          [&](i64 j) { return __ldg(dbv + j) * a0; });
   const T rr = r0 - dinv[k] * ad;
   r[k] = rr;
   dout[k] = (blk ? c.a[1] : c.a[0]) * dk + (blk ? c.b[1] : c.b[0]) * rr;
@@ -682,9 +683,11 @@ __global__ void __launch_bounds__(256, MB)
   } while (0)
 
 // b_c(I) = sum_i P(i, I) res(i) over the fine nodes within distance 1 of 2I (interior coarse
-// nodes, whose 3^dim fine neighbours all exist, skip the bounds tests; same order of the sum)
+// nodes, whose 3^dim fine neighbours all exist, skip the bounds tests; same order of the sum),
+// and if db_c is given D_c^-1 b_c there (for k_cheb_first on the coarse level)
 template <int DIM, typename T>
-__global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T* __restrict__ bc) {
+__global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T* __restrict__ bc,
+                           const T* __restrict__ dinv_c, T* __restrict__ db_c) {
   constexpr int NS = Pow3<DIM>::V;
   {
     int cx, cy, cz;
@@ -706,6 +709,7 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
           s += w * r[ox + fsy * oy + fsz * oz];
         }
         bc[blk * mc.nn + I] = s;
+        if (db_c) db_c[blk * mc.nn + I] = dinv_c[blk * mc.nn + I] * s;
       }
       return;
     }
@@ -721,6 +725,7 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
         s += w * res[blk * mf.nn + fx + (i64)mf.nnx * (fy + (i64)mf.nny * fz)];
       }
       bc[blk * mc.nn + I] = s;
+      if (db_c) db_c[blk * mc.nn + I] = dinv_c[blk * mc.nn + I] * s;
     }
   }
 }
@@ -755,10 +760,15 @@ __global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, cons
   }
 }
 
+// b = r in the smoother precision, and if db is given D^-1 b (for k_cheb_first)
 template <typename T>
-__global__ void k_to_t(i64 n, const double* __restrict__ r, T* __restrict__ b) {
-  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x)
-    b[i] = narrow<T>(r[i]);
+__global__ void k_to_t(i64 n, const double* __restrict__ r, T* __restrict__ b, const T* __restrict__ dinv,
+                       T* __restrict__ db) {
+  for (i64 i = blockIdx.x * (i64)blockDim.x + threadIdx.x; i < n; i += (i64)gridDim.x * blockDim.x) {
+    const T bi = narrow<T>(r[i]);
+    b[i] = bi;
+    if (db) db[i] = dinv[i] * bi;
+  }
 }
 // z = x (+ p, the pending Chebyshev direction, if not null), widened to FP64
 template <typename T>
@@ -1031,7 +1041,7 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st, doubl
   int k0 = 0;
   if (fuse && zero_x && degree >= 2) {  // zero start: initialisation and first step in one pass
     next_coef();
-    TUSAS_SMOOTH_LAUNCH(k_cheb_first, L, L.m, S, Di, B, X, Rr, dnext, it, cc);
+    TUSAS_SMOOTH_LAUNCH(k_cheb_first, L, L.m, S, Di, (const T*)L.res, X, Rr, dnext, it, cc);  // res holds D^-1 b
     std::swap(dcur, dnext);
     k0 = 1;
   } else {
@@ -1075,10 +1085,12 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st, double* zout, bool* zdone) {
   } else {
     TUSAS_SMOOTH_LAUNCH(k_resid, F, F.m, S, B, (const T*)F.x, (T*)F.res);
   }
+  // FP32: D_c^-1 b_c into the coarse level's residual buffer for its k_cheb_first
+  T* dbc = sizeof(T) == sizeof(float) ? (T*)C.res : nullptr;
   if (d3)
-    k_restrict<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+    k_restrict<3, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b, (const T*)C.dinv, dbc);
   else
-    k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b);
+    k_restrict<2, T><<<grid3(C.m), block3(C.m), 0, st>>>(F.m, C.m, (const T*)F.res, (T*)C.b, (const T*)C.dinv, dbc);
   count_launches(1);
   e = vcycle<T>(l + 1, st);
   if (e != cudaSuccess) return e;
@@ -1103,7 +1115,9 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
     return cudaGetLastError();
   }
   {
-    k_to_t<T><<<grid_nodes(n), 256, 0, st>>>(n, r, (T*)L0.b);
+    // FP32: D^-1 b into the level's residual buffer (free until its residual pass) for k_cheb_first
+    T* db = sizeof(T) == sizeof(float) ? (T*)L0.res : nullptr;
+    k_to_t<T><<<grid_nodes(n), 256, 0, st>>>(n, r, (T*)L0.b, (const T*)L0.dinv, db);
     count_launches(1);
   }
   bool zdone = false;
