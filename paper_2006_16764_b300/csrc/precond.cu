@@ -603,6 +603,27 @@ __global__ void __launch_bounds__(256, MB) k_cheb_step_out(DevMesh m, const T* _
   z[k] = (double)(xk + dn);
 }
 
+// The last Chebyshev step with a stencil product of a pre-smoothing, with the deferred step
+// folded in: xout = (x + d) + dout, the sum k_resid_p would form at every neighbour (the same
+// rounding), so the residual after the smoothing reads one array. Neither x, r nor dout is
+// needed afterwards.
+template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
+__global__ void __launch_bounds__(256, MB) k_cheb_step_x(DevMesh m, const T* __restrict__ st, const T* __restrict__ dinv,
+                                                         const T* __restrict__ x, const T* __restrict__ r,
+                                                         const T* __restrict__ d, Coef2<T> c, T* __restrict__ xout) {
+  constexpr int NS = Sten<DIM, R>::V;
+  int ix, iy, iz, blk;
+  i64 i;
+  if (!node3b(m, ix, iy, iz, i, blk)) return;
+  const i64 k = blk * m.nn + i;
+  const T dk = d[k];
+  const T xk = x[k] + dk;
+  const T ad = stencil_apply<DIM, T, R>(st + blk * NS * m.nn, d + blk * m.nn, m, i, ix, iy, iz);
+  const T rr = r[k] - dinv[k] * ad;
+  const T dn = (blk ? c.a[1] : c.a[0]) * dk + (blk ? c.b[1] : c.b[0]) * rr;
+  xout[k] = xk + dn;
+}
+
 template <int DIM, typename T, int R = 1, int MB = SmoothMinB<DIM, R>::V>
 __global__ void __launch_bounds__(256, MB) k_resid(DevMesh m, const T* __restrict__ st, const T* __restrict__ bvec, const T* __restrict__ x,
                         T* __restrict__ res) {
@@ -1009,7 +1030,7 @@ cudaError_t Precond::setup(const ElemCtx& c, double theta, const double* U, cons
 }
 
 template <typename T>
-cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout, bool* zdone) {
+cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout, bool* zdone, bool fold) {
   PrecondLevel& L = lv[l];
   Coef2<T> it, cc;
   double theta[2], delta[2], sigma[2], rho[2];
@@ -1060,6 +1081,15 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st, doubl
       L.pend = nullptr;
       return cudaGetLastError();
     }
+    if (fuse && fold && kk == degree - 2) {  // the smoothed x, last step included, into the free buffer
+      TUSAS_SMOOTH_LAUNCH(k_cheb_step_x, L, L.m, S, Di, X, Rr, dcur, cc, dnext);
+      void* old_x = L.x;
+      L.x = dnext;
+      L.d = dcur;
+      L.d2 = old_x;
+      L.pend = nullptr;
+      return cudaGetLastError();
+    }
     TUSAS_SMOOTH_LAUNCH(k_cheb_step, L, L.m, S, Di, X, Rr, dcur, dnext, cc, last);
     std::swap(dcur, dnext);
   }
@@ -1070,7 +1100,7 @@ template <typename T>
 cudaError_t Precond::vcycle(int l, cudaStream_t st, double* zout, bool* zdone) {
   const int last = (int)lv.size() - 1;
   if (l == last) return cheb<T>(l, true, coarse_degree, st);
-  cudaError_t e = cheb<T>(l, true, cheb_degree, st);
+  cudaError_t e = cheb<T>(l, true, cheb_degree, st, nullptr, nullptr, true);
   if (e != cudaSuccess) return e;
   PrecondLevel& F = lv[l];
   PrecondLevel& C = lv[l + 1];

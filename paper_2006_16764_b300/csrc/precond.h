@@ -58,9 +58,12 @@ class Precond {
   template <typename T>
   cudaError_t vcycle(int l, cudaStream_t st, double* zout = nullptr, bool* zdone = nullptr);
   // Chebyshev smoothing of level l; the last step's x += d is left to the next reader of
-  // x (residual, prolongation or the FP64 output), which adds lv[l].pend
+  // x (residual, prolongation or the FP64 output), which adds lv[l].pend. fold: the last
+  // stencil step writes x with that step included instead (a pre-smoothing followed by
+  // the residual)
   template <typename T>
-  cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout = nullptr, bool* zdone = nullptr);
+  cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout = nullptr, bool* zdone = nullptr,
+                   bool fold = false);
 };
 
 }  // namespace tusas
