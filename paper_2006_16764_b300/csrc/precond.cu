@@ -391,6 +391,12 @@ static dim3 grid3b(const DevMesh& m) {
   return dim3(g.x, g.y, 2 * g.z);
 }
 
+// k_prolong: one thread per fine x-pair (coarse column), fine row and plane
+static dim3 grid_prolong(const DevMesh& mf, const DevMesh& mc) {
+  const dim3 b = block3(mf);
+  return dim3((mc.nnx + b.x - 1) / b.x, (mf.nny + b.y - 1) / b.y, (mf.nnz + b.z - 1) / b.z);
+}
+
 static int grid_nodes(i64 n) {
   i64 g = (n + 255) / 256;
   if (g > 148 * 32) g = 148 * 32;
@@ -530,9 +536,13 @@ struct SmoothMinB {
 // stencil loads, which the larger budget keeps in flight at once instead of in several
 // dependent rounds (7.2 instead of 8.7 us per launch on a 33 x 25 x 9 level; a 702-block
 // level ran 2 us slower with it than with all its blocks resident at 32 registers).
-static const int SMOOTH_LAT_MINB = 2;
-static bool smooth_latency_grid(dim3 g) {
-  return (long long)g.x * g.y * g.z <= 148LL * SMOOTH_LAT_MINB;  // one wave of the variant
+// Grids of up to 3 blocks per SM (the 33 x 33 x 17 coarsest level of a 256 x 256 x 128 box: 324
+// blocks) take a 3-blocks-per-SM variant (up to 85 registers): every block is resident either
+// way, so the larger budget costs no occupancy.
+static const int SMOOTH_LAT_MINB = 2, SMOOTH_LAT3_MINB = 3;
+static int smooth_latency_grid(dim3 g) {
+  const long long nb = (long long)g.x * g.y * g.z;
+  return nb <= 148LL * SMOOTH_LAT_MINB ? SMOOTH_LAT_MINB : nb <= 148LL * SMOOTH_LAT3_MINB ? SMOOTH_LAT3_MINB : 0;
 }
 
 template <typename T>
@@ -683,21 +693,25 @@ __global__ void __launch_bounds__(256, MB)
 
 // One smoother-type launch on level LV (both blocks): the kernel instance for the level's
 // dimension and stencil radius, and for radius-1 levels that do not fill the GPU the
-// latency variant (SMOOTH_LAT_MINB). T and st come from the caller.
+// latency variants (SMOOTH_LAT_MINB, SMOOTH_LAT3_MINB). T and st come from the caller.
 #define TUSAS_SMOOTH_LAUNCH(KERN, LV, ...)                                                       \
   do {                                                                                          \
     const dim3 g_ = grid3b((LV).m), b_ = block3((LV).m);                                        \
-    const bool lat_ = smooth_latency_grid(g_);                                                  \
+    const int lat_ = smooth_latency_grid(g_);                                                   \
     if ((LV).m.dim == 3 && (LV).r == 2)                                                         \
       KERN<3, T, 2><<<g_, b_, 0, st>>>(__VA_ARGS__);                                            \
-    else if ((LV).m.dim == 3 && lat_)                                                           \
+    else if ((LV).m.dim == 3 && lat_ == SMOOTH_LAT_MINB)                                        \
       KERN<3, T, 1, SMOOTH_LAT_MINB><<<g_, b_, 0, st>>>(__VA_ARGS__);                           \
+    else if ((LV).m.dim == 3 && lat_ == SMOOTH_LAT3_MINB)                                       \
+      KERN<3, T, 1, SMOOTH_LAT3_MINB><<<g_, b_, 0, st>>>(__VA_ARGS__);                          \
     else if ((LV).m.dim == 3)                                                                   \
       KERN<3, T><<<g_, b_, 0, st>>>(__VA_ARGS__);                                               \
     else if ((LV).r == 2)                                                                       \
       KERN<2, T, 2><<<g_, b_, 0, st>>>(__VA_ARGS__);                                            \
-    else if (lat_)                                                                              \
+    else if (lat_ == SMOOTH_LAT_MINB)                                                           \
       KERN<2, T, 1, SMOOTH_LAT_MINB><<<g_, b_, 0, st>>>(__VA_ARGS__);                           \
+    else if (lat_ == SMOOTH_LAT3_MINB)                                                          \
+      KERN<2, T, 1, SMOOTH_LAT3_MINB><<<g_, b_, 0, st>>>(__VA_ARGS__);                          \
     else                                                                                        \
       KERN<2, T><<<g_, b_, 0, st>>>(__VA_ARGS__);                                               \
     count_launches(1);                                                                          \
@@ -754,30 +768,51 @@ __global__ void k_restrict(DevMesh mf, DevMesh mc, const T* __restrict__ res, T*
 // x_f(i) += sum_J P(i, J) (x_c(J) + p_c(J)); p_c: the coarse level's pending Chebyshev
 // direction, or null. Fine node i = 2J + a (a_d in {0, 1}) interpolates between the coarse
 // nodes J and J + a, axis by axis (x first) as the mean of the two values: where a_d = 0 both
-// are the same node and the mean is exact, so every node takes the same branch-free path.
+// are the same node and the mean is exact, so every node takes the same branch-free path. One
+// thread takes the fine x-pair 2j, 2j + 1 of one row in both blocks: the pair reads the same 2^dim
+// coarse values (the last coarse column has no odd fine node). Grid: grid_prolong.
 template <int DIM, typename T>
 __global__ void k_prolong(DevMesh mf, DevMesh mc, const T* __restrict__ xc, const T* __restrict__ pc,
                           T* __restrict__ xf) {
-  int fx, fy, fz;
-  i64 i;
-  if (!node3(mf, fx, fy, fz, i)) return;
+  const int jx = blockIdx.x * blockDim.x + threadIdx.x;
+  const int fy = blockIdx.y * blockDim.y + threadIdx.y;
+  const int fz = blockIdx.z * blockDim.z + threadIdx.z;
+  if (jx >= mc.nnx || fy >= mf.nny || fz >= mf.nnz) return;
   const i64 sy = mc.nnx, sz = (i64)mc.nnx * mc.nny;
-  const i64 J0 = (fx >> 1) + sy * (fy >> 1) + sz * (fz >> 1);
-  const i64 dx = fx & 1, dy = (fy & 1) ? sy : 0, dz = (DIM == 3 && (fz & 1)) ? sz : 0;
+  const i64 J0 = jx + sy * (fy >> 1) + sz * (fz >> 1);
+  const bool odd = jx + 1 < mc.nnx;  // fine node 2 jx + 1 exists
+  const i64 dx = odd ? 1 : 0, dy = (fy & 1) ? sy : 0, dz = (DIM == 3 && (fz & 1)) ? sz : 0;
+  const i64 i = 2 * (i64)jx + (i64)mf.nnx * (fy + (i64)mf.nny * fz);
   const T half = T(0.5);
 #pragma unroll
   for (int blk = 0; blk < 2; ++blk) {
     const T* xb = xc + blk * mc.nn;
     const T* pb = pc ? pc + blk * mc.nn : nullptr;
     auto cv = [&](i64 J) { return pb ? xb[J] + pb[J] : xb[J]; };
-    auto plane = [&](i64 J) {
-      const T e0 = half * (cv(J) + cv(J + dx));
-      const T e1 = half * (cv(J + dy) + cv(J + dy + dx));
+    // c[z][y][x]: the coarse values at J0 + (x ? dx : 0) + (y ? dy : 0) + (z ? dz : 0)
+    T c[DIM == 3 ? 2 : 1][2][2];
+#pragma unroll
+    for (int z = 0; z < (DIM == 3 ? 2 : 1); ++z) {
+      const i64 Jz = J0 + (z ? dz : 0);
+      c[z][0][0] = cv(Jz);
+      c[z][0][1] = cv(Jz + dx);
+      c[z][1][0] = cv(Jz + dy);
+      c[z][1][1] = cv(Jz + dy + dx);
+    }
+    // even node: both x values are the node itself (a_x = 0); odd node: the x-pair's two columns
+    auto plane = [&](int z, int ox) {
+      const T e0 = half * (c[z][0][0] + c[z][0][ox]);
+      const T e1 = half * (c[z][1][0] + c[z][1][ox]);
       return half * (e0 + e1);
     };
-    T v = plane(J0);
-    if (DIM == 3) v = half * (v + plane(J0 + dz));
-    xf[blk * mf.nn + i] += v;
+    T ve = plane(0, 0), vo = plane(0, 1);
+    if constexpr (DIM == 3) {
+      ve = half * (ve + plane(1, 0));
+      vo = half * (vo + plane(1, 1));
+    }
+    T* xo = xf + blk * mf.nn + i;
+    xo[0] += ve;
+    if (odd) xo[1] += vo;
   }
 }
 
@@ -1099,7 +1134,10 @@ cudaError_t Precond::cheb(int l, bool zero_x, int degree, cudaStream_t st, doubl
 template <typename T>
 cudaError_t Precond::vcycle(int l, cudaStream_t st, double* zout, bool* zdone) {
   const int last = (int)lv.size() - 1;
-  if (l == last) return cheb<T>(l, true, coarse_degree, st);
+  // below the finest level the smoothed x is read only by the prolongation: its last
+  // stencil step writes x with the step's own direction added (fold), so the prolongation
+  // reads one coarse array
+  if (l == last) return cheb<T>(l, true, coarse_degree, st, nullptr, nullptr, true);
   cudaError_t e = cheb<T>(l, true, cheb_degree, st, nullptr, nullptr, true);
   if (e != cudaSuccess) return e;
   PrecondLevel& F = lv[l];
@@ -1125,12 +1163,14 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st, double* zout, bool* zdone) {
   e = vcycle<T>(l + 1, st);
   if (e != cudaSuccess) return e;
   if (d3)
-    k_prolong<3, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend, (T*)F.x);
+    k_prolong<3, T><<<grid_prolong(F.m, C.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend,
+                                                                     (T*)F.x);
   else
-    k_prolong<2, T><<<grid3(F.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend, (T*)F.x);
+    k_prolong<2, T><<<grid_prolong(F.m, C.m), block3(F.m), 0, st>>>(F.m, C.m, (const T*)C.x, (const T*)C.pend,
+                                                                     (T*)F.x);
   count_launches(1);
   C.pend = nullptr;
-  return cheb<T>(l, false, cheb_degree, st, zout, zdone);
+  return cheb<T>(l, false, cheb_degree, st, zout, zdone, l > 0);
 }
 
 template <typename T>

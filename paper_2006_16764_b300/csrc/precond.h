@@ -60,7 +60,7 @@ class Precond {
   // Chebyshev smoothing of level l; the last step's x += d is left to the next reader of
   // x (residual, prolongation or the FP64 output), which adds lv[l].pend. fold: the last
   // stencil step writes x with that step included instead (a pre-smoothing followed by
-  // the residual)
+  // the residual, a coarse level's smoothing followed by the prolongation)
   template <typename T>
   cudaError_t cheb(int l, bool zero_x, int degree, cudaStream_t st, double* zout = nullptr, bool* zdone = nullptr,
                    bool fold = false);
