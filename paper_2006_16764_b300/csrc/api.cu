@@ -39,6 +39,9 @@ struct tusas_handle {
   cudaEvent_t ev_st = nullptr;    // recorded after k_arnoldi_givens
   tusas::Precond pc;
   bool pc_ready = false;
+  // the Krylov vector whose FP32 multigrid input the last Gram-Schmidt pass wrote (consumed by
+  // the next preconditioner apply of that vector), or null
+  const double* pc_input_for = nullptr;
   std::string err;
   // instrumentation: CUDA-event pairs per kernel class
   bool timers_on = false;
@@ -524,6 +527,7 @@ int tusas_precond_apply(tusas_handle* h, const double* r, double* z) {
     return TUSAS_OK;
   }
   if (!h->pc_ready) return fail(h, TUSAS_EINVAL, "call tusas_precond_setup first");
+  h->pc_input_for = nullptr;
   const size_t t0 = tbeg(h);
   TCK(h->pc.apply(r, z, h->st));
   tend(h, TUSAS_T_PC_APPLY, t0);
@@ -597,8 +601,10 @@ static int prec_apply(tusas_handle* h, const double* r, double* z) {
     TCK(tusas::vcopy(h->N, r, z, h->st));
     return TUSAS_OK;
   }
+  const bool input_ready = r == h->pc_input_for;
+  h->pc_input_for = nullptr;
   const size_t t0 = tbeg(h);
-  TCK(h->pc.apply(r, z, h->st));
+  TCK(h->pc.apply(r, z, h->st, input_ready));
   tend(h, TUSAS_T_PC_APPLY, t0);
   return TUSAS_OK;
 }
@@ -678,6 +684,7 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
   std::vector<double> H((m + 1) * m), g(m + 1), y(m);
   double stat[4];
   TCK(cudaMemsetAsync(x, 0, sizeof(double) * N, h->st));
+  h->pc_input_for = nullptr;
   int its = 0;
   // r = b
   double* r = h->V;  // V_0 doubles as the residual buffer
@@ -714,7 +721,12 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       tusas::count_launches(1);
       TCK(cudaGetLastError());
       TCK(cudaEventRecord(h->ev_st, h->st));
-      TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, dst + 2, w, h->partials, nullptr, h->st));
+      // the FP32 multigrid's input for w, preconditioned next unless the cycle ends here
+      tusas::GsNarrow nw;
+      const bool narrow_w = j + 1 < m && h->prm.precond != 0 && h->pc.fp32_input(&nw.b, &nw.db, &nw.dinv);
+      TCK(tusas::gs_pass(2, N, j + 1, h->V, N, h->sc + 64, dst + 2, w, h->partials, nullptr, h->st,
+                         narrow_w ? nw : tusas::GsNarrow()));
+      h->pc_input_for = narrow_w ? w : nullptr;
       tend(h, TUSAS_T_ORTHO, to);
       // the status is read while the last pass runs
       TCK(cudaEventSynchronize(h->ev_st));
@@ -724,6 +736,7 @@ static int gmres(tusas_handle* h, int op, const double* b, double* x, double tol
       mu = j + 1;
       if (resid <= tol_abs || its >= maxit || stat[3] == 0.0) break;
     }
+    h->pc_input_for = nullptr;
     // the triangle R = H[0..mu-1][0..mu-1] and g once per cycle
     TCK(cudaMemcpyAsync(H.data(), dH, sizeof(double) * mu * m, cudaMemcpyDeviceToHost, h->st));
     TCK(cudaMemcpyAsync(g.data(), dg, sizeof(double) * (mu + 1), cudaMemcpyDeviceToHost, h->st));

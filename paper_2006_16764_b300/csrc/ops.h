@@ -122,10 +122,17 @@ cudaError_t multi_axpy_norm(i64 n, int k, const double* X, i64 ld, const double*
 //   pass 0: out[j] = X_j . w (reduced)
 //   pass 1: w -= sum_j c[j] X_j, then the per-block partial sums of X_j . w in partials[b][j]
 //           and of ||w||^2 in partials[b][k], left for the caller to reduce (b < gs_blocks())
-//   pass 2: w = (w - sum_j c[j] X_j) s[0]
+//   pass 2: w = (w - sum_j c[j] X_j) s[0]; with nw.b set it also writes nw.b = w narrowed
+//           to FP32 (narrow<float>) and nw.db = nw.dinv * nw.b, the FP32 multigrid's input
+//           for w (Precond::fp32_input), n elements each
+struct GsNarrow {
+  float* b = nullptr;
+  float* db = nullptr;
+  const float* dinv = nullptr;
+};
 int gs_blocks();
 cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, const double* s, double* w,
-                    double* partials, double* out, cudaStream_t st);
+                    double* partials, double* out, cudaStream_t st, GsNarrow nw = GsNarrow());
 // x = sum_j c[j] X_j + x (c on host memory passed by value through a device array)
 cudaError_t multi_comb(i64 n, int k, const double* X, i64 ld, const double* c, double* x, cudaStream_t st);
 

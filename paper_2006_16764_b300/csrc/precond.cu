@@ -1174,7 +1174,7 @@ cudaError_t Precond::vcycle(int l, cudaStream_t st, double* zout, bool* zdone) {
 }
 
 template <typename T>
-cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
+cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st, bool input_ready) {
   PrecondLevel& L0 = lv[0];
   const i64 n = 2 * L0.nn;
   if (kind == 1) {
@@ -1184,7 +1184,7 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
     }
     return cudaGetLastError();
   }
-  {
+  if (!input_ready) {
     // FP32: D^-1 b into the level's residual buffer (free until its residual pass) for k_cheb_first
     T* db = sizeof(T) == sizeof(float) ? (T*)L0.res : nullptr;
     k_to_t<T><<<grid_nodes(n), 256, 0, st>>>(n, r, (T*)L0.b, (const T*)L0.dinv, db);
@@ -1201,9 +1201,18 @@ cudaError_t Precond::apply_t(const double* r, double* z, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t Precond::apply(const double* r, double* z, cudaStream_t st) {
+cudaError_t Precond::apply(const double* r, double* z, cudaStream_t st, bool input_ready) {
   if (kind == 0 || lv.empty()) return cudaErrorInvalidValue;  // identity is applied by the caller
-  return fp32 ? apply_t<float>(r, z, st) : apply_t<double>(r, z, st);
+  if (input_ready && !fp32_input(nullptr, nullptr, nullptr)) return cudaErrorInvalidValue;
+  return fp32 ? apply_t<float>(r, z, st, input_ready) : apply_t<double>(r, z, st, false);
+}
+
+bool Precond::fp32_input(float** b, float** db, const float** dinv) const {
+  if (kind != 2 || !fp32 || lv.empty()) return false;
+  if (b) *b = (float*)lv[0].b;
+  if (db) *db = (float*)lv[0].res;  // free until the level's residual pass (k_cheb_first reads it)
+  if (dinv) *dinv = (const float*)lv[0].dinv;
+  return true;
 }
 
 }  // namespace tusas

@@ -43,14 +43,20 @@ class Precond {
   // coefficients of Eqs. pref2 / preconc2), the Galerkin coarse stencils,
   // D^-1 and the Gershgorin bounds. Synchronises the stream once.
   cudaError_t setup(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st);
-  // z = M^-1 r (FP64 in and out).
-  cudaError_t apply(const double* r, double* z, cudaStream_t st);
+  // z = M^-1 r (FP64 in and out). input_ready: the FP32 multigrid's input for r (the slots
+  // of fp32_input) was written by the caller after the last setup, so the narrowing pass is
+  // skipped.
+  cudaError_t apply(const double* r, double* z, cudaStream_t st, bool input_ready = false);
+  // The FP32 multigrid's input slots, for a caller that produces r itself: b = r narrowed to
+  // FP32 (narrow<float>) and db = dinv * b, 2 nn floats each. False (and nothing set) for
+  // point Jacobi or an FP64 hierarchy.
+  bool fp32_input(float** b, float** db, const float** dinv) const;
 
  private:
   template <typename T>
   cudaError_t setup_t(const ElemCtx& c, double theta, const double* U, const double* Un, cudaStream_t st);
   template <typename T>
-  cudaError_t apply_t(const double* r, double* z, cudaStream_t st);
+  cudaError_t apply_t(const double* r, double* z, cudaStream_t st, bool input_ready);
   template <typename T>
   cudaError_t galerkin_and_bounds(cudaStream_t st);
   // zout: the finest level's post-smoothing writes its result there in FP64 (and sets

@@ -435,11 +435,24 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_dots(i64 nv, int k, const do
   gs_block_sum<KM + 1>(acc, k + 1, partials);
 }
 
-// pass 2: w = (w - sum_j c_j X_j) s[0]
+// The FP32 multigrid's input for the vector element(s) e of pass 2 (GsNarrow).
+__device__ __forceinline__ void gs_narrow_store(const GsNarrow& nw, i64 e, double o) {
+  const float b = narrow<float>(o);
+  nw.b[e] = b;
+  nw.db[e] = nw.dinv[e] * b;
+}
+__device__ __forceinline__ void gs_narrow_store(const GsNarrow& nw, i64 e, double2 o) {
+  const float2 b = make_float2(narrow<float>(o.x), narrow<float>(o.y));
+  const float2 d = reinterpret_cast<const float2*>(nw.dinv)[e];
+  reinterpret_cast<float2*>(nw.b)[e] = b;
+  reinterpret_cast<float2*>(nw.db)[e] = make_float2(d.x * b.x, d.y * b.y);
+}
+
+// pass 2: w = (w - sum_j c_j X_j) s[0], and the FP32 multigrid's input for w if nw.b is set
 template <int KM, int VEC, bool EXACT>
 __global__ void __launch_bounds__(GS_T) k_gs_update_scale(i64 nv, int k, const double* __restrict__ X, i64 ldv,
                                                           const double* __restrict__ c, const double* __restrict__ s,
-                                                          double* __restrict__ w) {
+                                                          double* __restrict__ w, GsNarrow nw) {
   typedef typename Vec<VEC>::T T;
   constexpr int UNR = GsUnroll<KM>::V;
   if (EXACT) k = KM;
@@ -467,7 +480,11 @@ __global__ void __launch_bounds__(GS_T) k_gs_update_scale(i64 nv, int k, const d
       for (int j = 0; j < KM; ++j)
         if (EXACT || j < k) wi[u] = Vec<VEC>::axpy(cc[j], x[j][u], wi[u]);
       const i64 e = i + (i64)u * GS_T;
-      if (e < hi) wv[e] = Vec<VEC>::scale(sc, wi[u]);
+      if (e < hi) {
+        const T o = Vec<VEC>::scale(sc, wi[u]);
+        wv[e] = o;
+        if (nw.b) gs_narrow_store(nw, e, o);
+      }
     }
   }
 }
@@ -514,13 +531,13 @@ static const int GS_FUSED_MAX = 16;
 // 3: update alone; 4: dots + norm (3 then 4 is pass 1 for long cycles)
 template <int KM, int VEC, bool EXACT>
 static void gs_kernel(int pass, i64 nv, int k, const double* X, i64 ldv, const double* c, const double* s, double* w,
-                      double* partials, cudaStream_t st) {
+                      double* partials, cudaStream_t st, GsNarrow nw) {
   if (pass == 0) {
     k_gs_dots<KM, VEC, EXACT, false><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, w, partials);
   } else if (pass == 1) {
     if constexpr (KM <= GS_FUSED_MAX) k_gs_update_dots<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w, partials);
   } else if (pass == 2) {
-    k_gs_update_scale<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, s, w);
+    k_gs_update_scale<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, s, w, nw);
   } else if (pass == 3) {
     k_gs_update<KM, VEC, EXACT><<<GS_BLOCKS, GS_T, 0, st>>>(nv, k, X, ldv, c, w);
   } else {
@@ -531,12 +548,12 @@ static void gs_kernel(int pass, i64 nv, int k, const double* X, i64 ldv, const d
 // 16-byte loads: one instantiation per vector count up to 30 (the longest GMRES cycle); the
 // scalar-load fallback takes rounded counts.
 static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 ld, const double* c,
-                                  const double* s, double* w, double* partials, cudaStream_t st) {
+                                  const double* s, double* w, double* partials, cudaStream_t st, GsNarrow nw) {
   const i64 nv = n / 2, ldv = ld / 2;
   switch (k) {
 #define TUSAS_GS_K(K) \
   case K:             \
-    gs_kernel<K, 2, true>(pass, nv, k, X, ldv, c, s, w, partials, st); \
+    gs_kernel<K, 2, true>(pass, nv, k, X, ldv, c, s, w, partials, st, nw); \
     break;
     TUSAS_GS_K(1) TUSAS_GS_K(2) TUSAS_GS_K(3) TUSAS_GS_K(4) TUSAS_GS_K(5) TUSAS_GS_K(6) TUSAS_GS_K(7)
     TUSAS_GS_K(8) TUSAS_GS_K(9) TUSAS_GS_K(10) TUSAS_GS_K(11) TUSAS_GS_K(12) TUSAS_GS_K(13) TUSAS_GS_K(14)
@@ -545,22 +562,22 @@ static cudaError_t gs_launch_vec2(int pass, i64 n, int k, const double* X, i64 l
     TUSAS_GS_K(29) TUSAS_GS_K(30)
 #undef TUSAS_GS_K
     default:
-      gs_kernel<31, 2, false>(pass, nv, k, X, ldv, c, s, w, partials, st);
+      gs_kernel<31, 2, false>(pass, nv, k, X, ldv, c, s, w, partials, st, nw);
   }
   count_launches(1);
   return cudaGetLastError();
 }
 
 static cudaError_t gs_launch_scalar(int pass, i64 n, int k, const double* X, i64 ld, const double* c,
-                                    const double* s, double* w, double* partials, cudaStream_t st) {
+                                    const double* s, double* w, double* partials, cudaStream_t st, GsNarrow nw) {
   if (k <= 4)
-    gs_kernel<4, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
+    gs_kernel<4, 1, false>(pass, n, k, X, ld, c, s, w, partials, st, nw);
   else if (k <= 8)
-    gs_kernel<8, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
+    gs_kernel<8, 1, false>(pass, n, k, X, ld, c, s, w, partials, st, nw);
   else if (k <= 16)
-    gs_kernel<16, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
+    gs_kernel<16, 1, false>(pass, n, k, X, ld, c, s, w, partials, st, nw);
   else
-    gs_kernel<31, 1, false>(pass, n, k, X, ld, c, s, w, partials, st);
+    gs_kernel<31, 1, false>(pass, n, k, X, ld, c, s, w, partials, st, nw);
   count_launches(1);
   return cudaGetLastError();
 }
@@ -568,20 +585,24 @@ static cudaError_t gs_launch_scalar(int pass, i64 n, int k, const double* X, i64
 int gs_blocks() { return GS_BLOCKS; }
 
 cudaError_t gs_pass(int pass, i64 n, int k, const double* X, i64 ld, const double* c, const double* s, double* w,
-                    double* partials, double* out, cudaStream_t st) {
+                    double* partials, double* out, cudaStream_t st, GsNarrow nw) {
   if (k < 1 || k > 31 || pass < 0 || pass > 2) return cudaErrorInvalidValue;
-  const bool vec = n % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)w % 16) == 0;
+  if (pass != 2) nw = GsNarrow();
+  if (nw.b && (!nw.db || !nw.dinv)) return cudaErrorInvalidValue;
+  // the 16-byte path stores the FP32 outputs as 8-byte pairs
+  const bool nw_ok = !nw.b || (((uintptr_t)nw.b | (uintptr_t)nw.db | (uintptr_t)nw.dinv) % 8) == 0;
+  const bool vec = n % 2 == 0 && ld % 2 == 0 && ((uintptr_t)X % 16) == 0 && ((uintptr_t)w % 16) == 0 && nw_ok;
   if (pass == 1 && k > GS_FUSED_MAX) {
     // the fused update + dots would spill with this many vectors in registers: update, then
     // dots + norm
-    cudaError_t e = vec ? gs_launch_vec2(3, n, k, X, ld, c, s, w, partials, st)
-                        : gs_launch_scalar(3, n, k, X, ld, c, s, w, partials, st);
+    cudaError_t e = vec ? gs_launch_vec2(3, n, k, X, ld, c, s, w, partials, st, nw)
+                        : gs_launch_scalar(3, n, k, X, ld, c, s, w, partials, st, nw);
     if (e != cudaSuccess) return e;
-    return vec ? gs_launch_vec2(4, n, k, X, ld, c, s, w, partials, st)
-               : gs_launch_scalar(4, n, k, X, ld, c, s, w, partials, st);
+    return vec ? gs_launch_vec2(4, n, k, X, ld, c, s, w, partials, st, nw)
+               : gs_launch_scalar(4, n, k, X, ld, c, s, w, partials, st, nw);
   }
-  cudaError_t e = vec ? gs_launch_vec2(pass, n, k, X, ld, c, s, w, partials, st)
-                      : gs_launch_scalar(pass, n, k, X, ld, c, s, w, partials, st);
+  cudaError_t e = vec ? gs_launch_vec2(pass, n, k, X, ld, c, s, w, partials, st, nw)
+                      : gs_launch_scalar(pass, n, k, X, ld, c, s, w, partials, st, nw);
   if (e != cudaSuccess || pass != 0) return e;
   k_reduce_partials<<<1, 32 * k, 0, st>>>(GS_BLOCKS, k, 32, partials, out);
   count_launches(1);
