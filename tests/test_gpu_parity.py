@@ -106,15 +106,20 @@ def test_residual_is_bitwise_deterministic():
 def _precond_case(dim, fp32, kind=2):
     if dim == 2:
         w = synth.scaled(synth.workload("dendrite2d_1024"), 32, 32)
-    else:
+    elif dim == 3:
         w = synth.scaled(synth.workload("alloy3d_256x256x128"), 16, 16, 32)
+    else:
+        # 65 x 65 x 33 nodes: the finest level launches 1734 smoother blocks (the 8-blocks-per-SM
+        # build), the 33 x 33 x 17 level 324 (the 3-blocks-per-SM build), the coarser ones fewer
+        # than 297 (the 2-blocks-per-SM build)
+        w = synth.scaled(synth.workload("alloy3d_256x256x128"), 64, 64, 32)
     prm = dataclasses.replace(w.params, precond=kind, smoother_fp32=fp32)
     U0 = synth.initial_state(w)
     U = U0 + 0.01 * synth.random_vector(w.mesh, 3)
     return w, prm, U, U0
 
 
-@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("dim", [2, 3, "3d-64x64x32"])
 @pytest.mark.parametrize("kind,fp32,tol", [(1, 0, 1e-13), (2, 0, 1e-10), (2, 1, 2e-4)])
 def test_preconditioner_matches_oracle(dim, kind, fp32, tol):
     """Jacobi and the GMG V-cycle per block: FP64 operators to roundoff, FP32 to a few
