@@ -251,10 +251,9 @@ int tusas_fma_peak(double* fp64_flops, double* fp32_flops);
  * (TUSAS_NOALLOC_MAX_K x 296 + TUSAS_NOALLOC_MAX_K doubles, about 76 KB per
  * GPU, held until the process exits); nothing is allocated or freed. The
  * first call on a device looks up that array's address (cudaGetSymbolAddress
- * with the device current) and keeps it for the process; make that first call
- * before any stream capture. A cudaDeviceReset of that device reloads the
- * library's module and makes the kept address stale: do not call this entry
- * point on a device after resetting it.
+ * with the device current) and keeps it for the process. A cudaDeviceReset of
+ * that device reloads the library's module and makes the kept address stale:
+ * do not call this entry point on a device after resetting it.
  * All calls share the array: calls that overlap on the GPU race and must be
  * serialised by the caller. Works on `stream` (a cudaStream_t, NULL = legacy
  * default) and synchronises it. Returns TUSAS_EINVAL for k < 1,
