@@ -81,6 +81,38 @@ def test_tangent_adjoint_and_parameter_derivative(name, mesh, prm):
     assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v)) <= 1e-5
 
 
+@pytest.mark.parametrize("name,mesh,prm", [
+    ("2d-alloy", Mesh(2, 35, 17, 0, 0.8), ALLOY),
+    ("3d-alloy-literal", Mesh(3, 17, 10, 9, 0.8), dataclasses.replace(ALLOY, time_form=1)),
+    ("3d-pure", Mesh(3, 19, 9, 6, 0.8, -1.0, 2.0, 0.5), PURE),
+], ids=["2d-alloy", "3d-alloy-literal", "3d-pure"])
+def test_flat_phase_field_takes_the_zero_gradient_branch(name, mesh, prm):
+    """phi = 1 (U and U^n) on the nodes with x index below 7: there grad phi is exactly zero at
+    every Gauss point, and both sides take the anisotropy's guarded branch (a = 1, n = 0) for
+    the residual, the tangent, the transposes and dF/d eps4."""
+    U, Un = _inputs(mesh, 13)
+    n = mesh.n_nodes
+    flat = np.arange(n) % (mesh.nx + 1) < 7
+    U[:n][flat] = 1.0
+    Un[:n][flat] = 1.0
+    v = synth.random_vector(mesh, 14)
+    dt, tn = 0.37, 1.25
+    h = handle(mesh, prm)
+    h.set_state(dev(Un), tn, dt)
+    tU, tv = dev(U), dev(v)
+    out = dev(np.zeros_like(U))
+    h.residual(tU, out)
+    assert rel(host(out), OR.residual(mesh, prm, U, Un, tn, dt)) <= 1e-12
+    h.jvp(tU, tv, out)
+    assert rel(host(out), OJ.jvp(mesh, prm, U, Un, tn, dt, v)) <= 1e-12
+    h.jtvp(tU, tv, out)
+    assert rel(host(out), OJ.jtvp(mesh, prm, U, Un, tn, dt, v)) <= 1e-12
+    h.jtvp_prev(tU, tv, out)
+    assert rel(host(out), OJ.dF_dUn_T(mesh, prm, U, Un, tn, dt, v)) <= 1e-12
+    h.dFdp(tU, out, 0)
+    assert rel(host(out), OJ.dF_deps4(mesh, prm, U, Un, tn, dt)) <= 1e-12
+
+
 def test_residual_is_bitwise_deterministic():
     mesh = Mesh(3, 21, 13, 9, 0.8)
     U, Un = _inputs(mesh, 3)
