@@ -362,9 +362,15 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
   // 3D: tile-level sum factorisation for the tangent and residual passes
   constexpr bool tan3 = DIM == 3 && (MODE == M_JV || MODE == M_JTV);
   constexpr bool res3 = DIM == 3 && (MODE == M_RES || MODE == M_RES_LIN);
+  // the residual stages phi^n with gradients and phihat_old only where the time term or the
+  // Eq. (theta) estimate uses them (Res3L<true>); otherwise the smaller layout
+  const bool ext = a.P.time_form != 0 || (a.P.phihat_old && a.phold);
   if constexpr (res3) {
-    const cudaError_t e = cudaFuncSetAttribute(res3_kernel<MODEL, MODE == M_RES_LIN>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Res3::BYTES);
+    const cudaError_t e =
+        ext ? cudaFuncSetAttribute(res3_kernel<MODEL, MODE == M_RES_LIN, true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Res3L<true>::BYTES)
+            : cudaFuncSetAttribute(res3_kernel<MODEL, MODE == M_RES_LIN, false>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Res3L<false>::BYTES);
     if (e != cudaSuccess) return e;
   }
   for (int col = 0; col < (1 << DIM); ++col) {
@@ -379,7 +385,10 @@ static cudaError_t run_colours(const ElemCtx& c, ElemArgs a, cudaStream_t st) {
     if constexpr (tan3)
       e = launch_colour(tan3_kernel<MODEL, MODE == M_JTV>, (unsigned)blocks, T3::NE, Tan3::BYTES, st, col > 0, a);
     else if constexpr (res3)
-      e = launch_colour(res3_kernel<MODEL, MODE == M_RES_LIN>, (unsigned)blocks, T3::NE, Res3::BYTES, st, col > 0, a);
+      e = ext ? launch_colour(res3_kernel<MODEL, MODE == M_RES_LIN, true>, (unsigned)blocks, T3::NE,
+                              Res3L<true>::BYTES, st, col > 0, a)
+              : launch_colour(res3_kernel<MODEL, MODE == M_RES_LIN, false>, (unsigned)blocks, T3::NE,
+                              Res3L<false>::BYTES, st, col > 0, a);
     else
       e = launch_colour(elem_kernel<DIM, MODEL, MODE>, (unsigned)blocks, NE, 0, st, col > 0, a);
     if (e != cudaSuccess) return e;

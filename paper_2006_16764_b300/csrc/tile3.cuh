@@ -437,39 +437,42 @@ __global__ void __launch_bounds__(T3::NE, 4) tan3_kernel(const ElemArgs A) {
 }
 
 // ---- residual (LIN = false) and residual + stored linearisation (LIN = true) -----------
-// Nodal fields: phi, u (with gradients), phi - phi^n, u - u^n (values), phi^n (with
-// gradients, for the difference-of-products time term) and phihat_old (values, for the
-// Eq. (theta) estimate); the optional ones are staged only when used.
-struct Res3 {
-  static const int NF = 6;
-  static const int OFF_X = 0;                                   // x-stage of the 6 fields
+// Nodal fields: phi, u (with gradients), phi - phi^n, u - u^n (values), and with EXT phi^n
+// (with gradients, for the difference-of-products time term) and phihat_old (values, for the
+// Eq. (theta) estimate), staged only when used. Without EXT the layout holds the first four:
+// 48 KB instead of 70 KB per CTA.
+template <bool EXT>
+struct Res3L {
+  static const int NF = EXT ? 6 : 4;
+  static const int OFF_X = 0;                                   // x-stage of the NF fields
   static const int X_PHI = 0, X_U = T3::XG, X_DP = 2 * T3::XG, X_DU = X_DP + T3::XV, X_PN = X_DU + T3::XV,
                    X_PO = X_PN + T3::XG;
-  static const int XS = X_PO + T3::XV;
-  static const int OFF_N = XS;                                  // staged nodes [6][NT]
+  static const int XS = EXT ? X_PO + T3::XV : X_PN;
+  static const int OFF_N = XS;                                  // staged nodes [NF][NT]
   static const int OFF_Y = XS;                                  // y-stage (aliases the nodes)
   static const int Y_PHI = 0, Y_U = T3::YG, Y_DP = 2 * T3::YG, Y_DU = Y_DP + T3::YV, Y_PN = Y_DU + T3::YV,
                    Y_PO = Y_PN + T3::YG;
-  static const int YS = Y_PO + T3::YV;
+  static const int YS = EXT ? Y_PO + T3::YV : Y_PN;
   static const int NS = NF * T3::NT;
   static const int FWD = XS + (YS > NS ? YS : NS);
   static const int DOUBLES = FWD > T3::BWD ? FWD : T3::BWD;
   static const size_t BYTES = sizeof(double) * DOUBLES;
 };
 
-// The residual runs 3 CTAs per SM: with the Gauss points taken by column it needs 156
-// registers (all eight points' interpolated inputs at once needed 206, and forcing 3 CTAs
-// then spilled); the linearisation pass, 200 registers, runs 2.
-template <int MODEL, bool LIN>
-__global__ void __launch_bounds__(T3::NE, (LIN ? 2 : 3)) res3_kernel(const ElemArgs A) {
+// The residual runs 3 CTAs per SM with the EXT layout and 4 without: with the Gauss points
+// taken by column it needs 152 registers (all eight points' interpolated inputs at once
+// needed 206, and forcing 3 CTAs then spilled); the linearisation pass, 200 registers, runs 2.
+template <int MODEL, bool LIN, bool EXT>
+__global__ void __launch_bounds__(T3::NE, (LIN ? 2 : (EXT ? 3 : 4))) res3_kernel(const ElemArgs A) {
   constexpr int NE = T3::NE, NT = T3::NT;
   constexpr int NC = NLin<3, MODEL>::VALUE;
+  using Res3 = Res3L<EXT>;
   extern __shared__ double sm[];
   const DevMesh& m = A.m;
   const T3Tile T(A);
   const int tid = threadIdx.x;
-  const bool tf1 = A.P.time_form != 0;
-  const bool pho_on = A.P.phihat_old && A.phold;
+  const bool tf1 = EXT && A.P.time_form != 0;
+  const bool pho_on = EXT && A.P.phihat_old && A.phold;
   // the next tile colour may start on free SMs now (it waits at the node sums)
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
   double* sN = sm + Res3::OFF_N;
