@@ -45,14 +45,14 @@ CPU_SAMPLE = (48, 48, 32)
 # the conversions and the inactive lanes of every FP64 instruction. Measured on the full
 # 256x256x128 alloy box in the state the bench times: the isolated residual on the converged
 # state (its flat Gauss points skip the anisotropy), the mean of the 5 linearisation passes of
-# one step (1316-1397), the tangent (its instruction stream does not depend on the data).
+# one step (1297-1378), the tangent (its instruction stream does not depend on the data).
 # Against the pipe's slot rate (the FMA-chain peak / 2) they give its occupancy.
-FP64_PIPE_SLOTS_PER_ELEM = {"residual": 745.9, "residual_lin": 1355.2, "jv": 501.0}
+FP64_PIPE_SLOTS_PER_ELEM = {"residual": 739.5, "residual_lin": 1336.2, "jv": 501.0}
 # On the 256x192x64 profiling box, per element: the same slots, and the FP64 flops of the
 # compiled kernels (DADD + DMUL + 2 DFMA: smsp__sass_thread_inst_executed_op_d{add,mul,fma}_pred_on,
 # which take three passes and so are not captured on the full box).
-PROFILE_PIPE_SLOTS_PER_ELEM = {"residual": 826.5, "residual_lin": 1407.5, "jv": 501.0}
-PROFILE_FLOPS_PER_ELEM = {"residual": 1128.3, "residual_lin": 1894.3, "jv": 802.7}
+PROFILE_PIPE_SLOTS_PER_ELEM = {"residual": 827.5, "residual_lin": 1388.5, "jv": 501.0}
+PROFILE_FLOPS_PER_ELEM = {"residual": 1149.3, "residual_lin": 1891.3, "jv": 802.7}
 # FP64 flops per element on the full box: its slots times the profiling box's flops per slot
 # (exact for the tangent; an estimate for the residual passes, whose skipped work has about
 # the mix of the rest).
@@ -68,7 +68,7 @@ LIN_BYTES_PER_ELEM = 22 * 8 * 8.0
 # DRAM bytes per element measured by ncu on the same pass (dram__bytes_read.sum +
 # dram__bytes_write.sum over the 8 colour launches / elements); the traffic scales
 # with the elements processed (same tiles, same per-element streams).
-NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1447.6, "jv": 1544.8}
+NCU_BYTES_PER_ELEM = {"residual": 153.2, "residual_lin": 1447.7, "jv": 1544.7}
 
 
 def parse():
@@ -883,8 +883,8 @@ def run_ours(args, ws, rank, local):
                  "peak_tflops": fp64_peak / 1e12,
                  "frac": FP64_FLOPS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / fp64_peak,
                  "issue_frac": FP64_PIPE_SLOTS_PER_ELEM["residual"] * ne / (res_per * 1e-3) / (fp64_peak / 2),
-                 "basis": "FP64-pipe slots per element measured on this box and state (ncu, 745.9); flops "
-                          "from them with the profiling box's flops per slot (estimate)"},
+                 "basis": "FP64-pipe slots per element measured on this box and state (ncu, %.1f); flops "
+                          "from them with the profiling box's flops per slot (estimate)" % FP64_PIPE_SLOTS_PER_ELEM["residual"]},
         "hbm": {"algorithmic_bytes": ALG_BYTES_PER_NODE["residual"] * nn,
                 "achieved_gbs": ALG_BYTES_PER_NODE["residual"] * nn / (res_per * 1e-3) / 1e9,
                 "peak_gbs": hbm_peak, "peak_kind": hbm_kind},
